@@ -1,0 +1,174 @@
+/*
+ * libsci -- GAP-TV / ADMM-TV reconstruction for video snapshot compressive
+ * imaging (SCI) on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: X. Yuan, "Various Total Variation for Snapshot Video Compressive
+ * Imaging", arXiv 2005.08028.  Equation numbers count the paper's numbered
+ * displays in order (Eq. 3: Y = sum_k X_k . C_k + G; Eqs. 21-22: GAP;
+ * Eqs. 24-26: ADMM; Eqs. 29-32: the ITV2D/ITV3D dual projections);
+ * "Algorithm 1" is the paper's GAP-ATV-Clip/Cham/FGP listing.
+ *
+ * Conventions for every call below
+ * --------------------------------
+ *  - Layout: a video (x, theta, u) is float32 [B][nx][ny], frame-major then
+ *    row-major; element (k, i, j) is at k*nx*ny + i*ny + j.  i < nx is the
+ *    vertical index (difference operator D_v), j < ny the horizontal one (D_h).
+ *    A measurement y is float32 [nx][ny].
+ *  - Masks: binary masks C_k in {0,1} (B <= 32) are passed bit-packed as
+ *    uint32 [nx][ny]; bit k of word (i, j) is C_k(i, j).  sci_masks_pack
+ *    builds this from a dense uint8 [B][nx][ny] array.
+ *  - Pointers: all array pointers are DEVICE pointers owned by the caller,
+ *    unless a comment says "host".  The library never frees or keeps them
+ *    beyond the call (the solver's CUDA-graph cache remembers their values;
+ *    see sci_graph_cache_clear).
+ *  - Scratch: calls that need scratch take (work, work_bytes), a caller-owned
+ *    device buffer of at least the size that the matching *_workspace query
+ *    returns, aligned to 256 bytes.  The library allocates no device memory.
+ *  - Streams: every call is asynchronous on `stream` (a cudaStream_t; NULL is
+ *    the legacy default stream).  Argument errors are detected on the host and
+ *    returned before anything is enqueued.  SCI_ERR_CUDA reports a failed
+ *    launch (cudaGetLastError after the enqueue); errors raised while the
+ *    kernels run surface at the caller's next synchronisation.
+ *  - No exceptions cross this interface.
+ */
+#ifndef SCI_H_
+#define SCI_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* sci_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+    SCI_OK = 0,
+    SCI_ERR_ARG = 1,        /* null pointer, non-positive size, bad enum, lambda <= 0, ... */
+    SCI_ERR_SHAPE = 2,      /* B > 32, or sizes whose element count overflows */
+    SCI_ERR_CUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+    SCI_ERR_NONFINITE = 4,  /* non-finite scalar argument */
+    SCI_ERR_TIMEOUT = 5,    /* reserved: a bounded device-side wait gave up */
+    SCI_ERR_WORKSPACE = 6   /* work == NULL, misaligned, or work_bytes too small */
+} sci_status;
+
+typedef enum { SCI_TV_ATV = 0, SCI_TV_ITV2D = 1, SCI_TV_VTV = 2 } sci_tv_type;
+typedef enum { SCI_F32 = 0, SCI_BF16 = 1, SCI_F16 = 2 } sci_dtype;
+
+/* Solver parameters (Algorithm 1; Sec. 2.2). */
+typedef struct {
+    int tv;           /* sci_tv_type: ATV (Eq. 8), ITV2D (Eq. 9) or VTV = ITV3D (Eq. 10) */
+    float lambda;     /* TV weight lambda > 0 of TVdenoise = prox of lambda*TV */
+    float rho;        /* ADMM penalty rho >= 0 (Eq. 24); ignored by sci_gap_tv */
+    int outer_iters;  /* T >= 0 outer iterations */
+    int inner_iters;  /* S >= 1 FGP dual updates per TVdenoise */
+    int storage;      /* sci_dtype of the library's internal fields; math is FP32 */
+    int fuse_k;       /* FGP updates fused per launch; 0 = library choice */
+    int init;         /* 1: start from theta = Phi^T y (and u = 0); 0: resume from theta (and u) */
+    int use_graph;    /* 1: run the T iterations as one cached CUDA graph; 0: plain launches */
+} sci_params;
+
+/* Human-readable name of a status code (static string). */
+const char* sci_status_str(sci_status s);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int sci_version(void);
+
+/*
+ * Pack dense binary masks into the bit layout above (storage only; Eq. 2's
+ * D_k = diag(vec C_k)).  masks: uint8 [B][nx][ny] with values 0 or 1.
+ * bits: uint32 [nx][ny] (output).  bad_count: optional device int that the
+ * kernel increments once per entry that is neither 0 nor 1 (such entries are
+ * packed as 1); pass NULL to skip the check.  1 <= B <= 32.
+ */
+sci_status sci_masks_pack(const uint8_t* masks, int nx, int ny, int B, uint32_t* bits,
+                          int* bad_count, sci_stream_t stream);
+
+/* Forward operator y = Phi x = sum_k C_k . X_k (Eq. 3 without noise). */
+sci_status sci_forward(const float* x, const uint32_t* bits, int nx, int ny, int B,
+                       float* y, sci_stream_t stream);
+
+/* Adjoint x = Phi^T y: X_k = C_k . Y (Phi = [D_1..D_B], Eq. 2). */
+sci_status sci_adjoint(const float* y, const uint32_t* bits, int nx, int ny, int B,
+                       float* x, sci_stream_t stream);
+
+/*
+ * rho == 0: GAP projection x = theta + Phi^T (Phi Phi^T)^+ (y - Phi theta)
+ * (Eq. 21), with Phi Phi^T = diag(R), R = sum_k C_k^2, and R^+ = 0 where R = 0.
+ * rho > 0: ADMM x-update (Eq. 24), x = v + Phi^T ((y - Phi v) / (R + rho)),
+ * v = theta - u.  u may be NULL (treated as 0).  1/(R + rho) is formed in
+ * FP64 and rounded to FP32.  x may alias neither theta nor u.
+ */
+sci_status sci_project(const float* theta, const float* u, const float* y,
+                       const uint32_t* bits, int nx, int ny, int B, float rho, float* x,
+                       sci_stream_t stream);
+
+/* Bytes of scratch sci_tv_prox needs. */
+size_t sci_tv_prox_workspace(int nx, int ny, int B, int tv);
+
+/*
+ * TVdenoise by FGP (Algorithm 1, ATV-FGP box; Eqs. 29-32 for ITV2D / VTV):
+ * inner_iters dual updates from w = p = 0, nu = 1, step 1/(8 lambda), then
+ * theta = x - lambda (D_h^T p_h + D_v^T p_v).  x, theta: float32 [B][nx][ny]
+ * (may not alias).  D_h, D_v are forward differences without wrap-around.
+ */
+sci_status sci_tv_prox(const float* x, int nx, int ny, int B, int tv, float lambda,
+                       int inner_iters, float* theta, void* work, size_t work_bytes,
+                       sci_stream_t stream);
+
+/* Bytes of scratch sci_gap_tv / sci_admm_tv need for these sizes and params. */
+size_t sci_solver_workspace(int nx, int ny, int B, const sci_params* params);
+
+/*
+ * GAP-TV (Eqs. 21-22, Algorithm 1): T outer iterations of
+ *   x = projection of theta onto {Phi x = y};  theta = TVdenoise(x).
+ * theta: in/out float32 [B][nx][ny] (input ignored when params->init = 1).
+ * x_out: float32 [B][nx][ny], receives x^(T) (theta^(0) when T = 0); may be NULL.
+ * resid: optional device double array; when resid_every > 0 it receives
+ *   ||y - Phi theta^(t)||_2^2 (FP64 accumulation) for t = resid_every,
+ *   2*resid_every, ... <= T, at index t/resid_every - 1.
+ */
+sci_status sci_gap_tv(const float* y, const uint32_t* bits, int nx, int ny, int B,
+                      const sci_params* params, float* theta, float* x_out,
+                      double* resid, int resid_every, void* work, size_t work_bytes,
+                      sci_stream_t stream);
+
+/*
+ * ADMM-TV (Eqs. 24-26): T iterations of
+ *   x = ADMM x-update (rho = params->rho);  theta = TVdenoise(u + x);  u = u + x - theta.
+ * TVdenoise uses params->lambda (Eq. 25 carries no rho).  theta, u: in/out
+ * float32 [B][nx][ny] (inputs ignored when params->init = 1: theta = Phi^T y, u = 0).
+ * Other arguments as sci_gap_tv.
+ */
+sci_status sci_admm_tv(const float* y, const uint32_t* bits, int nx, int ny, int B,
+                       const sci_params* params, float* theta, float* u, float* x_out,
+                       double* resid, int resid_every, void* work, size_t work_bytes,
+                       sci_stream_t stream);
+
+/* Release every CUDA graph the solver has cached (call before freeing buffers
+ * whose addresses an earlier solve used, if the same addresses may be reused
+ * with different contents sizes or parameters; safe at any time). */
+void sci_graph_cache_clear(void);
+
+/* Scratch for the FP64 reductions below: at least this many bytes. */
+size_t sci_reduce_workspace(void);
+
+/*
+ * out[0] = sum_i (a[i] - b[i])^2 with FP64 accumulation in a fixed order
+ * (deterministic).  b may be NULL (then sum a[i]^2).  out: device double.
+ * PSNR = 10 log10(peak^2 * n / out[0]) is formed by the caller.
+ */
+sci_status sci_sqdiff_f64(const float* a, const float* b, size_t n, double* out,
+                          void* work, size_t work_bytes, sci_stream_t stream);
+
+/* out[0] = ||y - Phi theta||_2^2 with FP64 accumulation (deterministic). */
+sci_status sci_residual_f64(const float* theta, const float* y, const uint32_t* bits,
+                            int nx, int ny, int B, double* out, void* work,
+                            size_t work_bytes, sci_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCI_H_ */

@@ -1,0 +1,416 @@
+// C-ABI entry points of libsci (declared in include/sci.h): argument
+// validation, workspace layout, the GAP-TV / ADMM-TV outer loop and its
+// CUDA-graph cache.
+//
+// Outer loop (Algorithm 1 for GAP, Eqs. 24-26 for ADMM), with theta (and u)
+// as the only state carried between iterations:
+//   r  = rinv * (y - sum_k c_k (theta_k - u_k))     rinv = 1/R (GAP, pseudo-inverse)
+//                                                    or 1/(R + rho) (ADMM); u = 0 for GAP
+//   xt = theta + c_k r                               GAP: the projection x (Eq. 21)
+//                                                    ADMM: u + x, x from Eq. 24
+//   theta' = FGP prox of xt (S dual updates)
+//   ADMM: u' = u + x - theta' = xt - theta'
+// The projection is folded into the first FGP launch (which forms xt on the
+// fly) and the next residual into the last one, so one outer iteration is
+// S + 1 launches and no separate projection pass.
+#include <cmath>
+#include <cstring>
+#include <list>
+#include <mutex>
+#include <vector>
+
+#include "sci_internal.cuh"
+
+using namespace sci;
+
+namespace {
+
+constexpr int kVersion = 10000;  // 1.0.0
+
+bool finite_pos(float v) { return std::isfinite(v) && v > 0.f; }
+
+// Momentum coefficients (nu_s - 1)/nu_{s+1}, nu_0 = 1, computed in FP64.
+std::vector<float> momentum_coeffs(int S) {
+    std::vector<float> c((size_t)std::max(S, 1));
+    double nu = 1.0;
+    for (int s = 0; s < S; ++s) {
+        const double nx = (1.0 + std::sqrt(1.0 + 4.0 * nu * nu)) / 2.0;
+        c[(size_t)s] = (float)((nu - 1.0) / nx);
+        nu = nx;
+    }
+    return c;
+}
+
+// ---- workspace layout ----
+struct Layout {
+    size_t rinv, r, partials, xt, p[3], theta_s, u_s, total;
+};
+
+Layout solver_layout(int nx, int ny, int B, int storage, bool admm) {
+    Layout L{};
+    const size_t n = (size_t)nx * ny, N = n * (size_t)B, es = dtype_bytes(storage);
+    Geo g{nx, ny, B, (long long)n};
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t at = off; off += align256(bytes); return at; };
+    L.rinv = take(n * 4);
+    L.r = take(n * 4);
+    L.partials = take((size_t)std::max(out_partial_count(g), kReduceParts) * 8);
+    L.xt = take(N * es);
+    for (int b = 0; b < 3; ++b) L.p[b] = take(2 * N * es);
+    L.theta_s = storage != SCI_F32 ? take(N * es) : 0;
+    L.u_s = (storage != SCI_F32 && admm) ? take(N * es) : 0;
+    L.total = off;
+    return L;
+}
+
+Layout prox_layout(int nx, int ny, int B) {
+    Layout L{};
+    const size_t N = (size_t)nx * ny * B;
+    size_t off = 0;
+    for (int b = 0; b < 3; ++b) { L.p[b] = off; off += align256(2 * N * 4); }
+    L.total = off;
+    return L;
+}
+
+bool sizes_ok(int nx, int ny, int B) {
+    if (nx <= 0 || ny <= 0 || B <= 0) return false;
+    const double N = (double)nx * ny * B;
+    return N < 9.0e15;
+}
+
+sci_status validate_params(const sci_params* p, bool admm) {
+    if (p == nullptr) return SCI_ERR_ARG;
+    if (p->tv < SCI_TV_ATV || p->tv > SCI_TV_VTV) return SCI_ERR_ARG;
+    if (!std::isfinite(p->lambda) || !std::isfinite(p->rho)) return SCI_ERR_NONFINITE;
+    if (!(p->lambda > 0.f)) return SCI_ERR_ARG;
+    if (admm && !(p->rho >= 0.f)) return SCI_ERR_ARG;
+    if (p->outer_iters < 0 || p->inner_iters < 1) return SCI_ERR_ARG;
+    if (p->storage < SCI_F32 || p->storage > SCI_F16) return SCI_ERR_ARG;
+    if (p->fuse_k < 0) return SCI_ERR_ARG;
+    return SCI_OK;
+}
+
+sci_status validate_work(void* work, size_t have, size_t need) {
+    if (need == 0) return SCI_OK;
+    if (work == nullptr || have < need) return SCI_ERR_WORKSPACE;
+    if (((uintptr_t)work & 255u) != 0) return SCI_ERR_WORKSPACE;
+    return SCI_OK;
+}
+
+// ---- the outer loop ----
+struct SolveArgs {
+    bool admm;
+    const float* y;
+    const uint32_t* bits;
+    int nx, ny, B;
+    sci_params prm;
+    float* theta;
+    float* u;
+    float* x_out;
+    double* resid;
+    int resid_every;
+    void* work;
+};
+
+template <typename T>
+void enqueue_solve(const SolveArgs& A, cudaStream_t s) {
+    const Geo g{A.nx, A.ny, A.B, (long long)A.nx * A.ny};
+    const long long N = (long long)A.B * g.n;
+    const Layout L = solver_layout(A.nx, A.ny, A.B, A.prm.storage, A.admm);
+    char* w = static_cast<char*>(A.work);
+    float* rinv = reinterpret_cast<float*>(w + L.rinv);
+    float* r = reinterpret_cast<float*>(w + L.r);
+    double* partials = reinterpret_cast<double*>(w + L.partials);
+    T* xt = reinterpret_cast<T*>(w + L.xt);
+    T* P[3] = {reinterpret_cast<T*>(w + L.p[0]), reinterpret_cast<T*>(w + L.p[1]),
+               reinterpret_cast<T*>(w + L.p[2])};
+    const bool f32 = std::is_same<T, float>::value;
+    T* theta = f32 ? reinterpret_cast<T*>(A.theta) : reinterpret_cast<T*>(w + L.theta_s);
+    T* u = nullptr;
+    if (A.admm) u = f32 ? reinterpret_cast<T*>(A.u) : reinterpret_cast<T*>(w + L.u_s);
+
+    launch_rinv(A.bits, g, A.admm ? A.prm.rho : 0.f, rinv, s);
+    if (A.prm.init) {
+        launch_adjoint<T>(A.y, A.bits, g, theta, s);
+        if (A.admm) launch_zero(u, (size_t)N * sizeof(T), s);
+    } else if (!f32) {
+        launch_cast<float, T>(A.theta, theta, N, s);
+        if (A.admm) launch_cast<float, T>(A.u, u, N, s);
+    }
+    const int T_outer = A.prm.outer_iters, S = A.prm.inner_iters;
+    const float lam = A.prm.lambda;
+    if (T_outer > 0) launch_residual_field<T>(theta, u, A.y, A.bits, rinv, g, r, s);
+    const std::vector<float> coef = momentum_coeffs(S);
+    const OuterMode mode = A.admm ? OuterMode::Admm : OuterMode::Gap;
+    const int nparts = out_partial_count(g);
+    for (int t = 0; t < T_outer; ++t) {
+        launch_fgp_first<T>(A.prm.tv, mode, nullptr, theta, r, A.bits, g, lam, xt, P[0], s);
+        int cur = 0, prev = -1;
+        for (int it = 1; it < S; ++it) {
+            const int out = 3 - cur - (prev < 0 ? (cur == 0 ? 1 : 0) : prev);
+            launch_fgp_iter<T>(A.prm.tv, xt, P[cur], prev >= 0 ? P[prev] : nullptr, coef[(size_t)it - 1],
+                               g, lam, P[out], s);
+            prev = cur;
+            cur = out;
+        }
+        const bool last = t == T_outer - 1;
+        const bool metric = A.resid != nullptr && A.resid_every > 0 && ((t + 1) % A.resid_every == 0);
+        OutArgs oa{};
+        oa.mode = mode;
+        oa.y = A.y;
+        oa.bits = A.bits;
+        oa.rinv = rinv;
+        oa.r_next = last ? nullptr : r;
+        oa.x_out = (last && f32) ? A.x_out : nullptr;
+        oa.resid_partials = metric ? partials : nullptr;
+        if (last && !f32 && A.x_out != nullptr) {
+            // x^(T) from xt (GAP) or xt - u (ADMM) before the output overwrites u.
+            if (A.admm) {
+                // x = xt - u_old: stage u_old in FP32 through x_out, then subtract below.
+                launch_cast<T, float>(u, A.x_out, N, s);
+            }
+        }
+        launch_fgp_out<T>(oa, xt, P[cur], g, lam, theta, u, s);
+        if (last && !f32 && A.x_out != nullptr) {
+            // x_out = xt (GAP) or xt - u_old (ADMM, u_old staged above).
+            launch_xt_minus(xt, A.prm.storage, A.x_out, N, A.admm, s);
+        }
+        if (metric) launch_sum_partials(partials, nparts, A.resid + ((t + 1) / A.resid_every - 1), s);
+    }
+    if (!f32) {
+        launch_cast<T, float>(theta, A.theta, N, s);
+        if (A.admm) launch_cast<T, float>(u, A.u, N, s);
+    }
+    if (T_outer == 0 && A.x_out != nullptr)
+        cudaMemcpyAsync(A.x_out, A.theta, (size_t)N * 4, cudaMemcpyDeviceToDevice, s);
+}
+
+void enqueue_solve_any(const SolveArgs& A, cudaStream_t s) {
+    switch (A.prm.storage) {
+        case SCI_BF16: enqueue_solve<__nv_bfloat16>(A, s); break;
+        case SCI_F16: enqueue_solve<__half>(A, s); break;
+        default: enqueue_solve<float>(A, s); break;
+    }
+}
+
+// ---- CUDA graph cache: one instantiated graph per distinct solve call ----
+struct GraphEntry {
+    int device;
+    SolveArgs args;
+    cudaGraphExec_t exec;
+};
+std::mutex g_mu;
+std::list<GraphEntry> g_cache;  // most recent first
+constexpr size_t kMaxGraphs = 16;
+cudaStream_t g_capture_stream[64] = {};
+
+bool same_args(const SolveArgs& a, const SolveArgs& b) {
+    return a.admm == b.admm && a.y == b.y && a.bits == b.bits && a.nx == b.nx && a.ny == b.ny &&
+           a.B == b.B && std::memcmp(&a.prm, &b.prm, sizeof(sci_params)) == 0 && a.theta == b.theta &&
+           a.u == b.u && a.x_out == b.x_out && a.resid == b.resid && a.resid_every == b.resid_every &&
+           a.work == b.work;
+}
+
+sci_status run_solve(const SolveArgs& A, cudaStream_t stream) {
+    if (cudaGetLastError() != cudaSuccess) { /* clear a stale error from earlier calls */ }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) return SCI_ERR_CUDA;
+    if (!A.prm.use_graph || cap != cudaStreamCaptureStatusNone) {
+        enqueue_solve_any(A, stream);
+        return check_launch();
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SCI_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_mu);
+    for (auto it = g_cache.begin(); it != g_cache.end(); ++it) {
+        if (it->device == dev && same_args(it->args, A)) {
+            g_cache.splice(g_cache.begin(), g_cache, it);
+            if (cudaGraphLaunch(g_cache.front().exec, stream) != cudaSuccess) return SCI_ERR_CUDA;
+            return SCI_OK;
+        }
+    }
+    if (g_capture_stream[dev] == nullptr &&
+        cudaStreamCreateWithFlags(&g_capture_stream[dev], cudaStreamNonBlocking) != cudaSuccess)
+        return SCI_ERR_CUDA;
+    cudaStream_t cs = g_capture_stream[dev];
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SCI_ERR_CUDA;
+    enqueue_solve_any(A, cs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t launch_err = cudaGetLastError();
+    if (cudaStreamEndCapture(cs, &graph) != cudaSuccess || launch_err != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return SCI_ERR_CUDA;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return SCI_ERR_CUDA;
+    g_cache.push_front(GraphEntry{dev, A, exec});
+    while (g_cache.size() > kMaxGraphs) {
+        cudaGraphExecDestroy(g_cache.back().exec);
+        g_cache.pop_back();
+    }
+    if (cudaGraphLaunch(exec, stream) != cudaSuccess) return SCI_ERR_CUDA;
+    return SCI_OK;
+}
+
+sci_status solve_common(bool admm, const float* y, const uint32_t* bits, int nx, int ny, int B,
+                        const sci_params* params, float* theta, float* u, float* x_out,
+                        double* resid, int resid_every, void* work, size_t work_bytes,
+                        sci_stream_t stream) {
+    if (y == nullptr || bits == nullptr || theta == nullptr || (admm && u == nullptr)) return SCI_ERR_ARG;
+    if (!sizes_ok(nx, ny, B)) return SCI_ERR_ARG;
+    if (B > 32) return SCI_ERR_SHAPE;
+    sci_status st = validate_params(params, admm);
+    if (st != SCI_OK) return st;
+    if (resid_every < 0 || (resid_every > 0 && resid == nullptr)) return SCI_ERR_ARG;
+    const Layout L = solver_layout(nx, ny, B, params->storage, admm);
+    st = validate_work(work, work_bytes, L.total);
+    if (st != SCI_OK) return st;
+    SolveArgs A{admm, y, bits, nx, ny, B, *params, theta, u, x_out, resid, resid_every, work};
+    return run_solve(A, (cudaStream_t)stream);
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* sci_status_str(sci_status s) {
+    switch (s) {
+        case SCI_OK: return "ok";
+        case SCI_ERR_ARG: return "invalid argument";
+        case SCI_ERR_SHAPE: return "unsupported shape";
+        case SCI_ERR_CUDA: return "CUDA error";
+        case SCI_ERR_NONFINITE: return "non-finite argument";
+        case SCI_ERR_TIMEOUT: return "device wait timed out";
+        case SCI_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    }
+    return "unknown status";
+}
+
+int sci_version(void) { return kVersion; }
+
+sci_status sci_masks_pack(const uint8_t* masks, int nx, int ny, int B, uint32_t* bits, int* bad_count,
+                          sci_stream_t stream) {
+    if (masks == nullptr || bits == nullptr || !sizes_ok(nx, ny, B)) return SCI_ERR_ARG;
+    if (B > 32) return SCI_ERR_SHAPE;
+    launch_pack(masks, Geo{nx, ny, B, (long long)nx * ny}, bits, bad_count, (cudaStream_t)stream);
+    return check_launch();
+}
+
+sci_status sci_forward(const float* x, const uint32_t* bits, int nx, int ny, int B, float* y,
+                       sci_stream_t stream) {
+    if (x == nullptr || bits == nullptr || y == nullptr || !sizes_ok(nx, ny, B)) return SCI_ERR_ARG;
+    if (B > 32) return SCI_ERR_SHAPE;
+    launch_forward(x, bits, Geo{nx, ny, B, (long long)nx * ny}, y, (cudaStream_t)stream);
+    return check_launch();
+}
+
+sci_status sci_adjoint(const float* y, const uint32_t* bits, int nx, int ny, int B, float* x,
+                       sci_stream_t stream) {
+    if (x == nullptr || bits == nullptr || y == nullptr || !sizes_ok(nx, ny, B)) return SCI_ERR_ARG;
+    if (B > 32) return SCI_ERR_SHAPE;
+    launch_adjoint<float>(y, bits, Geo{nx, ny, B, (long long)nx * ny}, x, (cudaStream_t)stream);
+    return check_launch();
+}
+
+sci_status sci_project(const float* theta, const float* u, const float* y, const uint32_t* bits, int nx,
+                       int ny, int B, float rho, float* x, sci_stream_t stream) {
+    if (theta == nullptr || y == nullptr || bits == nullptr || x == nullptr || !sizes_ok(nx, ny, B))
+        return SCI_ERR_ARG;
+    if (B > 32) return SCI_ERR_SHAPE;
+    if (!std::isfinite(rho)) return SCI_ERR_NONFINITE;
+    if (rho < 0.f || x == theta || (u != nullptr && x == u)) return SCI_ERR_ARG;
+    launch_project(theta, u, y, bits, Geo{nx, ny, B, (long long)nx * ny}, rho, x, (cudaStream_t)stream);
+    return check_launch();
+}
+
+size_t sci_tv_prox_workspace(int nx, int ny, int B, int tv) {
+    (void)tv;
+    if (!sizes_ok(nx, ny, B)) return 0;
+    return prox_layout(nx, ny, B).total;
+}
+
+sci_status sci_tv_prox(const float* x, int nx, int ny, int B, int tv, float lambda, int inner_iters,
+                       float* theta, void* work, size_t work_bytes, sci_stream_t stream) {
+    if (x == nullptr || theta == nullptr || x == theta || !sizes_ok(nx, ny, B)) return SCI_ERR_ARG;
+    if (tv < SCI_TV_ATV || tv > SCI_TV_VTV || inner_iters < 1) return SCI_ERR_ARG;
+    if (!std::isfinite(lambda)) return SCI_ERR_NONFINITE;
+    if (!finite_pos(lambda)) return SCI_ERR_ARG;
+    const Layout L = prox_layout(nx, ny, B);
+    sci_status st = validate_work(work, work_bytes, L.total);
+    if (st != SCI_OK) return st;
+    const Geo g{nx, ny, B, (long long)nx * ny};
+    cudaStream_t s = (cudaStream_t)stream;
+    char* w = static_cast<char*>(work);
+    float* P[3] = {reinterpret_cast<float*>(w + L.p[0]), reinterpret_cast<float*>(w + L.p[1]),
+                   reinterpret_cast<float*>(w + L.p[2])};
+    const std::vector<float> coef = momentum_coeffs(inner_iters);
+    launch_fgp_first<float>(tv, OuterMode::Prox, x, nullptr, nullptr, nullptr, g, lambda, nullptr, P[0], s);
+    int cur = 0, prev = -1;
+    for (int it = 1; it < inner_iters; ++it) {
+        const int out = 3 - cur - (prev < 0 ? (cur == 0 ? 1 : 0) : prev);
+        launch_fgp_iter<float>(tv, x, P[cur], prev >= 0 ? P[prev] : nullptr, coef[(size_t)it - 1], g, lambda,
+                               P[out], s);
+        prev = cur;
+        cur = out;
+    }
+    OutArgs oa{};
+    oa.mode = OuterMode::Prox;
+    oa.xin = x;
+    oa.theta_f32 = theta;
+    launch_fgp_out<float>(oa, x, P[cur], g, lambda, nullptr, nullptr, s);
+    return check_launch();
+}
+
+size_t sci_solver_workspace(int nx, int ny, int B, const sci_params* params) {
+    if (params == nullptr || !sizes_ok(nx, ny, B)) return 0;
+    if (params->storage < SCI_F32 || params->storage > SCI_F16) return 0;
+    return solver_layout(nx, ny, B, params->storage, true).total;
+}
+
+sci_status sci_gap_tv(const float* y, const uint32_t* bits, int nx, int ny, int B, const sci_params* params,
+                      float* theta, float* x_out, double* resid, int resid_every, void* work,
+                      size_t work_bytes, sci_stream_t stream) {
+    return solve_common(false, y, bits, nx, ny, B, params, theta, nullptr, x_out, resid, resid_every, work,
+                        work_bytes, stream);
+}
+
+sci_status sci_admm_tv(const float* y, const uint32_t* bits, int nx, int ny, int B, const sci_params* params,
+                       float* theta, float* u, float* x_out, double* resid, int resid_every, void* work,
+                       size_t work_bytes, sci_stream_t stream) {
+    return solve_common(true, y, bits, nx, ny, B, params, theta, u, x_out, resid, resid_every, work,
+                        work_bytes, stream);
+}
+
+void sci_graph_cache_clear(void) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    for (auto& e : g_cache) cudaGraphExecDestroy(e.exec);
+    g_cache.clear();
+}
+
+size_t sci_reduce_workspace(void) { return (size_t)kReduceParts * sizeof(double); }
+
+sci_status sci_sqdiff_f64(const float* a, const float* b, size_t n, double* out, void* work,
+                          size_t work_bytes, sci_stream_t stream) {
+    if (a == nullptr || out == nullptr || n == 0) return SCI_ERR_ARG;
+    sci_status st = validate_work(work, work_bytes, sci_reduce_workspace());
+    if (st != SCI_OK) return st;
+    launch_sqdiff(a, b, (long long)n, static_cast<double*>(work), out, (cudaStream_t)stream);
+    return check_launch();
+}
+
+sci_status sci_residual_f64(const float* theta, const float* y, const uint32_t* bits, int nx, int ny, int B,
+                            double* out, void* work, size_t work_bytes, sci_stream_t stream) {
+    if (theta == nullptr || y == nullptr || bits == nullptr || out == nullptr || !sizes_ok(nx, ny, B))
+        return SCI_ERR_ARG;
+    if (B > 32) return SCI_ERR_SHAPE;
+    sci_status st = validate_work(work, work_bytes, sci_reduce_workspace());
+    if (st != SCI_OK) return st;
+    launch_residual_norm<float>(theta, y, bits, Geo{nx, ny, B, (long long)nx * ny},
+                                static_cast<double*>(work), out, (cudaStream_t)stream);
+    return check_launch();
+}
+
+}  // extern "C"

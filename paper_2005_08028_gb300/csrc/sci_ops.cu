@@ -1,0 +1,258 @@
+// Measurement-model kernels: mask packing, Phi x, Phi^T y, the GAP / ADMM
+// projection, the per-pixel residual field and FP64 reductions.
+//
+// Sec. 1 of the paper: Y = sum_k X_k . C_k + G (Eq. 3), Phi = [D_1..D_B] with
+// diagonal D_k (Eq. 2), so Phi Phi^T = diag(R), R = sum_k C_k^2, and the GAP
+// projection (Eq. 21) and ADMM x-update (Eq. 24) act pixel by pixel.
+//
+// Every kernel here gives one thread one pixel (i, j) and loops over the B
+// frames, so the frame sum of a pixel stays in registers.  A warp covers 32
+// consecutive columns: each frame load is one coalesced 128-byte line.
+#include "sci_internal.cuh"
+
+namespace sci {
+
+__global__ void k_pack(const uint8_t* __restrict__ masks, Geo g, uint32_t* __restrict__ bits,
+                       int* __restrict__ bad) {
+    int i, j;
+    pixel_ij(i, j);
+    if (i >= g.nx || j >= g.ny) return;
+    const long long pix = (long long)i * g.ny + j;
+    uint32_t w = 0;
+    int nbad = 0;
+    for (int k = 0; k < g.B; ++k) {
+        const uint8_t v = masks[k * g.n + pix];
+        if (v != 0) w |= 1u << k;
+        nbad += (v > 1);
+    }
+    bits[pix] = w;
+    if (bad != nullptr && nbad) atomicAdd(bad, nbad);
+}
+
+__global__ void k_forward(const float* __restrict__ x, const uint32_t* __restrict__ bits, Geo g,
+                          float* __restrict__ y) {
+    int i, j;
+    pixel_ij(i, j);
+    if (i >= g.nx || j >= g.ny) return;
+    const long long pix = (long long)i * g.ny + j;
+    const uint32_t w = bits[pix];
+    float acc = 0.f;
+    for (int k = 0; k < g.B; ++k) acc += mask_bit(w, k) * x[k * g.n + pix];
+    y[pix] = acc;
+}
+
+template <typename T>
+__global__ void k_adjoint(const float* __restrict__ y, const uint32_t* __restrict__ bits, Geo g,
+                          T* __restrict__ x) {
+    int i, j;
+    pixel_ij(i, j);
+    if (i >= g.nx || j >= g.ny) return;
+    const long long pix = (long long)i * g.ny + j;
+    const uint32_t w = bits[pix];
+    const float yv = y[pix];
+    for (int k = 0; k < g.B; ++k) st<T>(x, k * g.n + pix, mask_bit(w, k) * yv);
+}
+
+// 1/(R + rho) in FP64, rounded to FP32; 0 where R + rho == 0 (pseudo-inverse).
+__global__ void k_rinv(const uint32_t* __restrict__ bits, Geo g, float rho, float* __restrict__ rinv) {
+    const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= g.n) return;
+    const uint32_t mask = g.B >= 32 ? 0xffffffffu : ((1u << g.B) - 1u);
+    const double R = (double)__popc(bits[pix] & mask) + (double)rho;
+    rinv[pix] = R == 0.0 ? 0.f : (float)(1.0 / R);
+}
+
+// r = rinv * (y - sum_k c_k (theta_k - u_k)); u may be null.
+template <typename T>
+__global__ void k_residual_field(const T* __restrict__ theta, const T* __restrict__ u,
+                                 const float* __restrict__ y, const uint32_t* __restrict__ bits,
+                                 const float* __restrict__ rinv, Geo g, float* __restrict__ r) {
+    int i, j;
+    pixel_ij(i, j);
+    if (i >= g.nx || j >= g.ny) return;
+    const long long pix = (long long)i * g.ny + j;
+    const uint32_t w = bits[pix];
+    float acc = 0.f;
+    for (int k = 0; k < g.B; ++k) {
+        float v = ld<T>(theta, k * g.n + pix);
+        if (u != nullptr) v -= ld<T>(u, k * g.n + pix);
+        acc += mask_bit(w, k) * v;
+    }
+    r[pix] = rinv[pix] * (y[pix] - acc);
+}
+
+// x = v + c_k * (y - sum_k c_k v_k) / (R + rho), v = theta - u.
+__global__ void k_project(const float* __restrict__ theta, const float* __restrict__ u,
+                          const float* __restrict__ y, const uint32_t* __restrict__ bits, Geo g,
+                          float rho, float* __restrict__ x) {
+    int i, j;
+    pixel_ij(i, j);
+    if (i >= g.nx || j >= g.ny) return;
+    const long long pix = (long long)i * g.ny + j;
+    const uint32_t w = bits[pix];
+    float acc = 0.f;
+    for (int k = 0; k < g.B; ++k) {
+        float v = theta[k * g.n + pix];
+        if (u != nullptr) v -= u[k * g.n + pix];
+        acc += mask_bit(w, k) * v;
+    }
+    const uint32_t mask = g.B >= 32 ? 0xffffffffu : ((1u << g.B) - 1u);
+    const double R = (double)__popc(w & mask) + (double)rho;
+    const float rinv = R == 0.0 ? 0.f : (float)(1.0 / R);
+    const float rr = rinv * (y[pix] - acc);
+    for (int k = 0; k < g.B; ++k) {
+        float v = theta[k * g.n + pix];
+        if (u != nullptr) v -= u[k * g.n + pix];
+        x[k * g.n + pix] = v + mask_bit(w, k) * rr;
+    }
+}
+
+template <typename Tin, typename Tout>
+__global__ void k_cast(const Tin* __restrict__ in, Tout* __restrict__ out, long long count) {
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < count;
+         idx += (long long)gridDim.x * blockDim.x)
+        st<Tout>(out, idx, ld<Tin>(in, idx));
+}
+
+// ---- FP64 reductions (fixed order: per-thread strided sums, warp shuffle,
+// per-block tree, then one block sums the partials in index order) ----
+__global__ void k_sqdiff_partial(const float* __restrict__ a, const float* __restrict__ b,
+                                 long long n, double* __restrict__ partials) {
+    double acc = 0.0;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const double d = (double)a[idx] - (b != nullptr ? (double)b[idx] : 0.0);
+        acc += d * d;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+template <typename T>
+__global__ void k_resid_partial(const T* __restrict__ theta, const float* __restrict__ y,
+                                const uint32_t* __restrict__ bits, Geo g,
+                                double* __restrict__ partials) {
+    double acc = 0.0;
+    for (long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x; pix < g.n;
+         pix += (long long)gridDim.x * blockDim.x) {
+        const uint32_t w = bits[pix];
+        float s = 0.f;
+        for (int k = 0; k < g.B; ++k) s += mask_bit(w, k) * ld<T>(theta, k * g.n + pix);
+        const double d = (double)y[pix] - (double)s;
+        acc += d * d;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partials, int count, double* __restrict__ out) {
+    double acc = 0.0;
+    for (int idx = threadIdx.x; idx < count; idx += blockDim.x) acc += partials[idx];
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) out[0] = acc;
+}
+
+// x_out = xt (GAP) or xt - x_out (ADMM: x_out holds u_old in FP32), for 16-bit storage.
+template <typename T>
+__global__ void k_xt_minus(const T* __restrict__ xt, float* __restrict__ x, long long N, bool sub) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float v = ld<T>(xt, i);
+        x[i] = sub ? v - x[i] : v;
+    }
+}
+void launch_xt_minus(const void* xt, int storage, float* x, long long N, bool sub, cudaStream_t s) {
+    const int blocks = 152 * 8;
+    if (storage == SCI_BF16)
+        k_xt_minus<__nv_bfloat16><<<blocks, 256, 0, s>>>((const __nv_bfloat16*)xt, x, N, sub);
+    else if (storage == SCI_F16)
+        k_xt_minus<__half><<<blocks, 256, 0, s>>>((const __half*)xt, x, N, sub);
+    else
+        k_xt_minus<float><<<blocks, 256, 0, s>>>((const float*)xt, x, N, sub);
+}
+
+// ---------------------------------------------------------------- launchers
+
+void launch_pack(const uint8_t* masks, Geo g, uint32_t* bits, int* bad, cudaStream_t s) {
+    k_pack<<<pixel_grid(g.nx, g.ny), pixel_block(), 0, s>>>(masks, g, bits, bad);
+}
+
+void launch_forward(const float* x, const uint32_t* bits, Geo g, float* y, cudaStream_t s) {
+    k_forward<<<pixel_grid(g.nx, g.ny), pixel_block(), 0, s>>>(x, bits, g, y);
+}
+
+template <typename T>
+void launch_adjoint(const float* y, const uint32_t* bits, Geo g, T* x, cudaStream_t s) {
+    k_adjoint<T><<<pixel_grid(g.nx, g.ny), pixel_block(), 0, s>>>(y, bits, g, x);
+}
+
+void launch_rinv(const uint32_t* bits, Geo g, float rho, float* rinv, cudaStream_t s) {
+    const int threads = 256;
+    const long long blocks = (g.n + threads - 1) / threads;
+    k_rinv<<<(unsigned)blocks, threads, 0, s>>>(bits, g, rho, rinv);
+}
+
+template <typename T>
+void launch_residual_field(const T* theta, const T* u, const float* y, const uint32_t* bits,
+                           const float* rinv, Geo g, float* r, cudaStream_t s) {
+    k_residual_field<T><<<pixel_grid(g.nx, g.ny), pixel_block(), 0, s>>>(theta, u, y, bits, rinv, g, r);
+}
+
+void launch_project(const float* theta, const float* u, const float* y, const uint32_t* bits,
+                    Geo g, float rho, float* x, cudaStream_t s) {
+    k_project<<<pixel_grid(g.nx, g.ny), pixel_block(), 0, s>>>(theta, u, y, bits, g, rho, x);
+}
+
+template <typename Tin, typename Tout>
+void launch_cast(const Tin* in, Tout* out, long long count, cudaStream_t s) {
+    const int threads = 256;
+    long long blocks = (count + threads - 1) / threads;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_cast<Tin, Tout><<<(unsigned)blocks, threads, 0, s>>>(in, out, count);
+}
+
+void launch_zero(void* p, size_t bytes, cudaStream_t s) { cudaMemsetAsync(p, 0, bytes, s); }
+
+static int reduce_blocks(long long n) {
+    long long b = (n + 255) / 256;
+    if (b > kReduceParts) b = kReduceParts;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+void launch_sqdiff(const float* a, const float* b, long long n, double* partials, double* out,
+                   cudaStream_t s) {
+    const int blocks = reduce_blocks(n);
+    k_sqdiff_partial<<<blocks, 256, 0, s>>>(a, b, n, partials);
+    k_sum_partials<<<1, 1024, 0, s>>>(partials, blocks, out);
+}
+
+template <typename T>
+void launch_residual_norm(const T* theta, const float* y, const uint32_t* bits, Geo g,
+                          double* partials, double* out, cudaStream_t s) {
+    const int blocks = reduce_blocks(g.n);
+    k_resid_partial<T><<<blocks, 256, 0, s>>>(theta, y, bits, g, partials);
+    k_sum_partials<<<1, 1024, 0, s>>>(partials, blocks, out);
+}
+
+void launch_sum_partials(const double* partials, int count, double* out, cudaStream_t s) {
+    k_sum_partials<<<1, 1024, 0, s>>>(partials, count, out);
+}
+
+#define SCI_INST(T)                                                                           \
+    template void launch_adjoint<T>(const float*, const uint32_t*, Geo, T*, cudaStream_t);    \
+    template void launch_residual_field<T>(const T*, const T*, const float*, const uint32_t*, \
+                                           const float*, Geo, float*, cudaStream_t);          \
+    template void launch_residual_norm<T>(const T*, const float*, const uint32_t*, Geo,       \
+                                          double*, double*, cudaStream_t);
+SCI_INST(float)
+SCI_INST(__nv_bfloat16)
+SCI_INST(__half)
+#undef SCI_INST
+template void launch_cast<float, __nv_bfloat16>(const float*, __nv_bfloat16*, long long, cudaStream_t);
+template void launch_cast<__nv_bfloat16, float>(const __nv_bfloat16*, float*, long long, cudaStream_t);
+template void launch_cast<float, __half>(const float*, __half*, long long, cudaStream_t);
+template void launch_cast<__half, float>(const __half*, float*, long long, cudaStream_t);
+
+}  // namespace sci

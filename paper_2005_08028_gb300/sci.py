@@ -1,0 +1,260 @@
+"""Thin ctypes binding of libsci (include/sci.h) with torch tensors as buffers.
+
+Argument marshalling only: every step of the reconstruction runs in the CUDA
+kernels of libsci.so.  torch supplies device memory and the current stream.
+If the library cannot be loaded, every call raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+__all__ = [
+    "SciError", "TV", "DTYPE", "load", "sci_masks_pack", "sci_forward", "sci_adjoint",
+    "sci_project", "sci_tv_prox", "sci_gap_tv", "sci_admm_tv", "sci_sqdiff_f64",
+    "sci_residual_f64", "sci_graph_cache_clear", "Workspace", "SciParams",
+]
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsci.so")
+_lib = None
+_lock = threading.Lock()
+
+TV = {"atv": 0, "itv2d": 1, "vtv": 2}
+DTYPE = {"f32": 0, "bf16": 1, "f16": 2}
+_STATUS = {0: "SCI_OK", 1: "SCI_ERR_ARG", 2: "SCI_ERR_SHAPE", 3: "SCI_ERR_CUDA",
+           4: "SCI_ERR_NONFINITE", 5: "SCI_ERR_TIMEOUT", 6: "SCI_ERR_WORKSPACE"}
+
+
+class SciError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        super().__init__(f"{fn} failed: {_STATUS.get(status, status)}")
+        self.status = status
+
+
+class SciParams(C.Structure):
+    _fields_ = [("tv", C.c_int), ("lam", C.c_float), ("rho", C.c_float),
+                ("outer_iters", C.c_int), ("inner_iters", C.c_int), ("storage", C.c_int),
+                ("fuse_k", C.c_int), ("init", C.c_int), ("use_graph", C.c_int)]
+
+
+_vp, _i, _f, _sz = C.c_void_p, C.c_int, C.c_float, C.c_size_t
+_SIGS = {
+    "sci_status_str": (C.c_char_p, [_i]),
+    "sci_version": (_i, []),
+    "sci_masks_pack": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp]),
+    "sci_forward": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp]),
+    "sci_adjoint": (_i, [_vp, _vp, _i, _i, _i, _vp, _vp]),
+    "sci_project": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _f, _vp, _vp]),
+    "sci_tv_prox_workspace": (_sz, [_i, _i, _i, _i]),
+    "sci_tv_prox": (_i, [_vp, _i, _i, _i, _i, _f, _i, _vp, _vp, _sz, _vp]),
+    "sci_solver_workspace": (_sz, [_i, _i, _i, C.POINTER(SciParams)]),
+    "sci_gap_tv": (_i, [_vp, _vp, _i, _i, _i, C.POINTER(SciParams), _vp, _vp, _vp, _i, _vp, _sz, _vp]),
+    "sci_admm_tv": (_i, [_vp, _vp, _i, _i, _i, C.POINTER(SciParams), _vp, _vp, _vp, _vp, _i, _vp, _sz,
+                         _vp]),
+    "sci_graph_cache_clear": (None, []),
+    "sci_reduce_workspace": (_sz, []),
+    "sci_sqdiff_f64": (_i, [_vp, _vp, _sz, _vp, _vp, _sz, _vp]),
+    "sci_residual_f64": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp, _vp, _sz, _vp]),
+}
+
+
+def load(path: str | None = None):
+    """Load libsci.so (once) and declare the C signatures."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or _LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(
+                    f"libsci.so not found at {p}: build it with "
+                    "`python -c 'import __graft_entry__ as g; g.build()'`")
+            lib = C.CDLL(p)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(fn: str, status: int):
+    if status != 0:
+        raise SciError(fn, status)
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(device: torch.device):
+    return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is not None:
+            if not t.is_cuda:
+                raise ValueError("libsci works on CUDA tensors only")
+            if not t.is_contiguous():
+                raise ValueError("tensors must be contiguous")
+
+
+class Workspace:
+    """A growable device scratch buffer (torch-allocated, 512-byte aligned)."""
+
+    def __init__(self, device="cuda"):
+        self.device = torch.device(device)
+        self.buf = None
+
+    def get(self, nbytes: int) -> torch.Tensor:
+        nbytes = max(int(nbytes), 256)
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        return self.buf
+
+
+# ---------------------------------------------------------------- measurement model
+
+def sci_masks_pack(masks: torch.Tensor, check: bool = True) -> torch.Tensor:
+    """Dense binary masks uint8 [B][nx][ny] -> packed int32 [nx][ny] (bit k = mask k)."""
+    _need_cuda(masks)
+    if masks.dtype != torch.uint8 or masks.dim() != 3:
+        raise ValueError("masks must be uint8 [B][nx][ny]")
+    B, nx, ny = masks.shape
+    bits = torch.empty((nx, ny), dtype=torch.int32, device=masks.device)
+    bad = torch.zeros(1, dtype=torch.int32, device=masks.device) if check else None
+    _check("sci_masks_pack", load().sci_masks_pack(_ptr(masks), nx, ny, B, _ptr(bits), _ptr(bad),
+                                                   _stream(masks.device)))
+    if check and int(bad.item()) != 0:
+        raise ValueError(f"masks must be binary: {int(bad.item())} entries are neither 0 nor 1")
+    return bits
+
+
+def sci_forward(x: torch.Tensor, bits: torch.Tensor) -> torch.Tensor:
+    """y = Phi x = sum_k C_k . X_k (Eq. 3)."""
+    _need_cuda(x, bits)
+    B, nx, ny = x.shape
+    y = torch.empty((nx, ny), dtype=torch.float32, device=x.device)
+    _check("sci_forward", load().sci_forward(_ptr(x), _ptr(bits), nx, ny, B, _ptr(y), _stream(x.device)))
+    return y
+
+
+def sci_adjoint(y: torch.Tensor, bits: torch.Tensor, B: int) -> torch.Tensor:
+    """x = Phi^T y, frame k = C_k . Y (Eq. 2)."""
+    _need_cuda(y, bits)
+    nx, ny = y.shape
+    x = torch.empty((B, nx, ny), dtype=torch.float32, device=y.device)
+    _check("sci_adjoint", load().sci_adjoint(_ptr(y), _ptr(bits), nx, ny, B, _ptr(x), _stream(y.device)))
+    return x
+
+
+def sci_project(theta: torch.Tensor, y: torch.Tensor, bits: torch.Tensor, rho: float = 0.0,
+                u: torch.Tensor | None = None) -> torch.Tensor:
+    """GAP projection (rho = 0, Eq. 21) or ADMM x-update (rho > 0, Eq. 24)."""
+    _need_cuda(theta, y, bits, u)
+    B, nx, ny = theta.shape
+    x = torch.empty_like(theta)
+    _check("sci_project", load().sci_project(_ptr(theta), _ptr(u), _ptr(y), _ptr(bits), nx, ny, B,
+                                             float(rho), _ptr(x), _stream(theta.device)))
+    return x
+
+
+def sci_tv_prox(x: torch.Tensor, tv: str, lam: float, inner_iters: int,
+                work: Workspace | None = None) -> torch.Tensor:
+    """FGP TV proximal map with `inner_iters` dual updates (Algorithm 1, FGP box)."""
+    _need_cuda(x)
+    B, nx, ny = x.shape
+    lib = load()
+    need = lib.sci_tv_prox_workspace(nx, ny, B, TV[tv])
+    wbuf = (work or Workspace(x.device)).get(need)
+    theta = torch.empty_like(x)
+    _check("sci_tv_prox", lib.sci_tv_prox(_ptr(x), nx, ny, B, TV[tv], float(lam), int(inner_iters),
+                                          _ptr(theta), _ptr(wbuf), wbuf.numel(), _stream(x.device)))
+    return theta
+
+
+def _params(tv, lam, rho, outer, inner, storage, fuse_k, init, use_graph):
+    return SciParams(TV[tv], float(lam), float(rho), int(outer), int(inner), DTYPE[storage],
+                     int(fuse_k), int(init), int(use_graph))
+
+
+def _solve(admm: bool, y, bits, B, tv, lam, outer, inner, rho=0.0, storage="f32", theta=None, u=None,
+           init=None, x_out=None, resid=None, resid_every=0, fuse_k=0, use_graph=True, work=None):
+    _need_cuda(y, bits, theta, u, x_out, resid)
+    nx, ny = y.shape
+    dev = y.device
+    if init is None:
+        init = theta is None
+    if theta is None:
+        theta = torch.empty((B, nx, ny), dtype=torch.float32, device=dev)
+    if admm and u is None:
+        if not init:
+            raise ValueError("resuming ADMM needs u")
+        u = torch.empty((B, nx, ny), dtype=torch.float32, device=dev)
+    if x_out is None:
+        x_out = torch.empty((B, nx, ny), dtype=torch.float32, device=dev)
+    prm = _params(tv, lam, rho, outer, inner, storage, fuse_k, init, use_graph)
+    lib = load()
+    need = lib.sci_solver_workspace(nx, ny, B, C.byref(prm))
+    wbuf = (work or Workspace(dev)).get(need)
+    if resid_every and resid is None:
+        resid = torch.zeros(max(1, outer // resid_every), dtype=torch.float64, device=dev)
+    if admm:
+        st = lib.sci_admm_tv(_ptr(y), _ptr(bits), nx, ny, B, C.byref(prm), _ptr(theta), _ptr(u),
+                             _ptr(x_out), _ptr(resid), int(resid_every), _ptr(wbuf), wbuf.numel(),
+                             _stream(dev))
+        _check("sci_admm_tv", st)
+        return x_out, theta, u, resid
+    st = lib.sci_gap_tv(_ptr(y), _ptr(bits), nx, ny, B, C.byref(prm), _ptr(theta), _ptr(x_out),
+                        _ptr(resid), int(resid_every), _ptr(wbuf), wbuf.numel(), _stream(dev))
+    _check("sci_gap_tv", st)
+    return x_out, theta, resid
+
+
+def sci_gap_tv(y, bits, B, tv, lam, outer, inner, **kw):
+    """GAP-TV (Algorithm 1).  Returns (x^(T), theta^(T), resid-or-None).
+
+    Keyword arguments: storage ('f32'|'bf16'|'f16'); theta (state buffer,
+    updated in place: resumed from unless init=True; default a new buffer
+    started at Phi^T y); init; x_out; resid; resid_every; fuse_k; use_graph;
+    work (a Workspace reused across calls).  Reusing the same buffers lets
+    the library replay its cached CUDA graph.
+    """
+    return _solve(False, y, bits, B, tv, lam, outer, inner, **kw)
+
+
+def sci_admm_tv(y, bits, B, tv, lam, rho, outer, inner, **kw):
+    """ADMM-TV (Eqs. 24-26).  Returns (x^(T), theta^(T), u^(T), resid-or-None)."""
+    return _solve(True, y, bits, B, tv, lam, outer, inner, rho=rho, **kw)
+
+
+def sci_graph_cache_clear():
+    load().sci_graph_cache_clear()
+
+
+def sci_sqdiff_f64(a: torch.Tensor, b: torch.Tensor | None = None,
+                   work: Workspace | None = None) -> torch.Tensor:
+    """sum (a - b)^2 (or sum a^2) with FP64 accumulation; a 1-element device double tensor."""
+    _need_cuda(a, b)
+    lib = load()
+    out = torch.empty(1, dtype=torch.float64, device=a.device)
+    wbuf = (work or Workspace(a.device)).get(lib.sci_reduce_workspace())
+    _check("sci_sqdiff_f64", lib.sci_sqdiff_f64(_ptr(a), _ptr(b), a.numel(), _ptr(out), _ptr(wbuf),
+                                                wbuf.numel(), _stream(a.device)))
+    return out
+
+
+def sci_residual_f64(theta: torch.Tensor, y: torch.Tensor, bits: torch.Tensor,
+                     work: Workspace | None = None) -> torch.Tensor:
+    """||y - Phi theta||^2 with FP64 accumulation; a 1-element device double tensor."""
+    _need_cuda(theta, y, bits)
+    B, nx, ny = theta.shape
+    lib = load()
+    out = torch.empty(1, dtype=torch.float64, device=theta.device)
+    wbuf = (work or Workspace(theta.device)).get(lib.sci_reduce_workspace())
+    _check("sci_residual_f64", lib.sci_residual_f64(_ptr(theta), _ptr(y), _ptr(bits), nx, ny, B, _ptr(out),
+                                                    _ptr(wbuf), wbuf.numel(), _stream(theta.device)))
+    return out

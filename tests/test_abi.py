@@ -1,0 +1,93 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every symbol that
+include/sci.h declares, and rejects bad arguments before touching the GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sci.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sci_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2005_08028_gb300 import build as b
+    path = b.build()
+    import paper_2005_08028_gb300.sci as s
+    return s.load(path)
+
+
+def test_header_declares_expected_calls():
+    names = declared_functions()
+    for must in ("sci_forward", "sci_adjoint", "sci_project", "sci_tv_prox", "sci_gap_tv",
+                 "sci_admm_tv", "sci_masks_pack"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_and_version(lib):
+    assert lib.sci_version() >= 10000
+    for code in range(7):
+        assert lib.sci_status_str(code)
+
+
+def test_argument_errors_return_before_any_launch(lib):
+    from paper_2005_08028_gb300.sci import SciParams
+    fake = C.c_void_p(0x10000)  # never dereferenced: validation fails first
+    prm = SciParams(0, 0.05, 0.0, 10, 5, 0, 0, 1, 1)
+    # null y
+    assert lib.sci_gap_tv(None, fake, 8, 8, 2, C.byref(prm), fake, fake, None, 0, fake, 1 << 30, None) == 1
+    # B > 32
+    assert lib.sci_gap_tv(fake, fake, 8, 8, 33, C.byref(prm), fake, fake, None, 0, fake, 1 << 30, None) == 2
+    # non-positive sizes
+    assert lib.sci_forward(fake, fake, 0, 8, 2, fake, None) == 1
+    # lambda <= 0 and non-finite lambda
+    bad = SciParams(0, -1.0, 0.0, 10, 5, 0, 0, 1, 1)
+    assert lib.sci_gap_tv(fake, fake, 8, 8, 2, C.byref(bad), fake, fake, None, 0, fake, 1 << 30, None) == 1
+    nan = SciParams(0, float("nan"), 0.0, 10, 5, 0, 0, 1, 1)
+    assert lib.sci_gap_tv(fake, fake, 8, 8, 2, C.byref(nan), fake, fake, None, 0, fake, 1 << 30, None) == 4
+    # S = 0, bad TV type, negative rho for ADMM
+    s0 = SciParams(0, 0.05, 0.0, 10, 0, 0, 0, 1, 1)
+    assert lib.sci_gap_tv(fake, fake, 8, 8, 2, C.byref(s0), fake, fake, None, 0, fake, 1 << 30, None) == 1
+    tv9 = SciParams(9, 0.05, 0.0, 10, 5, 0, 0, 1, 1)
+    assert lib.sci_gap_tv(fake, fake, 8, 8, 2, C.byref(tv9), fake, fake, None, 0, fake, 1 << 30, None) == 1
+    neg = SciParams(0, 0.05, -0.5, 10, 5, 0, 0, 1, 1)
+    assert lib.sci_admm_tv(fake, fake, 8, 8, 2, C.byref(neg), fake, fake, fake, None, 0, fake, 1 << 30,
+                           None) == 1
+    # workspace too small / misaligned
+    need = lib.sci_solver_workspace(8, 8, 2, C.byref(prm))
+    assert need > 0
+    assert lib.sci_gap_tv(fake, fake, 8, 8, 2, C.byref(prm), fake, fake, None, 0, fake, need - 1, None) == 6
+    assert lib.sci_gap_tv(fake, fake, 8, 8, 2, C.byref(prm), fake, fake, None, 0, C.c_void_p(0x10010),
+                          need, None) == 6
+    # resid_every without a buffer
+    assert lib.sci_gap_tv(fake, fake, 8, 8, 2, C.byref(prm), fake, fake, None, 3, fake, need, None) == 1
+    # prox: aliasing and bad inner_iters
+    assert lib.sci_tv_prox(fake, 8, 8, 2, 0, 0.05, 5, fake, fake, 1 << 30, None) == 1
+    assert lib.sci_tv_prox(fake, 8, 8, 2, 0, 0.05, 0, C.c_void_p(0x20000), fake, 1 << 30, None) == 1
+    # projection: negative rho, x aliasing theta
+    assert lib.sci_project(fake, None, fake, fake, 8, 8, 2, -1.0, C.c_void_p(0x20000), None) == 1
+    assert lib.sci_project(fake, None, fake, fake, 8, 8, 2, 0.0, fake, None) == 1
+
+
+def test_workspace_sizes_scale(lib):
+    from paper_2005_08028_gb300.sci import SciParams
+    p32 = SciParams(0, 0.05, 0.01, 10, 5, 0, 0, 1, 1)
+    p16 = SciParams(0, 0.05, 0.01, 10, 5, 1, 0, 1, 1)
+    a = lib.sci_solver_workspace(512, 512, 10, C.byref(p32))
+    b = lib.sci_solver_workspace(512, 512, 10, C.byref(p16))
+    N = 512 * 512 * 10
+    assert a >= 7 * N * 4  # xt + three 2-field dual buffers
+    assert b >= 9 * N * 2  # plus theta and u copies in 16-bit
+    assert lib.sci_tv_prox_workspace(64, 64, 4, 0) >= 6 * 64 * 64 * 4 * 4
