@@ -167,6 +167,40 @@ sci_status sci_residual_f64(const float* theta, const float* y, const uint32_t* 
                             int nx, int ny, int B, double* out, void* work,
                             size_t work_bytes, sci_stream_t stream);
 
+/*
+ * sci_tv_prox_noalloc -- the same FGP TV prox as sci_tv_prox, for callers
+ * that cannot hand the library any device memory for scratch.  (The paper
+ * has no counterpart: this is an interface convenience of this library.)
+ *
+ * Who needs it: code that must not call cudaMalloc or any allocator at the
+ * point of use -- a plugin living inside a host framework that owns all
+ * device memory, a latency-critical streaming loop where cudaFree's implicit
+ * device synchronisation is unacceptable, or a fixed-budget embedded pipeline
+ * that reserves all memory up front.  Such callers still pass x and theta.
+ *
+ * Scratch: a fixed array of 48 MiB compiled into libsci (three rotating FP32
+ * dual buffers, 24 bytes per voxel), so B*nx*ny may be at most
+ * sci_tv_prox_noalloc_max_voxels() = 2,097,152 (e.g. 512 x 512 x 8); larger
+ * sizes return SCI_ERR_SHAPE before anything is enqueued.  Every GPU that
+ * loads the library keeps this array until the process exits.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  The call allocates nothing: no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *
+ * All calls share the one array and it keeps the last call's contents; the
+ * first dual update overwrites every entry it later reads, so nothing needs
+ * clearing.  Calls whose execution overlaps on the GPU (different streams, or
+ * different host threads without ordering) race on the array: serialise them.
+ * Other arguments, layout and results are exactly those of sci_tv_prox.
+ */
+sci_status sci_tv_prox_noalloc(const float* x, int nx, int ny, int B, int tv, float lambda,
+                               int inner_iters, float* theta, sci_stream_t stream);
+
+/* Largest B*nx*ny that sci_tv_prox_noalloc accepts. */
+long long sci_tv_prox_noalloc_max_voxels(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,7 +15,7 @@ import torch
 __all__ = [
     "SciError", "TV", "DTYPE", "load", "sci_masks_pack", "sci_forward", "sci_adjoint",
     "sci_project", "sci_tv_prox", "sci_gap_tv", "sci_admm_tv", "sci_sqdiff_f64",
-    "sci_residual_f64", "sci_graph_cache_clear", "Workspace", "SciParams",
+    "sci_residual_f64", "sci_graph_cache_clear", "sci_tv_prox_noalloc", "Workspace", "SciParams",
 ]
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsci.so")
@@ -58,6 +58,8 @@ _SIGS = {
     "sci_reduce_workspace": (_sz, []),
     "sci_sqdiff_f64": (_i, [_vp, _vp, _sz, _vp, _vp, _sz, _vp]),
     "sci_residual_f64": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp, _vp, _sz, _vp]),
+    "sci_tv_prox_noalloc": (_i, [_vp, _i, _i, _i, _i, _f, _i, _vp, _vp]),
+    "sci_tv_prox_noalloc_max_voxels": (C.c_longlong, []),
 }
 
 
@@ -173,6 +175,22 @@ def sci_tv_prox(x: torch.Tensor, tv: str, lam: float, inner_iters: int,
     theta = torch.empty_like(x)
     _check("sci_tv_prox", lib.sci_tv_prox(_ptr(x), nx, ny, B, TV[tv], float(lam), int(inner_iters),
                                           _ptr(theta), _ptr(wbuf), wbuf.numel(), _stream(x.device)))
+    return theta
+
+
+def sci_tv_prox_noalloc(x: torch.Tensor, tv: str, lam: float, inner_iters: int) -> torch.Tensor:
+    """sci_tv_prox with the library's fixed internal scratch (no workspace).
+
+    For callers that cannot allocate device memory; B*nx*ny is limited to
+    sci_tv_prox_noalloc_max_voxels().  Concurrent calls on different streams
+    race on the shared scratch.
+    """
+    _need_cuda(x)
+    B, nx, ny = x.shape
+    theta = torch.empty_like(x)
+    _check("sci_tv_prox_noalloc", load().sci_tv_prox_noalloc(_ptr(x), nx, ny, B, TV[tv], float(lam),
+                                                             int(inner_iters), _ptr(theta),
+                                                             _stream(x.device)))
     return theta
 
 
