@@ -151,12 +151,6 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def launches_per_solve(c, admm):
-    # rinv + adjoint + residual field, then per outer iteration: one first
-    # FGP launch, S-1 FGP updates and one output launch.
-    return 3 + c["outer"] * (c["inner"] + 1)
-
-
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -192,8 +186,11 @@ def run_gpu(args):
                          work=pkg.Workspace(dev)))
 
     def solve_all(yy, bb):
+        n = 0
         for bf in bufs:
             _solve(pkg, bf, yy, bb)
+            n += pkg.sci_last_solve_launches()
+        return n
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -208,11 +205,12 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
+    launches = 0
     with Clocks(local) as clk:
         for k in range(args.steps):
             flush.zero_()
             evs[k][0].record(stream)
-            solve_all(y, bits)
+            launches += solve_all(y, bits)
             evs[k][1].record(stream)
         torch.cuda.synchronize(dev)
     if world > 1:
@@ -243,7 +241,6 @@ def run_gpu(args):
     # ---- end to end: host buffers through the public API ----
     e2e = _e2e(pkg, torch, dev, stream, args, c, masks_h, y, bufs, flush)
 
-    launches = args.steps * sum(launches_per_solve(c, a == "admm") for a, _ in COMBOS)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
@@ -295,37 +292,50 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+ALU_OPS_PER_UPDATE = 20  # FP32 operations per voxel per FGP dual update (FMA = 1)
+
+
+def _alu_peak():
+    """FP32 lane-operations per second: 152 SMs x 128 FP32 lanes x the max SM clock."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    mhz = 2070.0
+    if os.path.exists(path):
+        mhz = float(json.load(open(path)).get("sm_max_mhz", mhz))
+    return 152 * 128 * mhz * 1e6
+
+
 def _roofline(pkg, torch, dev, stream, c, B, nx, ny):
-    """Average duration of one FGP dual-update launch, from sci_tv_prox timed
-    with S = 1 and S = 1 + M: the difference is M update launches."""
+    """The dominant kernel, the temporally blocked FGP launch (k_fgp_fused):
+    sci_tv_prox with S equal to the solver's updates per launch is exactly one
+    such launch; it is timed with CUDA events for each TV form."""
     N = B * nx * ny
-    M = 20
     x = torch.rand((B, nx, ny), device=dev)
     work = pkg.Workspace(dev)
-    per_tv = {}
+    per_tv, ops, ms_total = {}, 0.0, 0.0
     for tv in ("atv", "itv2d", "vtv"):
-        for _ in range(2):
-            pkg.sci_tv_prox(x, tv, c["lam"], 1 + M, work=work)
-        ts = {}
-        for S in (1, 1 + M):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            reps = 10
-            e0.record(stream)
-            for _ in range(reps):
-                pkg.sci_tv_prox(x, tv, c["lam"], S, work=work)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            ts[S] = e0.elapsed_time(e1) / reps
-        per_tv[tv] = max(ts[1 + M] - ts[1], 1e-6) / M  # ms per update launch
-    ms = statistics.mean(per_tv.values())
-    alg_bytes = 28.0 * N  # read xt, p (2), q (2); write p' (2): 7 FP32 fields per voxel
-    achieved = alg_bytes / (ms * 1e-3) / 1e9
-    peak, kind = _peaks()
-    return {"kernel": "k_fgp_iter (one FGP dual update)", "bound": "hbm", "achieved": round(achieved, 1),
-            "peak": peak, "peak_kind": f"{kind} hbm_gbs", "unit": "GB/s", "frac": round(achieved / peak, 4),
-            "traffic": None, "alg_bytes_per_launch": alg_bytes,
-            "launch_ms": {k: round(v, 5) for k, v in per_tv.items()},
-            "note": "working set (~73 MB) is L2-resident at this size"}
+        K = pkg.sci_fused_updates(tv, B, c["inner"], 0)
+        if K <= 0:
+            continue
+        for _ in range(3):
+            pkg.sci_tv_prox(x, tv, c["lam"], K, work=work)
+        reps = 20
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            pkg.sci_tv_prox(x, tv, c["lam"], K, work=work)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        per_tv[tv] = {"updates_per_launch": K, "launch_ms": round(ms, 5)}
+        ops += ALU_OPS_PER_UPDATE * N * K
+        ms_total += ms
+    achieved = ops / (ms_total * 1e-3) / 1e12
+    peak = _alu_peak() / 1e12
+    return {"kernel": "k_fgp_fused (temporally blocked FGP dual updates)", "bound": "alu",
+            "achieved": round(achieved, 3), "peak": round(peak, 3),
+            "peak_kind": "derived: 152 SMs x 128 FP32 lanes x max SM clock", "unit": "T FP32-op/s",
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "alg_ops_per_voxel_update": ALU_OPS_PER_UPDATE, "per_tv": per_tv}
 
 
 def _e2e(pkg, torch, dev, stream, args, c, masks_h, y_dev, bufs, flush):

@@ -64,7 +64,9 @@ typedef struct {
     int outer_iters;  /* T >= 0 outer iterations */
     int inner_iters;  /* S >= 1 FGP dual updates per TVdenoise */
     int storage;      /* sci_dtype of the library's internal fields; math is FP32 */
-    int fuse_k;       /* FGP updates fused per launch; 0 = library choice */
+    int fuse_k;       /* FGP dual updates per temporally blocked launch: 0 = library
+                         choice, k >= 1 = at most k (clamped to what the tile's halo
+                         allows), -1 = one launch per update (no temporal blocking) */
     int init;         /* 1: start from theta = Phi^T y (and u = 0); 0: resume from theta (and u) */
     int use_graph;    /* 1: run the T iterations as one cached CUDA graph; 0: plain launches */
 } sci_params;
@@ -150,6 +152,15 @@ sci_status sci_admm_tv(const float* y, const uint32_t* bits, int nx, int ny, int
  * whose addresses an earlier solve used, if the same addresses may be reused
  * with different contents sizes or parameters; safe at any time). */
 void sci_graph_cache_clear(void);
+
+/* Number of CUDA kernels the calling thread's most recent sci_gap_tv /
+ * sci_admm_tv call enqueued (as graph nodes or launches); for accounting. */
+long long sci_last_solve_launches(void);
+
+/* FGP dual updates per temporally blocked launch that the solver and
+ * sci_tv_prox use for this TV, frame count and params->fuse_k (0: the
+ * one-launch-per-update kernels serve; -1: invalid arguments). */
+int sci_fused_updates(int tv, int B, int inner_iters, int fuse_k);
 
 /* Scratch for the FP64 reductions below: at least this many bytes. */
 size_t sci_reduce_workspace(void);

@@ -13,6 +13,7 @@
 // The projection is folded into the first FGP launch (which forms xt on the
 // fly) and the next residual into the last one, so one outer iteration is
 // S + 1 launches and no separate projection pass.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <list>
@@ -43,7 +44,7 @@ std::vector<float> momentum_coeffs(int S) {
 
 // ---- workspace layout ----
 struct Layout {
-    size_t rinv, r, partials, xt, p[3], theta_s, u_s, total;
+    size_t rinv, r, partials, xt, p[4], theta_s, theta_s2, u_s, total;
 };
 
 Layout solver_layout(int nx, int ny, int B, int storage, bool admm) {
@@ -56,8 +57,10 @@ Layout solver_layout(int nx, int ny, int B, int storage, bool admm) {
     L.r = take(n * 4);
     L.partials = take((size_t)std::max(out_partial_count(g), kReduceParts) * 8);
     L.xt = take(N * es);
-    for (int b = 0; b < 3; ++b) L.p[b] = take(2 * N * es);
+    for (int b = 0; b < 4; ++b) L.p[b] = take(2 * N * es);  // per-update path uses 3
     L.theta_s = storage != SCI_F32 ? take(N * es) : 0;
+    L.theta_s2 = take(N * es);  // second theta buffer: the fused launch reads theta^(t) halos
+                                // while other CTAs write theta^(t+1)
     L.u_s = (storage != SCI_F32 && admm) ? take(N * es) : 0;
     L.total = off;
     return L;
@@ -67,7 +70,7 @@ Layout prox_layout(int nx, int ny, int B) {
     Layout L{};
     const size_t N = (size_t)nx * ny * B;
     size_t off = 0;
-    for (int b = 0; b < 3; ++b) { L.p[b] = off; off += align256(2 * N * 4); }
+    for (int b = 0; b < 4; ++b) { L.p[b] = off; off += align256(2 * N * 4); }
     L.total = off;
     return L;
 }
@@ -86,7 +89,7 @@ sci_status validate_params(const sci_params* p, bool admm) {
     if (admm && !(p->rho >= 0.f)) return SCI_ERR_ARG;
     if (p->outer_iters < 0 || p->inner_iters < 1) return SCI_ERR_ARG;
     if (p->storage < SCI_F32 || p->storage > SCI_F16) return SCI_ERR_ARG;
-    if (p->fuse_k < 0) return SCI_ERR_ARG;
+    if (p->fuse_k < -1) return SCI_ERR_ARG;
     return SCI_OK;
 }
 
@@ -95,6 +98,50 @@ sci_status validate_work(void* work, size_t have, size_t need) {
     if (work == nullptr || have < need) return SCI_ERR_WORKSPACE;
     if (((uintptr_t)work & 255u) != 0) return SCI_ERR_WORKSPACE;
     return SCI_OK;
+}
+
+// Dual updates per fused launch: fuse_k = -1 turns temporal blocking off;
+// otherwise the largest count the tile halo allows (halo = K + 1), capped by
+// fuse_k when it is positive.  Returns 0 when the per-update kernels serve.
+int choose_fuse(int tv, int B, int S, int fuse_k) {
+    if (fuse_k < 0) return 0;
+    const int maxh = fused_max_halo(tv, B);
+    if (maxh < 2) return 0;
+    int K = maxh - 1;
+    if (tv == SCI_TV_VTV) K = std::min(K, 2);  // 32x32 tiles: a small halo wins
+    else K = std::min(K, 10);
+    if (fuse_k > 0) K = std::min(fuse_k, maxh - 1);
+    K = std::min(K, kMaxFuse);
+    return std::max(1, std::min(K, S));
+}
+
+// S dual updates of FGP in fused launches of at most K updates each.
+template <typename T>
+int enqueue_fused_prox(int tv, OuterMode mode, int K, int S, float lam, const std::vector<float>& coef,
+                       FusedArgs base, FusedBufs<T> bufs, float* x_out_last, cudaStream_t s) {
+    int launches = 0;
+    for (int s0 = 0; s0 < S; s0 += K) {
+        const int k = std::min(K, S - s0);
+        FusedArgs a = base;
+        a.mode = mode;
+        a.K = k;
+        a.halo = k + 1;
+        a.first = s0 == 0;
+        a.last = s0 + k == S;
+        a.lambda = lam;
+        a.step = (float)(1.0 / (8.0 * (double)lam));
+        for (int i = 0; i < k; ++i) a.coef[i] = coef[(size_t)(s0 + i)];
+        a.x_out = a.last ? x_out_last : nullptr;
+        if (!launch_fgp_fused<T>(tv, a, bufs, s)) return -1;
+        ++launches;
+        // the next launch reads what this one wrote, and writes the other set
+        for (int i = 0; i < 4; ++i) {
+            T* written = bufs.st_out[i];
+            bufs.st_out[i] = const_cast<T*>(bufs.st_in[i]);
+            bufs.st_in[i] = written;
+        }
+    }
+    return launches;
 }
 
 // ---- the outer loop ----
@@ -112,8 +159,11 @@ struct SolveArgs {
     void* work;
 };
 
+// Enqueues one solve; returns the number of kernels launched, or -1 if a
+// fused launch could not be configured.
 template <typename T>
-void enqueue_solve(const SolveArgs& A, cudaStream_t s) {
+int enqueue_solve(const SolveArgs& A, cudaStream_t s) {
+    int nk = 0;
     const Geo g{A.nx, A.ny, A.B, (long long)A.nx * A.ny};
     const long long N = (long long)A.B * g.n;
     const Layout L = solver_layout(A.nx, A.ny, A.B, A.prm.storage, A.admm);
@@ -122,39 +172,65 @@ void enqueue_solve(const SolveArgs& A, cudaStream_t s) {
     float* r = reinterpret_cast<float*>(w + L.r);
     double* partials = reinterpret_cast<double*>(w + L.partials);
     T* xt = reinterpret_cast<T*>(w + L.xt);
-    T* P[3] = {reinterpret_cast<T*>(w + L.p[0]), reinterpret_cast<T*>(w + L.p[1]),
-               reinterpret_cast<T*>(w + L.p[2])};
+    T* P[4] = {reinterpret_cast<T*>(w + L.p[0]), reinterpret_cast<T*>(w + L.p[1]),
+               reinterpret_cast<T*>(w + L.p[2]), reinterpret_cast<T*>(w + L.p[3])};
     const bool f32 = std::is_same<T, float>::value;
     T* theta = f32 ? reinterpret_cast<T*>(A.theta) : reinterpret_cast<T*>(w + L.theta_s);
+    T* theta_alt = reinterpret_cast<T*>(w + L.theta_s2);
     T* u = nullptr;
     if (A.admm) u = f32 ? reinterpret_cast<T*>(A.u) : reinterpret_cast<T*>(w + L.u_s);
+    T* const theta_home = theta;
 
     launch_rinv(A.bits, g, A.admm ? A.prm.rho : 0.f, rinv, s);
+    ++nk;
     if (A.prm.init) {
         launch_adjoint<T>(A.y, A.bits, g, theta, s);
+        ++nk;
         if (A.admm) launch_zero(u, (size_t)N * sizeof(T), s);
     } else if (!f32) {
         launch_cast<float, T>(A.theta, theta, N, s);
-        if (A.admm) launch_cast<float, T>(A.u, u, N, s);
+        ++nk;
+        if (A.admm) { launch_cast<float, T>(A.u, u, N, s); ++nk; }
     }
     const int T_outer = A.prm.outer_iters, S = A.prm.inner_iters;
     const float lam = A.prm.lambda;
-    if (T_outer > 0) launch_residual_field<T>(theta, u, A.y, A.bits, rinv, g, r, s);
+    if (T_outer > 0) { launch_residual_field<T>(theta, u, A.y, A.bits, rinv, g, r, s); ++nk; }
     const std::vector<float> coef = momentum_coeffs(S);
     const OuterMode mode = A.admm ? OuterMode::Admm : OuterMode::Gap;
     const int nparts = out_partial_count(g);
+    const int K = choose_fuse(A.prm.tv, A.B, S, A.prm.fuse_k);
     for (int t = 0; t < T_outer; ++t) {
+        const bool last = t == T_outer - 1;
+        const bool metric = A.resid != nullptr && A.resid_every > 0 && ((t + 1) % A.resid_every == 0);
+        double* resid_slot = metric ? A.resid + ((t + 1) / A.resid_every - 1) : nullptr;
+        if (K > 0) {
+            // temporally blocked: ceil(S/K) fused launches, then the next residual
+            FusedArgs base{};
+            base.g = g;
+            base.bits = A.bits;
+            base.r = r;
+            FusedBufs<T> fb{theta, u, theta_alt, u, xt,
+                            {P[0], P[0] + N, P[1], P[1] + N}, {P[2], P[2] + N, P[3], P[3] + N}};
+            const int nf = enqueue_fused_prox<T>(A.prm.tv, mode, K, S, lam, coef, base, fb,
+                                                 last ? A.x_out : nullptr, s);
+            if (nf < 0) return -1;
+            nk += nf;
+            std::swap(theta, theta_alt);
+            if (!last) { launch_residual_field<T>(theta, u, A.y, A.bits, rinv, g, r, s); ++nk; }
+            if (metric) { launch_residual_norm<T>(theta, A.y, A.bits, g, partials, resid_slot, s); nk += 2; }
+            continue;
+        }
         launch_fgp_first<T>(A.prm.tv, mode, nullptr, theta, r, A.bits, g, lam, xt, P[0], s);
+        ++nk;
         int cur = 0, prev = -1;
         for (int it = 1; it < S; ++it) {
             const int out = 3 - cur - (prev < 0 ? (cur == 0 ? 1 : 0) : prev);
             launch_fgp_iter<T>(A.prm.tv, xt, P[cur], prev >= 0 ? P[prev] : nullptr, coef[(size_t)it - 1],
                                g, lam, P[out], s);
+            ++nk;
             prev = cur;
             cur = out;
         }
-        const bool last = t == T_outer - 1;
-        const bool metric = A.resid != nullptr && A.resid_every > 0 && ((t + 1) % A.resid_every == 0);
         OutArgs oa{};
         oa.mode = mode;
         oa.y = A.y;
@@ -163,41 +239,44 @@ void enqueue_solve(const SolveArgs& A, cudaStream_t s) {
         oa.r_next = last ? nullptr : r;
         oa.x_out = (last && f32) ? A.x_out : nullptr;
         oa.resid_partials = metric ? partials : nullptr;
-        if (last && !f32 && A.x_out != nullptr) {
-            // x^(T) from xt (GAP) or xt - u (ADMM) before the output overwrites u.
-            if (A.admm) {
-                // x = xt - u_old: stage u_old in FP32 through x_out, then subtract below.
-                launch_cast<T, float>(u, A.x_out, N, s);
-            }
+        if (last && !f32 && A.x_out != nullptr && A.admm) {
+            // x = xt - u_old: stage u_old in FP32 through x_out before the output overwrites u
+            launch_cast<T, float>(u, A.x_out, N, s);
+            ++nk;
         }
         launch_fgp_out<T>(oa, xt, P[cur], g, lam, theta, u, s);
-        if (last && !f32 && A.x_out != nullptr) {
-            // x_out = xt (GAP) or xt - u_old (ADMM, u_old staged above).
-            launch_xt_minus(xt, A.prm.storage, A.x_out, N, A.admm, s);
-        }
-        if (metric) launch_sum_partials(partials, nparts, A.resid + ((t + 1) / A.resid_every - 1), s);
+        ++nk;
+        if (last && !f32 && A.x_out != nullptr) { launch_xt_minus(xt, A.prm.storage, A.x_out, N, A.admm, s); ++nk; }
+        if (metric) { launch_sum_partials(partials, nparts, resid_slot, s); ++nk; }
     }
     if (!f32) {
         launch_cast<T, float>(theta, A.theta, N, s);
-        if (A.admm) launch_cast<T, float>(u, A.u, N, s);
+        ++nk;
+        if (A.admm) { launch_cast<T, float>(u, A.u, N, s); ++nk; }
+    } else if (theta != theta_home) {
+        cudaMemcpyAsync(theta_home, theta, (size_t)N * sizeof(T), cudaMemcpyDeviceToDevice, s);
     }
     if (T_outer == 0 && A.x_out != nullptr)
         cudaMemcpyAsync(A.x_out, A.theta, (size_t)N * 4, cudaMemcpyDeviceToDevice, s);
+    return nk;
 }
 
-void enqueue_solve_any(const SolveArgs& A, cudaStream_t s) {
+int enqueue_solve_any(const SolveArgs& A, cudaStream_t s) {
     switch (A.prm.storage) {
-        case SCI_BF16: enqueue_solve<__nv_bfloat16>(A, s); break;
-        case SCI_F16: enqueue_solve<__half>(A, s); break;
-        default: enqueue_solve<float>(A, s); break;
+        case SCI_BF16: return enqueue_solve<__nv_bfloat16>(A, s);
+        case SCI_F16: return enqueue_solve<__half>(A, s);
+        default: return enqueue_solve<float>(A, s);
     }
 }
+
+thread_local long long g_last_launches = 0;
 
 // ---- CUDA graph cache: one instantiated graph per distinct solve call ----
 struct GraphEntry {
     int device;
     SolveArgs args;
     cudaGraphExec_t exec;
+    int launches;
 };
 std::mutex g_mu;
 std::list<GraphEntry> g_cache;  // most recent first
@@ -216,7 +295,9 @@ sci_status run_solve(const SolveArgs& A, cudaStream_t stream) {
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) return SCI_ERR_CUDA;
     if (!A.prm.use_graph || cap != cudaStreamCaptureStatusNone) {
-        enqueue_solve_any(A, stream);
+        const int nk = enqueue_solve_any(A, stream);
+        if (nk < 0) return SCI_ERR_CUDA;
+        g_last_launches = nk;
         return check_launch();
     }
     int dev = 0;
@@ -226,6 +307,7 @@ sci_status run_solve(const SolveArgs& A, cudaStream_t stream) {
         if (it->device == dev && same_args(it->args, A)) {
             g_cache.splice(g_cache.begin(), g_cache, it);
             if (cudaGraphLaunch(g_cache.front().exec, stream) != cudaSuccess) return SCI_ERR_CUDA;
+            g_last_launches = g_cache.front().launches;
             return SCI_OK;
         }
     }
@@ -234,10 +316,10 @@ sci_status run_solve(const SolveArgs& A, cudaStream_t stream) {
         return SCI_ERR_CUDA;
     cudaStream_t cs = g_capture_stream[dev];
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SCI_ERR_CUDA;
-    enqueue_solve_any(A, cs);
+    const int nk = enqueue_solve_any(A, cs);
     cudaGraph_t graph = nullptr;
     const cudaError_t launch_err = cudaGetLastError();
-    if (cudaStreamEndCapture(cs, &graph) != cudaSuccess || launch_err != cudaSuccess) {
+    if (cudaStreamEndCapture(cs, &graph) != cudaSuccess || launch_err != cudaSuccess || nk < 0) {
         if (graph) cudaGraphDestroy(graph);
         return SCI_ERR_CUDA;
     }
@@ -245,12 +327,13 @@ sci_status run_solve(const SolveArgs& A, cudaStream_t stream) {
     const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ie != cudaSuccess) return SCI_ERR_CUDA;
-    g_cache.push_front(GraphEntry{dev, A, exec});
+    g_cache.push_front(GraphEntry{dev, A, exec, nk});
     while (g_cache.size() > kMaxGraphs) {
         cudaGraphExecDestroy(g_cache.back().exec);
         g_cache.pop_back();
     }
     if (cudaGraphLaunch(exec, stream) != cudaSuccess) return SCI_ERR_CUDA;
+    g_last_launches = nk;
     return SCI_OK;
 }
 
@@ -344,9 +427,22 @@ sci_status sci_tv_prox(const float* x, int nx, int ny, int B, int tv, float lamb
     const Geo g{nx, ny, B, (long long)nx * ny};
     cudaStream_t s = (cudaStream_t)stream;
     char* w = static_cast<char*>(work);
-    float* P[3] = {reinterpret_cast<float*>(w + L.p[0]), reinterpret_cast<float*>(w + L.p[1]),
-                   reinterpret_cast<float*>(w + L.p[2])};
+    float* P[4] = {reinterpret_cast<float*>(w + L.p[0]), reinterpret_cast<float*>(w + L.p[1]),
+                   reinterpret_cast<float*>(w + L.p[2]), reinterpret_cast<float*>(w + L.p[3])};
     const std::vector<float> coef = momentum_coeffs(inner_iters);
+    const int K = choose_fuse(tv, B, inner_iters, 0);
+    if (K > 0) {
+        FusedArgs base{};
+        base.g = g;
+        base.xin = x;
+        base.theta_f32 = theta;
+        const size_t N = (size_t)B * nx * ny;
+        FusedBufs<float> fb{nullptr, nullptr, nullptr, nullptr, nullptr,
+                            {P[0], P[0] + N, P[1], P[1] + N}, {P[2], P[2] + N, P[3], P[3] + N}};
+        if (enqueue_fused_prox<float>(tv, OuterMode::Prox, K, inner_iters, lambda, coef, base, fb, nullptr, s) < 0)
+            return SCI_ERR_CUDA;
+        return check_launch();
+    }
     launch_fgp_first<float>(tv, OuterMode::Prox, x, nullptr, nullptr, nullptr, g, lambda, nullptr, P[0], s);
     int cur = 0, prev = -1;
     for (int it = 1; it < inner_iters; ++it) {
@@ -388,6 +484,13 @@ void sci_graph_cache_clear(void) {
     std::lock_guard<std::mutex> lock(g_mu);
     for (auto& e : g_cache) cudaGraphExecDestroy(e.exec);
     g_cache.clear();
+}
+
+long long sci_last_solve_launches(void) { return g_last_launches; }
+
+int sci_fused_updates(int tv, int B, int inner_iters, int fuse_k) {
+    if (tv < SCI_TV_ATV || tv > SCI_TV_VTV || B < 1 || inner_iters < 1 || fuse_k < -1) return -1;
+    return choose_fuse(tv, B, inner_iters, fuse_k);
 }
 
 size_t sci_reduce_workspace(void) { return (size_t)kReduceParts * sizeof(double); }

@@ -67,4 +67,40 @@ void launch_fgp_out(const OutArgs& a, const T* xt, const T* p, Geo g, float lamb
 void launch_sum_partials(const double* partials, int count, double* out, cudaStream_t s);
 int out_partial_count(Geo g);
 
+// ---- temporally blocked FGP (sci_fused.cu) ----
+constexpr int kMaxFuse = 32;  // dual updates per fused launch
+struct FusedArgs {
+    Geo g;
+    OuterMode mode;
+    int K;                  // dual updates in this launch
+    int halo;               // tile halo, >= K + 1
+    int first;              // 1: w = p = 0 and x-tilde formed here (from theta, r or xin)
+    int last;               // 1: write theta (and u, x_out); 0: carry p, w (and x-tilde)
+    float lambda, step;     // lambda and 1/(8 lambda)
+    float coef[kMaxFuse];   // momentum coefficients of this launch's updates
+    const float* xin;       // Prox mode: the prox input
+    float* theta_f32;       // Prox mode: the prox output
+    const uint32_t* bits;   // Gap / Admm: packed masks
+    const float* r;         // Gap / Admm: residual field
+    float* x_out;           // optional FP32 x^(t+1) (last launch only)
+};
+// Buffers of one fused launch.  A CTA reads its whole extended tile but
+// writes only its interior, so whatever a launch reads from a neighbour's
+// interior must not be written by the same launch: theta and the carried dual
+// state (p_h, p_v, w_h, w_v) therefore ping-pong between two buffers.
+template <typename T>
+struct FusedBufs {
+    const T* theta_in;  // Gap / Admm: theta^(t) (read with halos by the first launch)
+    const T* u_in;      // Admm: u^(t) (read at the thread's own voxels by the last launch)
+    T* theta_out;       // must not alias theta_in
+    T* u_out;           // may alias u_in (the same thread reads, then writes)
+    T* xt;              // x-tilde, written by the first launch, read by later ones
+    const T* st_in[4];  // carried p_h, p_v, w_h, w_v (read by non-first launches)
+    T* st_out[4];       // must not alias st_in (written by non-last launches)
+};
+// Largest halo the fused kernel supports for this TV / frame count (0: none).
+int fused_max_halo(int tv, int B);
+template <typename T>
+bool launch_fgp_fused(int tv, const FusedArgs& a, const FusedBufs<T>& b, cudaStream_t s);
+
 }  // namespace sci

@@ -15,7 +15,7 @@ import torch
 __all__ = [
     "SciError", "TV", "DTYPE", "load", "sci_masks_pack", "sci_forward", "sci_adjoint",
     "sci_project", "sci_tv_prox", "sci_gap_tv", "sci_admm_tv", "sci_sqdiff_f64",
-    "sci_residual_f64", "sci_graph_cache_clear", "sci_tv_prox_noalloc", "Workspace", "SciParams",
+    "sci_residual_f64", "sci_graph_cache_clear", "sci_tv_prox_noalloc", "sci_last_solve_launches", "sci_fused_updates", "Workspace", "SciParams",
 ]
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsci.so")
@@ -60,6 +60,8 @@ _SIGS = {
     "sci_residual_f64": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp, _vp, _sz, _vp]),
     "sci_tv_prox_noalloc": (_i, [_vp, _i, _i, _i, _i, _f, _i, _vp, _vp]),
     "sci_tv_prox_noalloc_max_voxels": (C.c_longlong, []),
+    "sci_last_solve_launches": (C.c_longlong, []),
+    "sci_fused_updates": (_i, [_i, _i, _i, _i]),
 }
 
 
@@ -251,6 +253,16 @@ def sci_admm_tv(y, bits, B, tv, lam, rho, outer, inner, **kw):
 
 def sci_graph_cache_clear():
     load().sci_graph_cache_clear()
+
+
+def sci_fused_updates(tv: str, B: int, inner_iters: int, fuse_k: int = 0) -> int:
+    """Dual updates per fused launch the library uses (0: per-update kernels)."""
+    return int(load().sci_fused_updates(TV[tv], int(B), int(inner_iters), int(fuse_k)))
+
+
+def sci_last_solve_launches() -> int:
+    """Kernels enqueued by this thread's most recent solve call."""
+    return int(load().sci_last_solve_launches())
 
 
 def sci_sqdiff_f64(a: torch.Tensor, b: torch.Tensor | None = None,

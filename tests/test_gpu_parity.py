@@ -92,6 +92,33 @@ def test_solver_small(pkg, algo, tv, nx, ny, B):
         assert maxabs(x, xr) <= TOL_F32 and maxabs(th, thr) <= TOL_F32 and maxabs(u, ur) <= TOL_F32
 
 
+@pytest.mark.parametrize("fuse_k", [-1, 1, 3, 0, 7])
+@pytest.mark.parametrize("algo", ["gap", "admm"])
+@pytest.mark.parametrize("tv,nx,ny,B", [("atv", 150, 300, 3), ("itv2d", 70, 130, 2), ("vtv", 150, 100, 10),
+                                        ("vtv", 45, 70, 7), ("vtv", 40, 50, 12), ("vtv", 20, 30, 20)])
+def test_solver_fused_depths(pkg, fuse_k, algo, tv, nx, ny, B):
+    """Every temporal-blocking depth (and the per-update path, fuse_k = -1)
+    matches the oracle on sizes spanning several tiles with ragged tails."""
+    case, y = make_problem(nx, ny, B, 7 * B + nx, sigma=0.01)
+    bits = pkg.sci_masks_pack(to_dev(case.masks))
+    T, S = 3, 8
+    if algo == "gap":
+        x, th, _ = pkg.sci_gap_tv(to_dev(y), bits, B, tv, 0.05, T, S, fuse_k=fuse_k)
+        xr, thr = O.gap_tv(y, case.masks, 0.05, T, S, tv)
+    else:
+        x, th, _, _ = pkg.sci_admm_tv(to_dev(y), bits, B, tv, 0.05, 0.01, T, S, fuse_k=fuse_k)
+        xr, thr, _ = O.admm_tv(y, case.masks, 0.05, 0.01, T, S, tv)
+    assert maxabs(x, xr) <= TOL_F32 and maxabs(th, thr) <= TOL_F32
+
+
+@pytest.mark.parametrize("tv", O.TV_TYPES)
+@pytest.mark.parametrize("S", [1, 10, 25])
+def test_tv_prox_large_tiles(pkg, tv, S):
+    x = np.random.default_rng(S).random((10, 300, 260)).astype(np.float32)
+    th = pkg.sci_tv_prox(to_dev(x), tv, 0.05, S)
+    assert maxabs(th, O.fgp_prox(x, 0.05, S, tv)) <= 1e-5
+
+
 def test_gap_atv_256x256x8_full(pkg):
     """The 256x256x8 workload at its stated iterations (T = 50, S = 5, ATV, lambda = 0.05)."""
     cfg = ss.CONFIGS["gap_atv_256x256x8"]
