@@ -399,10 +399,33 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["sci", "reference"], default="sci")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-case", choices=["fused"], default=None,
+                    help="run one launch of the dominant kernel per TV form and exit (for profilers)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.kernel_case:
+        return run_kernel_case(args)
     return run_gpu(args)
+
+
+def run_kernel_case(args):
+    """One temporally blocked FGP launch per TV form on the 512x512x10 size."""
+    import torch
+    from paper_2005_08028_gb300 import build as b
+    if not os.path.exists(b.LIB_PATH):
+        b.build()
+    import paper_2005_08028_gb300 as pkg
+    c = _cfg()
+    dev = torch.device("cuda")
+    x = torch.rand((c["B"], c["nx"], c["ny"]), device=dev)
+    work = pkg.Workspace(dev)
+    for tv in ("atv", "itv2d", "vtv"):
+        K = pkg.sci_fused_updates(tv, c["B"], c["inner"], 0)
+        pkg.sci_tv_prox(x, tv, c["lam"], K, work=work)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_case": args.kernel_case, "ok": True}))
+    return 0
 
 
 if __name__ == "__main__":

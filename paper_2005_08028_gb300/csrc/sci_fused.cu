@@ -8,20 +8,21 @@
 // updates the interior widened by H - K >= 1 pixels is exact; the extra pixel
 // feeds D^T p in the output theta = xt - lambda D^T p.
 //
-// Thread mapping: thread t owns the pixels t, t + NT, ..., t + (Q-1) NT of
-// the tile (one column, Q rows NT/EW apart) and all F frames of each.
-// F = 1 for ATV / ITV2D, whose frames are independent (blockIdx.z picks the
-// frame); F >= B for VTV, whose dual projection couples the B frames of a
-// pixel -- its norm is then a register sum inside one thread.  A warp covers
-// 32 consecutive columns of one row: global loads are coalesced and the row
-// tests below are warp-uniform.
+// Thread mapping: the tile is cut into NS = NT/EW horizontal strips of Q
+// rows; thread t owns column t % EW of strip t / EW -- Q vertically adjacent
+// pixels -- and all F frames of each.  F = 1 for ATV / ITV2D, whose frames
+// are independent (blockIdx.z picks the frame); F >= B for VTV, whose dual
+// projection couples the B frames of a pixel -- the norm is then a register
+// sum inside one thread.  A warp covers 32 consecutive columns of one strip,
+// so global accesses are coalesced and the row tests below are warp-uniform.
 //
-// State: p and w of the owned slots live in registers; x-tilde, theta and the
-// neighbour-visible copy of w live in shared memory (16 bytes per slot).  Per
-// update a slot costs 8 shared-memory accesses and ~20 FP32 operations; no
-// global memory is touched between the updates of one launch.  Rows whose
-// results can no longer reach the interior are skipped: the needed band
-// shrinks by one row per update.
+// State: p, w (and, when registers allow, x-tilde and theta) of the owned
+// slots live in registers.  Vertical neighbours inside a strip are register
+// reads; shared memory carries only what other threads read: theta and w_h
+// of every slot (left/right neighbours) and w_v of each strip's last row.
+// No global memory is touched between the updates of one launch.  Where it
+// pays (see the configurations), rows whose results can no longer reach the
+// interior are skipped: the band that matters shrinks by one row per update.
 #include <atomic>
 
 #include "sci_internal.cuh"
@@ -37,31 +38,45 @@ __device__ __forceinline__ float rt(float v) {
     return ld<T>(&tmp, 0);
 }
 
+template <typename T> __device__ __forceinline__ float ldg(const T* p, long long i);
+template <> __device__ __forceinline__ float ldg<float>(const float* p, long long i) { return __ldg(p + i); }
+template <> __device__ __forceinline__ float ldg<__nv_bfloat16>(const __nv_bfloat16* p, long long i) {
+    return __bfloat162float(__ldg(p + i));
+}
+template <> __device__ __forceinline__ float ldg<__half>(const __half* p, long long i) {
+    return __half2float(__ldg(p + i));
+}
+
 // Compile-time tile configuration.
-template <int NT_, int Q_, int F_, int EW_LOG2_>
+template <int NT_, int Q_, int F_, int EW_LOG2_, bool REG_, bool SKIP_>
 struct FusedCfg {
     static constexpr int NT = NT_;            // threads per CTA
-    static constexpr int Q = Q_;              // pixels per thread
+    static constexpr int Q = Q_;              // rows per strip (pixels per thread)
     static constexpr int F = F_;              // frames held per CTA
     static constexpr int EW_LOG2 = EW_LOG2_;
     static constexpr int EW = 1 << EW_LOG2;   // tile width (columns)
-    static constexpr int P = NT * Q;          // pixels per tile
-    static constexpr int EH = P / EW;         // tile height (rows)
-    static constexpr int RS = NT / EW;        // row stride between a thread's pixels
-    static constexpr size_t SMEM = (size_t)F * P * 4 * sizeof(float);  // xt, theta, wh, wv
+    static constexpr int NS = NT / EW;        // strips
+    static constexpr int EH = NS * Q;         // tile height (rows)
+    static constexpr bool REG = REG_;         // x-tilde and theta of owned slots in registers
+    static constexpr bool SKIP = SKIP_;       // skip rows that can no longer reach the interior
+    // shared memory: theta, w_h [F][EH][EW]; w_v [F][NS][EW]; x-tilde [F][EH][EW] unless REG
+    static constexpr size_t SMEM =
+        ((size_t)F * EH * EW * (REG ? 2 : 3) + (size_t)F * NS * EW) * sizeof(float);
     static_assert(NT % EW == 0, "a CTA must cover whole rows");
+    static_assert(EW % 32 == 0, "a warp must stay inside one strip row");
 };
 
 template <typename T, int TV, class Cfg>
 __global__ void __launch_bounds__(Cfg::NT, 1)
 k_fgp_fused(FusedArgs a, FusedBufs<T> b) {
-    constexpr int NT = Cfg::NT, Q = Cfg::Q, F = Cfg::F, EW = Cfg::EW, EH = Cfg::EH, P = Cfg::P;
-    constexpr int RS = Cfg::RS;
+    constexpr int Q = Cfg::Q, F = Cfg::F, EW = Cfg::EW, EH = Cfg::EH, NS = Cfg::NS;
+    constexpr bool REG = Cfg::REG, SKIP = Cfg::SKIP;
+    constexpr int FP = EH * EW;  // slots per frame
     extern __shared__ float smem[];
-    float* s_xt = smem;              // [F][P]
-    float* s_th = smem + F * P;      // [F][P]
-    float* s_wh = smem + 2 * F * P;  // [F][P]
-    float* s_wv = smem + 3 * F * P;  // [F][P]
+    float* s_th = smem;                      // [F][EH][EW]
+    float* s_wh = s_th + F * FP;             // [F][EH][EW]
+    float* s_wv = s_wh + F * FP;             // [F][NS][EW]: last row of each strip
+    float* s_xt = s_wv + F * NS * EW;        // [F][EH][EW] (only when !REG)
 
     const Geo g = a.g;
     const int H = a.halo;
@@ -71,44 +86,59 @@ k_fgp_fused(FusedArgs a, FusedBufs<T> b) {
     const int f0 = (F == 1) ? blockIdx.z : 0;    // global frame of slot f = 0
     const int tid = threadIdx.x;
     const int col = tid & (EW - 1);
-    const int row0 = tid >> Cfg::EW_LOG2;
+    const int strip = tid >> Cfg::EW_LOG2;
+    const int r0 = strip * Q;                    // first row of the strip
     const int gj = gj0 + col;
     const bool col_in = gj >= 0 && gj < g.ny;
-    const bool hr = gj < g.ny - 1;
     const bool col_int = col >= H && col < EW - H;
+    const int gi_top = gi0 + r0;
+
+    // per-row flags as bit masks (bit q: row r0 + q)
+    unsigned in_m = 0, ah_m = 0, av_m = 0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int gi = gi_top + q;
+        const bool in = col_in && gi >= 0 && gi < g.nx;
+        in_m |= (unsigned)in << q;
+        ah_m |= (unsigned)(in && gj < g.ny - 1) << q;
+        av_m |= (unsigned)(in && gi < g.nx - 1) << q;
+    }
 
     float ph[F][Q], pv[F][Q], wh[F][Q], wv[F][Q];
+    float xr[REG ? F : 1][REG ? Q : 1], thr[REG ? F : 1][REG ? Q : 1];
 
-    // ---- load x-tilde (and carried duals) for the whole extended tile ----
+    // ---- load x-tilde (and the carried duals) for the whole extended tile ----
 #pragma unroll
-    for (int f = 0; f < F; ++f) {
-        if (f >= nfr) break;
-        const long long fo = (long long)(f0 + f) * g.n;
+    for (int q = 0; q < Q; ++q) {
+        const bool in = (in_m >> q) & 1u;
+        const long long pix = in ? (long long)(gi_top + q) * g.ny + gj : 0;
+        uint32_t word = 0;
+        float rv = 0.f;
+        if (in && a.first && a.mode != OuterMode::Prox) {
+            word = __ldg(a.bits + pix);
+            rv = __ldg(a.r + pix);
+        }
 #pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const int r = row0 + q * RS, gi = gi0 + r;
-            const int o = f * P + r * EW + col;
+        for (int f = 0; f < F; ++f) {
+            if (f >= nfr) break;
+            const long long gidx = (long long)(f0 + f) * g.n + pix;
             float x = 0.f, a_ph = 0.f, a_pv = 0.f, a_wh = 0.f, a_wv = 0.f;
-            if (col_in && gi >= 0 && gi < g.nx) {
-                const long long pix = (long long)gi * g.ny + gj;
-                const long long gidx = fo + pix;
-                if (a.mode == OuterMode::Prox) {
-                    x = a.xin[gidx];
-                } else if (a.first) {
-                    x = rt<T>(ld<T>(b.theta_in, gidx) + mask_bit(a.bits[pix], f0 + f) * a.r[pix]);
-                } else {
-                    x = ld<T>(b.xt, gidx);
-                }
+            if (in) {
+                if (a.mode == OuterMode::Prox) x = __ldg(a.xin + gidx);
+                else if (a.first) x = rt<T>(ldg<T>(b.theta_in, gidx) + mask_bit(word, f0 + f) * rv);
+                else x = ldg<T>(b.xt, gidx);
                 if (!a.first) {
-                    a_ph = ld<T>(b.st_in[0], gidx);
-                    a_pv = ld<T>(b.st_in[1], gidx);
-                    a_wh = ld<T>(b.st_in[2], gidx);
-                    a_wv = ld<T>(b.st_in[3], gidx);
+                    a_ph = ldg<T>(b.st_in[0], gidx);
+                    a_pv = ldg<T>(b.st_in[1], gidx);
+                    a_wh = ldg<T>(b.st_in[2], gidx);
+                    a_wv = ldg<T>(b.st_in[3], gidx);
                 }
             }
-            s_xt[o] = x;
+            const int o = f * FP + (r0 + q) * EW + col;
+            if (REG) xr[REG ? f : 0][REG ? q : 0] = x;
+            else s_xt[o] = x;
             s_wh[o] = a_wh;
-            s_wv[o] = a_wv;
+            if (q == Q - 1) s_wv[(f * NS + strip) * EW + col] = a_wv;
             ph[f][q] = a_ph;
             pv[f][q] = a_pv;
             wh[f][q] = a_wh;
@@ -119,24 +149,29 @@ k_fgp_fused(FusedArgs a, FusedBufs<T> b) {
 
     const float lam = a.lambda, step = a.step;
     for (int s = 0; s < a.K; ++s) {
-        const int m = H - 1 - s;                       // margin still exact after this update
-        const int rlo_p = H - m, rhi_p = EH - H + m;   // rows whose p is updated
-        const bool skip_theta = a.first && s == 0;     // w = 0 there: theta = xt
-        // ---- theta = xt - lambda (D^T w) on rows [rlo_p, rhi_p] ----
+        // rows whose p stays exact after this update: [1 + s, EH - 1 - s);
+        // theta is needed on those rows and the one below
+        const int rlo = 1 + s, rhi = EH - 1 - s;
+        const int qlo = SKIP ? max(rlo - r0, 0) : 0;
+        const int qhi_p = SKIP ? min(rhi - r0, Q) : Q, qhi_t = SKIP ? min(rhi + 1 - r0, Q) : Q;
+        const bool skip_theta = a.first && s == 0;  // w = 0 there: theta = xt
+        // ---- theta = xt - lambda (D^T w) ----
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            const int r = row0 + q * RS;
-            if (r < rlo_p || r > rhi_p) continue;
+            if (q < qlo || q >= qhi_t) continue;
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 if (f >= nfr) break;
-                const int o = f * P + r * EW + col;
-                float th = s_xt[o];
+                const int o = f * FP + (r0 + q) * EW + col;
+                float th = REG ? xr[REG ? f : 0][REG ? q : 0] : s_xt[o];
                 if (!skip_theta) {
                     const float wl = col > 0 ? s_wh[o - 1] : 0.f;
-                    const float wu = r > 0 ? s_wv[o - EW] : 0.f;
+                    float wu;
+                    if (q > 0) wu = wv[f][q > 0 ? q - 1 : 0];
+                    else wu = strip > 0 ? s_wv[(f * NS + strip - 1) * EW + col] : 0.f;
                     th = th - lam * ((wl - wh[f][q]) + (wu - wv[f][q]));
                 }
+                if (REG) thr[REG ? f : 0][REG ? q : 0] = th;
                 s_th[o] = th;
             }
         }
@@ -145,23 +180,23 @@ k_fgp_fused(FusedArgs a, FusedBufs<T> b) {
         const float c = a.coef[s];
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            const int r = row0 + q * RS, gi = gi0 + r;
-            if (r < rlo_p || r >= rhi_p) continue;
-            const bool in = col_in && gi >= 0 && gi < g.nx;
-            const bool hd = gi < g.nx - 1;
+            if (q < qlo || q >= qhi_p) continue;
+            const bool mh = (ah_m >> q) & 1u, mv = (av_m >> q) & 1u;
             float n2 = 0.f;
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 if (f >= nfr) break;
-                const int o = f * P + r * EW + col;
-                const float t0 = s_th[o];
+                const int o = f * FP + (r0 + q) * EW + col;
+                const float t0 = REG ? thr[REG ? f : 0][REG ? q : 0] : s_th[o];
                 const float tr = col < EW - 1 ? s_th[o + 1] : t0;
-                const float td = r < EH - 1 ? s_th[o + EW] : t0;
-                const float ah = (in && hr) ? fmaf(tr - t0, step, wh[f][q]) : 0.f;
-                const float av = (in && hd) ? fmaf(td - t0, step, wv[f][q]) : 0.f;
+                float td;
+                if (q < Q - 1) td = REG ? thr[REG ? f : 0][REG && q < Q - 1 ? q + 1 : 0] : s_th[o + EW];
+                else td = (r0 + q < EH - 1) ? s_th[o + EW] : t0;
+                const float ah = mh ? fmaf(tr - t0, step, wh[f][q]) : 0.f;
+                const float av = mv ? fmaf(td - t0, step, wv[f][q]) : 0.f;
                 wh[f][q] = ah;
                 wv[f][q] = av;
-                if (TV == SCI_TV_VTV) n2 += ah * ah + av * av;
+                if (TV == SCI_TV_VTV) n2 = fmaf(ah, ah, fmaf(av, av, n2));
             }
             const float vscale = (TV == SCI_TV_VTV) ? fminf(1.f, rsqrtf(n2)) : 1.f;
 #pragma unroll
@@ -186,9 +221,8 @@ k_fgp_fused(FusedArgs a, FusedBufs<T> b) {
                 pv[f][q] = nv;
                 wh[f][q] = wnh;
                 wv[f][q] = wnv;
-                const int o = f * P + r * EW + col;
-                s_wh[o] = wnh;
-                s_wv[o] = wnv;
+                s_wh[f * FP + (r0 + q) * EW + col] = wnh;
+                if (q == Q - 1) s_wv[(f * NS + strip) * EW + col] = wnv;
             }
         }
         __syncthreads();
@@ -199,14 +233,15 @@ k_fgp_fused(FusedArgs a, FusedBufs<T> b) {
         // carry x-tilde (first launch of a solve), p and w of the interior
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            const int r = row0 + q * RS, gi = gi0 + r;
-            if (!col_int || r < H || r >= EH - H || !col_in || gi >= g.nx) continue;
-            const long long pix = (long long)gi * g.ny + gj;
+            const int r = r0 + q;
+            if (!((in_m >> q) & 1u) || !col_int || r < H || r >= EH - H) continue;
+            const long long pix = (long long)(gi_top + q) * g.ny + gj;
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 if (f >= nfr) break;
                 const long long gidx = (long long)(f0 + f) * g.n + pix;
-                if (a.first && a.mode != OuterMode::Prox) st<T>(b.xt, gidx, s_xt[f * P + r * EW + col]);
+                if (a.first && a.mode != OuterMode::Prox)
+                    st<T>(b.xt, gidx, REG ? xr[REG ? f : 0][REG ? q : 0] : s_xt[f * FP + r * EW + col]);
                 st<T>(b.st_out[0], gidx, ph[f][q]);
                 st<T>(b.st_out[1], gidx, pv[f][q]);
                 st<T>(b.st_out[2], gidx, wh[f][q]);
@@ -215,32 +250,48 @@ k_fgp_fused(FusedArgs a, FusedBufs<T> b) {
         }
         return;
     }
-    // theta = xt - lambda D^T p needs p at the left / up neighbours: stage p
-    // in the w slots (the update loop ended with a barrier).
+    // theta = xt - lambda D^T p needs p_h of the left neighbour and p_v of the
+    // row above: stage them where w_h / w_v were (the loop ended with a barrier).
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        const int r = row0 + q * RS;
 #pragma unroll
         for (int f = 0; f < F; ++f) {
             if (f >= nfr) break;
-            const int o = f * P + r * EW + col;
-            s_wh[o] = ph[f][q];
-            s_wv[o] = pv[f][q];
+            s_wh[f * FP + (r0 + q) * EW + col] = ph[f][q];
+            if (q == Q - 1) s_wv[(f * NS + strip) * EW + col] = pv[f][q];
+        }
+    }
+    // x^(t+1) = xt - u^(t) for ADMM (only when x is requested): u^(t) is read
+    // before u^(t+1) overwrites it.  Issue every load first (into the thread's
+    // own theta slots, free now) so none waits behind a store it might alias.
+    if (a.mode == OuterMode::Admm && a.x_out != nullptr) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int r = r0 + q;
+            const bool mine = ((in_m >> q) & 1u) && col_int && r >= H && r < EH - H;
+            const long long pix = mine ? (long long)(gi_top + q) * g.ny + gj : 0;
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                if (f >= nfr) break;
+                s_th[f * FP + r * EW + col] = mine ? ldg<T>(b.u_in, (long long)(f0 + f) * g.n + pix) : 0.f;
+            }
         }
     }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        const int r = row0 + q * RS, gi = gi0 + r;
-        if (!col_int || r < H || r >= EH - H || !col_in || gi >= g.nx) continue;
-        const long long pix = (long long)gi * g.ny + gj;
+        const int r = r0 + q;
+        if (!((in_m >> q) & 1u) || !col_int || r < H || r >= EH - H) continue;
+        const long long pix = (long long)(gi_top + q) * g.ny + gj;
 #pragma unroll
         for (int f = 0; f < F; ++f) {
             if (f >= nfr) break;
-            const int o = f * P + r * EW + col;
+            const int o = f * FP + r * EW + col;
             const float pl = col > 0 ? s_wh[o - 1] : 0.f;
-            const float pu = r > 0 ? s_wv[o - EW] : 0.f;
-            const float x0 = s_xt[o];
+            float pu;
+            if (q > 0) pu = pv[f][q > 0 ? q - 1 : 0];
+            else pu = strip > 0 ? s_wv[(f * NS + strip - 1) * EW + col] : 0.f;
+            const float x0 = REG ? xr[REG ? f : 0][REG ? q : 0] : s_xt[o];
             const float th = x0 - lam * ((pl - ph[f][q]) + (pu - pv[f][q]));
             const long long gidx = (long long)(f0 + f) * g.n + pix;
             if (a.mode == OuterMode::Prox) {
@@ -251,9 +302,8 @@ k_fgp_fused(FusedArgs a, FusedBufs<T> b) {
             if (a.mode == OuterMode::Gap) {
                 if (a.x_out != nullptr) a.x_out[gidx] = x0;
             } else {
-                const float u_old = ld<T>(b.u_in, gidx);
                 st<T>(b.u_out, gidx, x0 - rt<T>(th));
-                if (a.x_out != nullptr) a.x_out[gidx] = x0 - u_old;
+                if (a.x_out != nullptr) a.x_out[gidx] = x0 - s_th[o];
             }
         }
     }
@@ -261,11 +311,14 @@ k_fgp_fused(FusedArgs a, FusedBufs<T> b) {
 
 // ---------------------------------------------------------------- configurations
 
-using CfgF1 = FusedCfg<512, 16, 1, 7>;   // 128 x 64 tile, one frame
-using CfgF1s = FusedCfg<256, 8, 1, 6>;   // 64 x 32 tile, one frame (small images)
-using CfgV8 = FusedCfg<512, 2, 8, 5>;    // 32 x 32 tile, up to 8 frames
-using CfgV10 = FusedCfg<512, 2, 10, 5>;  // 32 x 32 tile, up to 10 frames
-using CfgV16 = FusedCfg<256, 2, 16, 5>;  // 32 x 16 tile, up to 16 frames
+// One-frame tiles (16-row strips) update every row: skipping rows would idle
+// whole strips and stall the others at the barriers.  The VTV tiles have
+// 2-row strips, where skipping balances well and saves work.
+using CfgF1 = FusedCfg<512, 16, 1, 7, true, false>;    // 128 x 64 tile, one frame
+using CfgF1s = FusedCfg<256, 8, 1, 6, true, false>;    // 64 x 32 tile, one frame (small images)
+using CfgV8 = FusedCfg<512, 2, 8, 5, false, true>;     // 32 x 32 tile, up to 8 frames
+using CfgV10 = FusedCfg<512, 2, 10, 5, false, true>;   // 32 x 32 tile, up to 10 frames
+using CfgV16 = FusedCfg<256, 2, 16, 5, false, true>;   // 32 x 16 tile, up to 16 frames
 
 std::atomic<unsigned long long> g_attr_done[48];
 
