@@ -148,6 +148,39 @@ sci_status sci_admm_tv(const float* y, const uint32_t* bits, int nx, int ny, int
                        double* resid, int resid_every, void* work, size_t work_bytes,
                        sci_stream_t stream);
 
+/* One measurement of a batched reconstruction. */
+typedef struct {
+    int nx, ny, B;          /* frame size and frame count (B <= 32; VTV: B <= 24) */
+    const float* y;         /* measurement, float32 [nx][ny] */
+    const uint32_t* bits;   /* packed masks, uint32 [nx][ny] */
+    float* theta;           /* in/out float32 [B][nx][ny] (input used when params->init = 0) */
+    float* x_out;           /* optional float32 [B][nx][ny]: x^(T) */
+} sci_problem;
+
+/* Bytes of scratch sci_gap_tv_batched needs for these problems (0: invalid). */
+size_t sci_gap_tv_batched_workspace(const sci_problem* problems, int count, const sci_params* params);
+
+/*
+ * GAP-TV (Algorithm 1) on `count` independent measurements of any mix of
+ * sizes, all with the same params.  problems: HOST array of descriptors
+ * (device pointers inside).  Each launch covers every measurement: the pixel
+ * kernels walk a table of 256-pixel blocks and the temporally blocked FGP
+ * kernel a table of tiles (largest measurements first), so the T iterations
+ * are about 2 + ceil(S/K) launches each, captured once as a CUDA graph and
+ * replayed on later identical calls.  The tables are copied from host memory
+ * at every call, so this call must not be made while `stream` is capturing
+ * (SCI_ERR_ARG).  VTV problems need B <= 24 (SCI_ERR_SHAPE otherwise).
+ * Results equal those of sci_gap_tv on each measurement.
+ */
+sci_status sci_gap_tv_batched(const sci_problem* problems, int count, const sci_params* params,
+                              void* work, size_t work_bytes, sci_stream_t stream);
+
+/* Kernels enqueued by this thread's most recent sci_gap_tv_batched call. */
+long long sci_last_batch_launches(void);
+
+/* Release every CUDA graph cached by sci_gap_tv_batched. */
+void sci_batch_graph_cache_clear(void);
+
 /* Release every CUDA graph the solver has cached (call before freeing buffers
  * whose addresses an earlier solve used, if the same addresses may be reused
  * with different contents sizes or parameters; safe at any time). */

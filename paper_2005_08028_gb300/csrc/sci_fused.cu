@@ -23,6 +23,7 @@
 // No global memory is touched between the updates of one launch.  Where it
 // pays (see the configurations), rows whose results can no longer reach the
 // interior are skipped: the band that matters shrinks by one row per update.
+#include <algorithm>
 #include <atomic>
 
 #include "sci_internal.cuh"
@@ -66,24 +67,65 @@ struct FusedCfg {
     static_assert(EW % 32 == 0, "a warp must stay inside one strip row");
 };
 
-template <typename T, int TV, class Cfg>
-__global__ void __launch_bounds__(Cfg::NT, 1)
-k_fgp_fused(FusedArgs a, FusedBufs<T> b) {
+// Problem views for fused_tile: a single problem read from the kernel's
+// parameter space, or one entry of a device-resident batch table.
+template <typename T>
+struct SingleProb {
+    const FusedArgs* a;
+    const FusedBufs<T>* b;
+    __device__ Geo g() const { return a->g; }
+    __device__ const uint32_t* bits() const { return a->bits; }
+    __device__ const float* r() const { return a->r; }
+    __device__ float* x_out() const { return a->x_out; }
+    __device__ const float* xin() const { return a->xin; }
+    __device__ float* theta_f32() const { return a->theta_f32; }
+    __device__ const T* theta_in() const { return b->theta_in; }
+    __device__ T* theta_out() const { return b->theta_out; }
+    __device__ const T* u_in() const { return b->u_in; }
+    __device__ T* u_out() const { return b->u_out; }
+    __device__ T* xt() const { return b->xt; }
+    __device__ const T* st_in(int i) const { return b->st_in[i]; }
+    __device__ T* st_out(int i) const { return b->st_out[i]; }
+};
+template <typename T>
+struct BatchProb {
+    const BatchItem<T>* it;
+    int tpar, spar, want_x;
+    __device__ Geo g() const { return it->g; }
+    __device__ const uint32_t* bits() const { return it->bits; }
+    __device__ const float* r() const { return it->r; }
+    __device__ float* x_out() const { return want_x ? it->x_out : nullptr; }
+    __device__ const float* xin() const { return nullptr; }
+    __device__ float* theta_f32() const { return nullptr; }
+    __device__ const T* theta_in() const { return it->theta[tpar]; }
+    __device__ T* theta_out() const { return it->theta[tpar ^ 1]; }
+    __device__ const T* u_in() const { return nullptr; }
+    __device__ T* u_out() const { return nullptr; }
+    __device__ T* xt() const { return it->xt; }
+    __device__ const T* st_in(int i) const { return it->st[spar][i]; }
+    __device__ T* st_out(int i) const { return it->st[spar ^ 1][i]; }
+};
+
+// One tile (bx, by) of frame bz (one-frame tiles) of one problem.  `a`
+// carries the launch-wide settings (K, halo, first/last, lambda, momentum),
+// `p` the problem's geometry and buffers.
+template <typename T, int TV, class Cfg, class Prob>
+__device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, int bx, int by, int bz,
+                                           float* smem) {
     constexpr int Q = Cfg::Q, F = Cfg::F, EW = Cfg::EW, EH = Cfg::EH, NS = Cfg::NS;
     constexpr bool REG = Cfg::REG, SKIP = Cfg::SKIP;
     constexpr int FP = EH * EW;  // slots per frame
-    extern __shared__ float smem[];
     float* s_th = smem;                      // [F][EH][EW]
     float* s_wh = s_th + F * FP;             // [F][EH][EW]
     float* s_wv = s_wh + F * FP;             // [F][NS][EW]: last row of each strip
     float* s_xt = s_wv + F * NS * EW;        // [F][EH][EW] (only when !REG)
 
-    const Geo g = a.g;
+    const Geo g = p.g();
     const int H = a.halo;
     const int TI = EH - 2 * H, TJ = EW - 2 * H;  // interior size
-    const int gi0 = blockIdx.y * TI - H, gj0 = blockIdx.x * TJ - H;
+    const int gi0 = by * TI - H, gj0 = bx * TJ - H;
     const int nfr = (F == 1) ? 1 : g.B;          // frames this CTA updates
-    const int f0 = (F == 1) ? blockIdx.z : 0;    // global frame of slot f = 0
+    const int f0 = (F == 1) ? bz : 0;            // global frame of slot f = 0
     const int tid = threadIdx.x;
     const int col = tid & (EW - 1);
     const int strip = tid >> Cfg::EW_LOG2;
@@ -115,8 +157,8 @@ k_fgp_fused(FusedArgs a, FusedBufs<T> b) {
         uint32_t word = 0;
         float rv = 0.f;
         if (in && a.first && a.mode != OuterMode::Prox) {
-            word = __ldg(a.bits + pix);
-            rv = __ldg(a.r + pix);
+            word = __ldg(p.bits() + pix);
+            rv = __ldg(p.r() + pix);
         }
 #pragma unroll
         for (int f = 0; f < F; ++f) {
@@ -124,14 +166,14 @@ k_fgp_fused(FusedArgs a, FusedBufs<T> b) {
             const long long gidx = (long long)(f0 + f) * g.n + pix;
             float x = 0.f, a_ph = 0.f, a_pv = 0.f, a_wh = 0.f, a_wv = 0.f;
             if (in) {
-                if (a.mode == OuterMode::Prox) x = __ldg(a.xin + gidx);
-                else if (a.first) x = rt<T>(ldg<T>(b.theta_in, gidx) + mask_bit(word, f0 + f) * rv);
-                else x = ldg<T>(b.xt, gidx);
+                if (a.mode == OuterMode::Prox) x = __ldg(p.xin() + gidx);
+                else if (a.first) x = rt<T>(ldg<T>(p.theta_in(), gidx) + mask_bit(word, f0 + f) * rv);
+                else x = ldg<T>(p.xt(), gidx);
                 if (!a.first) {
-                    a_ph = ldg<T>(b.st_in[0], gidx);
-                    a_pv = ldg<T>(b.st_in[1], gidx);
-                    a_wh = ldg<T>(b.st_in[2], gidx);
-                    a_wv = ldg<T>(b.st_in[3], gidx);
+                    a_ph = ldg<T>(p.st_in(0), gidx);
+                    a_pv = ldg<T>(p.st_in(1), gidx);
+                    a_wh = ldg<T>(p.st_in(2), gidx);
+                    a_wv = ldg<T>(p.st_in(3), gidx);
                 }
             }
             const int o = f * FP + (r0 + q) * EW + col;
@@ -241,11 +283,11 @@ k_fgp_fused(FusedArgs a, FusedBufs<T> b) {
                 if (f >= nfr) break;
                 const long long gidx = (long long)(f0 + f) * g.n + pix;
                 if (a.first && a.mode != OuterMode::Prox)
-                    st<T>(b.xt, gidx, REG ? xr[REG ? f : 0][REG ? q : 0] : s_xt[f * FP + r * EW + col]);
-                st<T>(b.st_out[0], gidx, ph[f][q]);
-                st<T>(b.st_out[1], gidx, pv[f][q]);
-                st<T>(b.st_out[2], gidx, wh[f][q]);
-                st<T>(b.st_out[3], gidx, wv[f][q]);
+                    st<T>(p.xt(), gidx, REG ? xr[REG ? f : 0][REG ? q : 0] : s_xt[f * FP + r * EW + col]);
+                st<T>(p.st_out(0), gidx, ph[f][q]);
+                st<T>(p.st_out(1), gidx, pv[f][q]);
+                st<T>(p.st_out(2), gidx, wh[f][q]);
+                st<T>(p.st_out(3), gidx, wv[f][q]);
             }
         }
         return;
@@ -264,7 +306,7 @@ k_fgp_fused(FusedArgs a, FusedBufs<T> b) {
     // x^(t+1) = xt - u^(t) for ADMM (only when x is requested): u^(t) is read
     // before u^(t+1) overwrites it.  Issue every load first (into the thread's
     // own theta slots, free now) so none waits behind a store it might alias.
-    if (a.mode == OuterMode::Admm && a.x_out != nullptr) {
+    if (a.mode == OuterMode::Admm && p.x_out() != nullptr) {
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const int r = r0 + q;
@@ -273,7 +315,7 @@ k_fgp_fused(FusedArgs a, FusedBufs<T> b) {
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 if (f >= nfr) break;
-                s_th[f * FP + r * EW + col] = mine ? ldg<T>(b.u_in, (long long)(f0 + f) * g.n + pix) : 0.f;
+                s_th[f * FP + r * EW + col] = mine ? ldg<T>(p.u_in(), (long long)(f0 + f) * g.n + pix) : 0.f;
             }
         }
     }
@@ -295,15 +337,15 @@ k_fgp_fused(FusedArgs a, FusedBufs<T> b) {
             const float th = x0 - lam * ((pl - ph[f][q]) + (pu - pv[f][q]));
             const long long gidx = (long long)(f0 + f) * g.n + pix;
             if (a.mode == OuterMode::Prox) {
-                a.theta_f32[gidx] = th;
+                p.theta_f32()[gidx] = th;
                 continue;
             }
-            st<T>(b.theta_out, gidx, th);
+            st<T>(p.theta_out(), gidx, th);
             if (a.mode == OuterMode::Gap) {
-                if (a.x_out != nullptr) a.x_out[gidx] = x0;
+                if (p.x_out() != nullptr) p.x_out()[gidx] = x0;
             } else {
-                st<T>(b.u_out, gidx, x0 - rt<T>(th));
-                if (a.x_out != nullptr) a.x_out[gidx] = x0 - s_th[o];
+                st<T>(p.u_out(), gidx, x0 - rt<T>(th));
+                if (p.x_out() != nullptr) p.x_out()[gidx] = x0 - s_th[o];
             }
         }
     }
@@ -313,14 +355,51 @@ k_fgp_fused(FusedArgs a, FusedBufs<T> b) {
 
 // One-frame tiles (16-row strips) update every row: skipping rows would idle
 // whole strips and stall the others at the barriers.  The VTV tiles have
-// 2-row strips, where skipping balances well and saves work.
+// 1- or 2-row strips, where skipping balances well and saves work.
 using CfgF1 = FusedCfg<512, 16, 1, 7, true, false>;    // 128 x 64 tile, one frame
 using CfgF1s = FusedCfg<256, 8, 1, 6, true, false>;    // 64 x 32 tile, one frame (small images)
 using CfgV8 = FusedCfg<512, 2, 8, 5, false, true>;     // 32 x 32 tile, up to 8 frames
 using CfgV10 = FusedCfg<512, 2, 10, 5, false, true>;   // 32 x 32 tile, up to 10 frames
 using CfgV16 = FusedCfg<256, 2, 16, 5, false, true>;   // 32 x 16 tile, up to 16 frames
+using CfgV24 = FusedCfg<256, 2, 24, 5, false, true>;   // 32 x 16 tile, up to 24 frames
 
-std::atomic<unsigned long long> g_attr_done[48];
+template <typename T, int TV, class Cfg>
+__global__ void __launch_bounds__(Cfg::NT, 1)
+k_fgp_fused(const __grid_constant__ FusedArgs a, const __grid_constant__ FusedBufs<T> b) {
+    extern __shared__ float smem[];
+    const SingleProb<T> p{&a, &b};
+    fused_tile<T, TV, Cfg>(a, p, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+}
+
+// Many problems of one tile class in one launch: work item w is a tile of
+// the problem whose [cta_begin, next cta_begin) range holds w.  A persistent
+// grid walks the work items (largest problems first).  Each class has its own
+// kernel: one kernel holding every class's tile code needs more registers
+// than an SM has and spills.
+template <typename T, int TV, class Cfg>
+__global__ void __launch_bounds__(Cfg::NT, 1)
+k_fgp_fused_batched(const __grid_constant__ FusedArgs a, const BatchItem<T>* __restrict__ items, int nitems,
+                    int total, int tpar, int spar, int want_x) {
+    extern __shared__ float smem[];
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+        int lo = 0, hi = nitems - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (items[mid].cta_begin <= w) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchItem<T>* it = items + lo;
+        const int local = w - it->cta_begin;
+        const int tiles_x = it->tiles_x, per_frame = tiles_x * it->tiles_y;
+        const int bz = local / per_frame, rem = local - bz * per_frame;
+        const int by = rem / tiles_x, bx = rem - by * tiles_x;
+        const BatchProb<T> p{it, tpar, spar, want_x};
+        fused_tile<T, TV, Cfg>(a, p, bx, by, bz, smem);
+        __syncthreads();  // shared memory is reused by the next work item
+    }
+}
+
+std::atomic<unsigned long long> g_attr_done[64];
 
 template <typename T, int TV, class Cfg>
 bool launch_cfg(int slot, const FusedArgs& a, const FusedBufs<T>& b, cudaStream_t s) {
@@ -346,7 +425,7 @@ bool launch_cfg(int slot, const FusedArgs& a, const FusedBufs<T>& b, cudaStream_
 // One "attribute set" flag word per (storage type, TV, configuration).
 template <typename T>
 constexpr int type_slot(int tv, int cfg) {
-    return (std::is_same<T, float>::value ? 0 : (std::is_same<T, __half>::value ? 1 : 2)) * 15 + tv * 5 + cfg;
+    return (std::is_same<T, float>::value ? 0 : (std::is_same<T, __half>::value ? 1 : 2)) * 21 + tv * 7 + cfg;
 }
 
 template <typename T, int TV>
@@ -359,7 +438,14 @@ bool launch_tv(const FusedArgs& a, const FusedBufs<T>& b, cudaStream_t s) {
     if (a.g.B <= 8) return launch_cfg<T, TV, CfgV8>(type_slot<T>(TV, 2), a, b, s);
     if (a.g.B <= 10) return launch_cfg<T, TV, CfgV10>(type_slot<T>(TV, 3), a, b, s);
     if (a.g.B <= 16) return launch_cfg<T, TV, CfgV16>(type_slot<T>(TV, 4), a, b, s);
+    if (a.g.B <= 24) return launch_cfg<T, TV, CfgV24>(type_slot<T>(TV, 5), a, b, s);
     return false;
+}
+
+template <class Cfg>
+void dims_of(int& EH, int& EW) {
+    EH = Cfg::EH;
+    EW = Cfg::EW;
 }
 
 }  // namespace
@@ -367,8 +453,82 @@ bool launch_tv(const FusedArgs& a, const FusedBufs<T>& b, cudaStream_t s) {
 int fused_max_halo(int tv, int B) {
     if (tv != SCI_TV_VTV) return 20;
     if (B <= 10) return 8;
-    if (B <= 16) return 4;
+    if (B <= 24) return 4;
     return 0;  // no fused kernel: the per-update kernels serve
+}
+
+int fused_class(int tv, int B) {
+    if (tv != SCI_TV_VTV) return 1;
+    if (B <= 8) return 8;
+    if (B <= 10) return 10;
+    if (B <= 16) return 16;
+    if (B <= 24) return 24;
+    return 0;
+}
+
+void fused_class_dims(int cls, int* EH, int* EW) {
+    int h = 0, w = 0;
+    switch (cls) {
+        case 1: dims_of<CfgF1>(h, w); break;
+        case 8: dims_of<CfgV8>(h, w); break;
+        case 10: dims_of<CfgV10>(h, w); break;
+        case 16: dims_of<CfgV16>(h, w); break;
+        default: dims_of<CfgV24>(h, w); break;
+    }
+    *EH = h;
+    *EW = w;
+}
+
+namespace {
+std::atomic<unsigned long long> g_battr_done[64];
+
+template <typename T, int TV, class Cfg>
+bool launch_batched_cfg(int slot, const FusedArgs& a, const BatchItem<T>* items, int nitems, int total,
+                        int tpar, int spar, int want_x, cudaStream_t s) {
+    auto k = k_fgp_fused_batched<T, TV, Cfg>;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(g_battr_done[slot].load() & bit)) {
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM) != cudaSuccess)
+            return false;
+        g_battr_done[slot].fetch_or(bit);
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::max(1, std::min(sms, total));
+    k<<<grid, Cfg::NT, Cfg::SMEM, s>>>(a, items, nitems, total, tpar, spar, want_x);
+    return true;
+}
+
+template <typename T, int TV>
+bool launch_batched_tv(int cls, const FusedArgs& a, const BatchItem<T>* items, int nitems, int total, int tpar,
+                       int spar, int want_x, cudaStream_t s) {
+    if (TV != SCI_TV_VTV) return launch_batched_cfg<T, TV, CfgF1>(type_slot<T>(TV, 0), a, items, nitems, total,
+                                                                  tpar, spar, want_x, s);
+    switch (cls) {
+        case 8: return launch_batched_cfg<T, TV, CfgV8>(type_slot<T>(TV, 2), a, items, nitems, total, tpar, spar,
+                                                        want_x, s);
+        case 10: return launch_batched_cfg<T, TV, CfgV10>(type_slot<T>(TV, 3), a, items, nitems, total, tpar,
+                                                          spar, want_x, s);
+        case 16: return launch_batched_cfg<T, TV, CfgV16>(type_slot<T>(TV, 4), a, items, nitems, total, tpar,
+                                                          spar, want_x, s);
+        case 24: return launch_batched_cfg<T, TV, CfgV24>(type_slot<T>(TV, 5), a, items, nitems, total, tpar,
+                                                          spar, want_x, s);
+        default: return false;
+    }
+}
+}  // namespace
+
+template <typename T>
+bool launch_fgp_fused_batched(int tv, int cls, const FusedArgs& a, const BatchItem<T>* items, int nitems,
+                              int total, int tpar, int spar, int want_x, cudaStream_t s) {
+    switch (tv) {
+        case SCI_TV_ATV: return launch_batched_tv<T, SCI_TV_ATV>(cls, a, items, nitems, total, tpar, spar, want_x, s);
+        case SCI_TV_ITV2D:
+            return launch_batched_tv<T, SCI_TV_ITV2D>(cls, a, items, nitems, total, tpar, spar, want_x, s);
+        default: return launch_batched_tv<T, SCI_TV_VTV>(cls, a, items, nitems, total, tpar, spar, want_x, s);
+    }
 }
 
 template <typename T>
@@ -379,6 +539,14 @@ bool launch_fgp_fused(int tv, const FusedArgs& a, const FusedBufs<T>& b, cudaStr
         default: return launch_tv<T, SCI_TV_VTV>(a, b, s);
     }
 }
+
+#define SCI_INST_B(T)                                                                                 \
+    template bool launch_fgp_fused_batched<T>(int, int, const FusedArgs&, const BatchItem<T>*, int, int, int, \
+                                              int, int, cudaStream_t);
+SCI_INST_B(float)
+SCI_INST_B(__nv_bfloat16)
+SCI_INST_B(__half)
+#undef SCI_INST_B
 
 template bool launch_fgp_fused<float>(int, const FusedArgs&, const FusedBufs<float>&, cudaStream_t);
 template bool launch_fgp_fused<__nv_bfloat16>(int, const FusedArgs&, const FusedBufs<__nv_bfloat16>&,

@@ -98,8 +98,33 @@ struct FusedBufs {
     const T* st_in[4];  // carried p_h, p_v, w_h, w_v (read by non-first launches)
     T* st_out[4];       // must not alias st_in (written by non-last launches)
 };
+// One problem of a batched launch (device-resident table entry).
+template <typename T>
+struct BatchItem {
+    Geo g;
+    int cls;                 // tile configuration class (fused_class)
+    int tiles_x, tiles_y;    // tile grid per frame (one-frame classes) or per problem
+    int cta_begin;           // first fused work item of this problem
+    int pix_begin;           // first 256-pixel block of this problem (pixel kernels)
+    const float* y;
+    const uint32_t* bits;
+    float* rinv;             // 1/R (pseudo-inverse)
+    float* r;                // residual field
+    float* x_out;            // optional FP32 x^(T)
+    float* theta_user;       // the caller's FP32 theta
+    T* theta[2];             // ping-pong theta buffers
+    T* xt;
+    T* st[2][4];             // ping-pong carried duals (p_h, p_v, w_h, w_v)
+};
 // Largest halo the fused kernel supports for this TV / frame count (0: none).
 int fused_max_halo(int tv, int B);
+// Tile configuration class for this TV / frame count (0: none) and its tile size.
+int fused_class(int tv, int B);
+void fused_class_dims(int cls, int* EH, int* EW);
+// One launch over every tile of the problems items[0..nitems) (all of class cls).
+template <typename T>
+bool launch_fgp_fused_batched(int tv, int cls, const FusedArgs& a, const BatchItem<T>* items, int nitems,
+                              int total, int tpar, int spar, int want_x, cudaStream_t s);
 template <typename T>
 bool launch_fgp_fused(int tv, const FusedArgs& a, const FusedBufs<T>& b, cudaStream_t s);
 

@@ -15,7 +15,8 @@ import torch
 __all__ = [
     "SciError", "TV", "DTYPE", "load", "sci_masks_pack", "sci_forward", "sci_adjoint",
     "sci_project", "sci_tv_prox", "sci_gap_tv", "sci_admm_tv", "sci_sqdiff_f64",
-    "sci_residual_f64", "sci_graph_cache_clear", "sci_tv_prox_noalloc", "sci_last_solve_launches", "sci_fused_updates", "Workspace", "SciParams",
+    "sci_residual_f64", "sci_graph_cache_clear", "sci_tv_prox_noalloc", "sci_last_solve_launches", "sci_fused_updates", "Batch", "SciProblem",
+    "sci_gap_tv_batched", "sci_last_batch_launches", "Workspace", "SciParams",
 ]
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsci.so")
@@ -40,6 +41,11 @@ class SciParams(C.Structure):
                 ("fuse_k", C.c_int), ("init", C.c_int), ("use_graph", C.c_int)]
 
 
+class SciProblem(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("B", C.c_int), ("y", C.c_void_p), ("bits", C.c_void_p),
+                ("theta", C.c_void_p), ("x_out", C.c_void_p)]
+
+
 _vp, _i, _f, _sz = C.c_void_p, C.c_int, C.c_float, C.c_size_t
 _SIGS = {
     "sci_status_str": (C.c_char_p, [_i]),
@@ -62,6 +68,10 @@ _SIGS = {
     "sci_tv_prox_noalloc_max_voxels": (C.c_longlong, []),
     "sci_last_solve_launches": (C.c_longlong, []),
     "sci_fused_updates": (_i, [_i, _i, _i, _i]),
+    "sci_gap_tv_batched_workspace": (_sz, [C.POINTER(SciProblem), _i, C.POINTER(SciParams)]),
+    "sci_gap_tv_batched": (_i, [C.POINTER(SciProblem), _i, C.POINTER(SciParams), _vp, _sz, _vp]),
+    "sci_last_batch_launches": (C.c_longlong, []),
+    "sci_batch_graph_cache_clear": (None, []),
 }
 
 
@@ -249,6 +259,50 @@ def sci_gap_tv(y, bits, B, tv, lam, outer, inner, **kw):
 def sci_admm_tv(y, bits, B, tv, lam, rho, outer, inner, **kw):
     """ADMM-TV (Eqs. 24-26).  Returns (x^(T), theta^(T), u^(T), resid-or-None)."""
     return _solve(True, y, bits, B, tv, lam, outer, inner, rho=rho, **kw)
+
+
+class Batch:
+    """Descriptors for sci_gap_tv_batched, kept alive with their buffers.
+
+    ys: list of float32 [nx][ny] measurements; bits: list of packed masks;
+    Bs: frame counts.  theta / x_out buffers are allocated once here, so
+    repeated solves reuse them (and the library's cached CUDA graph).
+    """
+
+    def __init__(self, ys, bits, Bs, x_out=True):
+        if not (len(ys) == len(bits) == len(Bs)) or not ys:
+            raise ValueError("ys, bits and Bs must be non-empty lists of the same length")
+        _need_cuda(*ys, *bits)
+        self.ys, self.bits, self.Bs = list(ys), list(bits), [int(b) for b in Bs]
+        dev = ys[0].device
+        self.thetas = [torch.empty((b, *y.shape), dtype=torch.float32, device=dev) for y, b in zip(ys, Bs)]
+        self.x_outs = ([torch.empty_like(t) for t in self.thetas] if x_out else [None] * len(ys))
+        arr = (SciProblem * len(ys))()
+        for k, (y, bb, b, th, xo) in enumerate(zip(self.ys, self.bits, self.Bs, self.thetas, self.x_outs)):
+            arr[k] = SciProblem(y.shape[0], y.shape[1], b, y.data_ptr(), bb.data_ptr(), th.data_ptr(),
+                                None if xo is None else xo.data_ptr())
+        self.problems = arr
+        self.work = Workspace(dev)
+        self.device = dev
+
+
+def sci_gap_tv_batched(batch: Batch, tv, lam, outer, inner, storage="f32", init=True, fuse_k=0,
+                       use_graph=True):
+    """GAP-TV on every measurement of `batch` (results in batch.x_outs / batch.thetas)."""
+    prm = _params(tv, lam, 0.0, outer, inner, storage, fuse_k, init, use_graph)
+    lib = load()
+    n = len(batch.ys)
+    need = lib.sci_gap_tv_batched_workspace(batch.problems, n, C.byref(prm))
+    if need == 0:
+        raise SciError("sci_gap_tv_batched_workspace", 1)
+    wbuf = batch.work.get(need)
+    _check("sci_gap_tv_batched", lib.sci_gap_tv_batched(batch.problems, n, C.byref(prm), _ptr(wbuf),
+                                                        wbuf.numel(), _stream(batch.device)))
+    return batch.x_outs, batch.thetas
+
+
+def sci_last_batch_launches() -> int:
+    return int(load().sci_last_batch_launches())
 
 
 def sci_graph_cache_clear():

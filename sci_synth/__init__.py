@@ -58,15 +58,22 @@ def video(nx: int, ny: int, B: int, rng) -> np.ndarray:
         phi = rng.uniform(0.0, 2.0 * np.pi)
         vel = rng.choice(np.array([-3, -2, -1, 1, 2, 3]), size=2)
         ca, sa = np.cos(ang), np.sin(ang)
+        tex = 0.5 + 0.25 * np.sin(2.0 * np.pi * (fx * ii + fy * jj) + phi)
+        tex = 0.3 + 0.7 * (tex - 0.25) / 0.5  # [0.25, 0.75] -> [0.3, 1.0]
+        reach = max(ra, rb) + 2.0
         for k in range(B):
-            di = ii - (ci + vel[0] * k)
-            dj = jj - (cj + vel[1] * k)
+            c0, c1 = ci + vel[0] * k, cj + vel[1] * k
+            i0, i1 = max(0, int(np.floor(c0 - reach))), min(nx, int(np.ceil(c0 + reach)) + 1)
+            j0, j1 = max(0, int(np.floor(c1 - reach))), min(ny, int(np.ceil(c1 + reach)) + 1)
+            if i0 >= i1 or j0 >= j1:
+                continue
+            di = ii[i0:i1] - c0
+            dj = jj[:, j0:j1] - c1
             u = (ca * di + sa * dj) / ra
             v = (-sa * di + ca * dj) / rb
             inside = (u * u + v * v) <= 1.0
-            tex = 0.5 + 0.25 * np.sin(2.0 * np.pi * (fx * ii + fy * jj) + phi)
-            tex = 0.3 + 0.7 * (tex - 0.25) / 0.5  # [0.25, 0.75] -> [0.3, 1.0]
-            out[k] = np.where(inside, tex, out[k])
+            blk = out[k, i0:i1, j0:j1]
+            out[k, i0:i1, j0:j1] = np.where(inside, tex[i0:i1, j0:j1], blk)
     return np.clip(out, 0.0, 1.0)
 
 
