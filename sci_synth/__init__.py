@@ -23,7 +23,7 @@ import numpy as np
 
 __all__ = [
     "Case", "CONFIGS", "video", "masks_bernoulli", "masks_shifted", "noise",
-    "make_case", "pack_mask_bits",
+    "make_case", "pack_mask_bits", "batch_sizes", "masks_and_noise_torch",
 ]
 
 
@@ -118,6 +118,24 @@ def pack_mask_bits(masks: np.ndarray) -> np.ndarray:
     for k in range(B):
         words |= masks[k].astype(np.uint64) << np.uint64(k)
     return words.astype(np.uint32)
+
+
+def batch_sizes(count: int, sizes, seed: int):
+    """Sizes of `count` measurements drawn uniformly (seeded) from `sizes`."""
+    rng = np.random.default_rng(np.random.SeedSequence(seed).spawn(4)[3])
+    return [tuple(sizes[i]) for i in rng.integers(0, len(sizes), size=count)]
+
+
+def masks_and_noise_torch(nx: int, ny: int, B: int, sigma: float, seed: int, device):
+    """Bernoulli(0.5) masks (uint8 [B][nx][ny]) and N(0, sigma^2) noise
+    ([nx][ny] float32) drawn on `device` from a seeded torch generator, for
+    workloads too large to draw on the host."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    m = (torch.rand((B, nx, ny), generator=gen, device=device) < 0.5).to(torch.uint8)
+    g = torch.randn((nx, ny), generator=gen, device=device) * sigma
+    return m, g
 
 
 @dataclasses.dataclass(frozen=True)

@@ -73,6 +73,6 @@ def test_2048x2048x32_reduced_precision_storage(pkg):
     # noise-free: the FP32 output satisfies Phi x = y on covered pixels
     x32 = res["f32"][0]
     yy = pkg.sci_forward(x32, bits)
-    R = torch.from_numpy(case.masks.sum(0)).to(y.device)
+    R = torch.from_numpy(case.masks.sum(0).astype(np.int32)).to(y.device)
     err = (yy - y).abs()[R > 0].max().item()
     assert err <= 1e-4
