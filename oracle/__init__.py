@@ -6,3 +6,4 @@ never calls it, and it never calls the CUDA library: the two share no code.
 """
 from .sci_oracle import *  # noqa: F401,F403
 from .sci_oracle import __all__  # noqa: F401
+from . import lprox_oracle  # noqa: F401
