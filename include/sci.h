@@ -181,6 +181,59 @@ long long sci_last_batch_launches(void);
 /* Release every CUDA graph cached by sci_gap_tv_batched. */
 void sci_batch_graph_cache_clear(void);
 
+/* ---------------------------------------------------------------------------
+ * Learned TV prox (no counterpart in the paper, whose Sec. 4 points at
+ * plug-and-play reconstruction as future work): theta = x + f(x), f a
+ * 4-layer 3x3x3 convolutional network 1 -> 32 -> 32 -> 32 -> 1 with ReLU
+ * between layers and zero padding over (frame, row, column).  BF16 weights
+ * and activations, FP32 accumulation; the 32 -> 32 layers run on the tensor
+ * cores (tcgen05).  It stands in for S FGP dual updates inside GAP-TV.
+ *
+ * params: FP32 [sci_lprox_param_count()] = w1 [27][32][1], b1 [32],
+ *   w2 [27][32][32], b2 [32], w3 [27][32][32], b3 [32], w4 [27][1][32], b4 [1];
+ *   tap = (dz+1)*9 + (dy+1)*3 + (dx+1);
+ *   out[v][o] = b[o] + sum_tap sum_i w[tap][o][i] in[v + (dz,dy,dx)][i].
+ * x, theta, target: float32 [count][B][nx][ny] (count volumes).
+ * ------------------------------------------------------------------------- */
+size_t sci_lprox_param_count(void);
+
+/* Scratch bytes for sci_lprox_apply (training = 0) or the training calls (1). */
+size_t sci_lprox_workspace(int nx, int ny, int B, int count, int training);
+
+/* theta = x + f(x) for `count` volumes. */
+sci_status sci_lprox_apply(const float* params, const float* x, int nx, int ny, int B, int count,
+                           float* theta, void* work, size_t work_bytes, sci_stream_t stream);
+
+/*
+ * One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected; `step`
+ * counts from 1) on the mean squared error between x + f(x) and target.
+ * params, adam_m, adam_v: FP32 [param_count], updated in place.  loss:
+ * optional device double receiving the sum of squared errors (before the step).
+ */
+sci_status sci_lprox_train_step(float* params, float* adam_m, float* adam_v, int step, float lr,
+                                const float* x, const float* target, int nx, int ny, int B, int count,
+                                double* loss, void* work, size_t work_bytes, sci_stream_t stream);
+
+/* Gradient of that loss with respect to params (FP32 [param_count]), no update. */
+sci_status sci_lprox_grads(const float* params, const float* x, const float* target, int nx, int ny,
+                           int B, int count, float* grad, double* loss, void* work, size_t work_bytes,
+                           sci_stream_t stream);
+
+/* Device int in `work` that the tensor-core kernel sets to 1 if a bounded wait
+ * gave up (cleared at the start of each call above); read after a sync. */
+sci_status sci_lprox_error_word(void* work, size_t work_bytes, int nx, int ny, int B, int count,
+                                int training, int** out);
+
+/*
+ * The tensor-core building block: a 3x3x3 convolution with 32 input and 32
+ * output channels over channels-last BF16 activations [nvol][D][H][W][32]
+ * (zero padding), weights BF16 [27][32 out][32 in], FP32 accumulation,
+ * output BF16 (relu != 0: + bias[32], then ReLU).  act, w 16-byte aligned.
+ * err: device int set to 1 if a bounded wait inside the kernel gave up.
+ */
+sci_status sci_conv3d_c32_bf16(const void* act, const void* w, const float* bias, int relu, int nvol,
+                               int D, int H, int W, void* out, int* err, sci_stream_t stream);
+
 /* Release every CUDA graph the solver has cached (call before freeing buffers
  * whose addresses an earlier solve used, if the same addresses may be reused
  * with different contents sizes or parameters; safe at any time). */

@@ -1,0 +1,388 @@
+// 3x3x3 convolution with 32 input and 32 output channels on the 5th-generation
+// tensor cores (tcgen05), BF16 operands, FP32 accumulation in tensor memory.
+// Used by the learned TV prox (its two hidden 32->32 layers, forward and
+// input-gradient passes).
+//
+// Implicit GEMM: an output tile is 128 voxels (BH rows x BW columns of one
+// frame of one volume) x 32 output channels.  For each of the 27 taps the
+// A operand is the 128 x 32 block of input activations shifted by the tap --
+// one TMA box of a 5-D tensor map over the channels-last activations
+// [volume][frame][row][column][channel]; out-of-range voxels arrive as zeros,
+// which is the convolution's zero padding -- and the B operand is that tap's
+// 32 x 32 weight block, resident in shared memory for the whole kernel.  Each
+// tap is two tcgen05.mma (M = 128, N = 32, K = 16) accumulating into one
+// 128-lane x 32-column FP32 tile of tensor memory.
+//
+// One thread drives a ring of A stages (TMA load -> MMA -> commit frees the
+// stage); four warps then read the accumulator with tcgen05.ld (warp w owns
+// lanes 32w..32w+31, i.e. voxels 32w..32w+31 of the tile) and apply the
+// epilogue.  Every mbarrier wait is bounded: on timeout the kernel records
+// an error code, stops issuing work, frees its tensor memory and returns.
+#include <cuda.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "sci_internal.cuh"
+
+namespace sci {
+
+namespace {
+
+constexpr int kStages = 4;
+constexpr int kTileM = 128;
+constexpr int kC = 32;
+constexpr uint32_t kABytes = kTileM * kC * 2;      // 8 KB per A stage
+constexpr uint32_t kWTapBytes = kC * kC * 2;       // 2 KB per tap
+constexpr uint32_t kWBytes = 27 * kWTapBytes;      // 54 KB
+constexpr long long kSpinLimit = 1LL << 26;        // bounded mbarrier waits
+
+// ---- PTX helpers --------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Wait for the phase with the given parity; false if the spin limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (long long it = 0; it < kSpinLimit; ++it) {
+        uint32_t done = 0;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1,
+                                            int c2, int c3, int c4) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6, "
+        "%7}], [%2];" ::"r"(dst),
+        "l"(map), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1,
+                                            int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+        "[%2];" ::"r"(dst),
+        "l"(map), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+// K-major operand in the 64-byte swizzled layout (rows of 32 BF16 = 64 B,
+// 8-row groups 512 B apart), as written by TMA with 64-byte swizzling.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);   // start address
+    d |= (uint64_t)(16u >> 4) << 16;           // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(512u >> 4) << 32;          // stride byte offset: 8 rows x 64 B
+    d |= (uint64_t)1 << 46;                    // descriptor version
+    d |= (uint64_t)4 << 61;                    // layout: 64-byte swizzle
+    return d;
+}
+
+// kind::f16 instruction descriptor: D = FP32, A = B = BF16, both K-major, M = 128, N = 32.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kC >> 3) << 17) |
+                            ((uint32_t)(kTileM >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_32cols(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct ConvTcArgs {
+    int nvol, D, H, W;      // volumes and their frames x rows x columns
+    int BW, BH;             // tile: BH rows x BW columns (BW * BH = 128)
+    int tiles_w, tiles_h;   // tiles per row block / per frame
+    long long ntiles;
+    int mode;               // ConvEpilogue
+    const float* bias;      // [32] (forward)
+    const __nv_bfloat16* mask_act;  // input-gradient mode: zero where this activation is <= 0
+    __nv_bfloat16* out;     // [nvol][D][H][W][32]
+    int* err;               // set to 1 on a wait timeout
+};
+
+__global__ void __launch_bounds__(128, 1)
+k_conv3d_c32_tc(const __grid_constant__ CUtensorMap act_map, const __grid_constant__ CUtensorMap w_map,
+                ConvTcArgs a) {
+    extern __shared__ __align__(1024) unsigned char dsmem[];
+    // 1024-byte aligned carve-up: weights, A stages, barriers
+    unsigned char* base = (unsigned char*)(((uintptr_t)dsmem + 1023) & ~(uintptr_t)1023);
+    unsigned char* s_w = base;                       // 27 x 2 KB
+    unsigned char* s_a = base + kWBytes;             // kStages x 8 KB (kWBytes is a multiple of 1024)
+    uint64_t* bars = reinterpret_cast<uint64_t*>(s_a + kStages * kABytes);
+    // bars: [0, kStages) full, [kStages, 2 kStages) empty, then weights, accumulator, drain
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 3);
+    volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t bar_full = smem_u32(bars), bar_empty = smem_u32(bars + kStages);
+    const uint32_t bar_w = smem_u32(bars + 2 * kStages), bar_acc = smem_u32(bars + 2 * kStages + 1);
+    const uint32_t bar_drain = smem_u32(bars + 2 * kStages + 2);
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(bar_full + 8 * s, 1);
+            mbar_init(bar_empty + 8 * s, 1);
+        }
+        mbar_init(bar_w, 1);
+        mbar_init(bar_acc, 1);
+        mbar_init(bar_drain, 1);
+        *s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(s_tmem))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *s_tmem;
+
+    // weights: 27 TMA boxes of 32 x 32
+    if (tid == 0) {
+        mbar_expect_tx(bar_w, kWBytes);
+        for (int t = 0; t < 27; ++t) tma_load_3d(smem_u32(s_w + t * kWTapBytes), &w_map, bar_w, 0, 0, t);
+        if (!mbar_wait(bar_w, 0)) {
+            *s_abort = 1;
+            atomicExch(a.err, 1);
+        }
+    }
+    __syncthreads();
+
+    uint32_t q = 0;          // A loads issued so far (ring sequence number)
+    uint32_t acc_phase = 0;  // accumulator barrier phase
+    for (long long tile = blockIdx.x; tile < a.ntiles && !*s_abort; tile += gridDim.x) {
+        long long tr = tile;
+        const int tw = (int)(tr % a.tiles_w); tr /= a.tiles_w;
+        const int th = (int)(tr % a.tiles_h); tr /= a.tiles_h;
+        const int z = (int)(tr % a.D);
+        const int vol = (int)(tr / a.D);
+        const int w0 = tw * a.BW, h0 = th * a.BH;
+
+        if (tid == 0) {
+            bool ok = true;
+            int produced = 0, consumed = 0;
+            // software pipeline: load tap t + kStages - 1 while the MMAs of tap t run
+            for (int step = 0; step < 27 + kStages - 1 && ok; ++step) {
+                if (step < 27) {  // produce tap `step`
+                    const uint32_t qq = q + step, s = qq % kStages, use = qq / kStages;
+                    if (use > 0 && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1)) { ok = false; break; }
+                    const int dz = step / 9 - 1, dy = (step / 3) % 3 - 1, dx = step % 3 - 1;
+                    mbar_expect_tx(bar_full + 8 * s, kABytes);
+                    tma_load_5d(smem_u32(s_a + s * kABytes), &act_map, bar_full + 8 * s, 0, w0 + dx, h0 + dy,
+                                z + dz, vol);
+                    produced = step + 1;
+                }
+                const int t = step - (kStages - 1);
+                if (t >= 0) {  // consume tap t
+                    const uint32_t qq = q + t, s = qq % kStages, use = qq / kStages;
+                    if (!mbar_wait(bar_full + 8 * s, use & 1)) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t abase = smem_u32(s_a + s * kABytes), bbase = smem_u32(s_w + t * kWTapBytes);
+                    umma_bf16(tmem, smem_desc_sw64(abase), smem_desc_sw64(bbase), t > 0 ? 1u : 0u);
+                    umma_bf16(tmem, smem_desc_sw64(abase + 32), smem_desc_sw64(bbase + 32), 1u);
+                    umma_commit(bar_empty + 8 * s);
+                    consumed = t + 1;
+                }
+            }
+            if (ok) {
+                umma_commit(bar_acc);
+            } else {
+                // drain before giving up: copies still in flight, then every issued MMA
+                for (int t = consumed; t < produced; ++t) {
+                    const uint32_t qq = q + t;
+                    mbar_wait(bar_full + 8 * (qq % kStages), (qq / kStages) & 1);
+                }
+                umma_commit(bar_drain);
+                mbar_wait(bar_drain, 0);
+                *s_abort = 1;
+                atomicExch(a.err, 1);
+            }
+            q += 27;
+        }
+        __syncthreads();
+        if (*s_abort) break;
+        // every thread waits for the accumulator, then reads its row
+        const bool got = mbar_wait(bar_acc, acc_phase & 1);
+        acc_phase++;
+        if (!got) {
+            *s_abort = 1;
+            atomicExch(a.err, 1);
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (got) {
+            float v[32];
+            tmem_ld_32cols(tmem + ((uint32_t)(warp * 32) << 16), v);
+            const int r = tid;  // tile row = voxel
+            const int hh = h0 + r / a.BW, ww = w0 + r % a.BW;
+            if (hh < a.H && ww < a.W) {
+                const long long vox = (((long long)vol * a.D + z) * a.H + hh) * a.W + ww;
+                __nv_bfloat16* dst = a.out + vox * kC;
+                if (a.mode == 0) {  // forward: bias + ReLU
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) v[c] = fmaxf(v[c] + a.bias[c], 0.f);
+                } else if (a.mode == 1) {  // input gradient masked by the activation's ReLU
+                    const __nv_bfloat16* m = a.mask_act + vox * kC;
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) v[c] = __bfloat162float(m[c]) > 0.f ? v[c] : 0.f;
+                }
+                uint4 pk[4];
+                uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
+                    pw[c] = *reinterpret_cast<uint32_t*>(&h2);
+                }
+                uint4* d4 = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) d4[c] = pk[c];
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    // drain: the last MMAs' commits may still be pending on the empty barriers;
+    // the accumulator barrier covered them on the success path.
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+    }
+}
+
+// ---- host: tensor maps ---------------------------------------------------
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encode_fn() {
+    static EncodeFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+    });
+    return fn;
+}
+
+}  // namespace
+
+size_t conv3d_c32_tc_smem() { return kWBytes + kStages * kABytes + 1024 + 256; }
+
+// out[vol][z][h][w][:] = epilogue(sum_tap W[tap] * act[vol][z+dz][h+dy][w+dx][:]).
+// act, out: BF16 [nvol][D][H][W][32]; w: BF16 [27][32 out][32 in].
+// mode 0: + bias, ReLU; mode 1: x (mask_act > 0); mode 2: plain.
+bool launch_conv3d_c32_tc(const __nv_bfloat16* act, const __nv_bfloat16* w, const float* bias,
+                          const __nv_bfloat16* mask_act, int mode, int nvol, int D, int H, int W,
+                          __nv_bfloat16* out, int* err, cudaStream_t s) {
+    EncodeFn enc = encode_fn();
+    if (enc == nullptr) return false;
+    ConvTcArgs a{};
+    a.nvol = nvol;
+    a.D = D;
+    a.H = H;
+    a.W = W;
+    a.BW = W <= 64 ? 64 : 128;
+    a.BH = kTileM / a.BW;
+    a.tiles_w = (W + a.BW - 1) / a.BW;
+    a.tiles_h = (H + a.BH - 1) / a.BH;
+    a.ntiles = (long long)nvol * D * a.tiles_h * a.tiles_w;
+    a.mode = mode;
+    a.bias = bias;
+    a.mask_act = mask_act;
+    a.out = out;
+    a.err = err;
+    if (((uintptr_t)act & 15) != 0 || ((uintptr_t)w & 15) != 0) return false;
+
+    CUtensorMap amap, wmap;
+    std::memset(&amap, 0, sizeof(amap));
+    std::memset(&wmap, 0, sizeof(wmap));
+    const cuuint64_t adims[5] = {(cuuint64_t)kC, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)nvol};
+    const cuuint64_t astr[4] = {(cuuint64_t)kC * 2, (cuuint64_t)W * kC * 2, (cuuint64_t)H * W * kC * 2,
+                                (cuuint64_t)D * H * W * kC * 2};
+    const cuuint32_t abox[5] = {(cuuint32_t)kC, (cuuint32_t)a.BW, (cuuint32_t)a.BH, 1, 1};
+    const cuuint32_t ones[5] = {1, 1, 1, 1, 1};
+    if (enc(&amap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(act), adims, astr, abox, ones,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    const cuuint64_t wdims[3] = {(cuuint64_t)kC, (cuuint64_t)kC, 27};
+    const cuuint64_t wstr[2] = {(cuuint64_t)kC * 2, (cuuint64_t)kC * kC * 2};
+    const cuuint32_t wbox[3] = {(cuuint32_t)kC, (cuuint32_t)kC, 1};
+    if (enc(&wmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(w), wdims, wstr, wbox, ones,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+
+    static bool attr = false;
+    const size_t smem = conv3d_c32_tc_smem();
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_conv3d_c32_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return false;
+        attr = true;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long grid = std::min<long long>(a.ntiles, (long long)sms * 2);
+    k_conv3d_c32_tc<<<(unsigned)grid, 128, smem, s>>>(amap, wmap, a);
+    return true;
+}
+
+}  // namespace sci
+
+extern "C" sci_status sci_conv3d_c32_bf16(const void* act, const void* w, const float* bias, int relu, int nvol,
+                                          int D, int H, int W, void* out, int* err, sci_stream_t stream) {
+    if (act == nullptr || w == nullptr || out == nullptr || err == nullptr || act == out) return SCI_ERR_ARG;
+    if (nvol <= 0 || D <= 0 || H <= 0 || W <= 0 || (relu && bias == nullptr)) return SCI_ERR_ARG;
+    if ((double)nvol * D * H * W > 2.0e9) return SCI_ERR_SHAPE;
+    if (!sci::launch_conv3d_c32_tc(static_cast<const __nv_bfloat16*>(act), static_cast<const __nv_bfloat16*>(w),
+                                   bias, nullptr, relu ? 0 : 2, nvol, D, H, W, static_cast<__nv_bfloat16*>(out), err,
+                                   (cudaStream_t)stream))
+        return SCI_ERR_CUDA;
+    return sci::check_launch();
+}

@@ -1,0 +1,449 @@
+// Learned TV prox: theta = x + f(x), f a 4-layer 3x3x3 convolutional network
+// (1 -> 32 -> 32 -> 32 -> 1 channels, ReLU between layers, zero "same"
+// padding over frame, row and column), BF16 weights and activations with
+// FP32 accumulation, FP32 master weights trained with Adam.
+//
+// The two 32 -> 32 layers (97% of the arithmetic) run on the tensor cores
+// (sci_conv_tc.cu), forward and input-gradient.  The 1-channel layers, the
+// weight gradients and the optimizer run on the CUDA cores here.
+//
+// The paper has no learned component (its future-work paragraph points at
+// plug-and-play reconstruction); this network stands in for S FGP dual
+// updates inside GAP-TV and is trained on (x, FGP_S(x)) pairs that the plain
+// method produces.
+//
+// Parameters (FP32, contiguous): w1 [27][32][1], b1 [32], w2 [27][32][32],
+// b2 [32], w3 [27][32][32], b3 [32], w4 [27][1][32], b4 [1]; tap index
+// (dz+1)*9 + (dy+1)*3 + (dx+1); layer l computes
+// out[v][o] = b[o] + sum_tap sum_i w[tap][o][i] * in[v + offset(tap)][i].
+#include <cmath>
+#include <cstring>
+
+#include "sci_internal.cuh"
+
+namespace sci {
+
+bool launch_conv3d_c32_tc(const __nv_bfloat16* act, const __nv_bfloat16* w, const float* bias,
+                          const __nv_bfloat16* mask_act, int mode, int nvol, int D, int H, int W,
+                          __nv_bfloat16* out, int* err, cudaStream_t s);
+
+namespace {
+
+constexpr int C = 32;
+constexpr size_t kW1 = 0, kB1 = 864, kW2 = 896, kB2 = kW2 + 27648, kW3 = kB2 + 32, kB3 = kW3 + 27648,
+                 kW4 = kB3 + 32, kB4 = kW4 + 864, kParams = kB4 + 1;
+
+struct Vol {
+    int nvol, D, H, W;
+    long long V;  // voxels
+};
+
+// neighbour (z+dz, y+dy, x+dx) of voxel (n, z, y, x), or -1 outside the volume
+__device__ __forceinline__ long long nb(const Vol& g, int n, int z, int y, int x, int tap) {
+    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    const int zz = z + dz, yy = y + dy, xx = x + dx;
+    if (zz < 0 || zz >= g.D || yy < 0 || yy >= g.H || xx < 0 || xx >= g.W) return -1;
+    return (((long long)n * g.D + zz) * g.H + yy) * g.W + xx;
+}
+
+__device__ __forceinline__ void decomp(const Vol& g, long long v, int& n, int& z, int& y, int& x) {
+    x = (int)(v % g.W);
+    long long t = v / g.W;
+    y = (int)(t % g.H);
+    t /= g.H;
+    z = (int)(t % g.D);
+    n = (int)(t / g.D);
+}
+
+__device__ __forceinline__ void load32(const __nv_bfloat16* p, float (&a)[32]) {
+    const uint4* p4 = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        uint4 u = p4[c];
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float2 f = __bfloat1622float2(h[k]);
+            a[8 * c + 2 * k] = f.x;
+            a[8 * c + 2 * k + 1] = f.y;
+        }
+    }
+}
+
+__device__ __forceinline__ void store32(__nv_bfloat16* p, const float (&a)[32]) {
+    uint4 pk[4];
+    uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+        __nv_bfloat162 h2 = __floats2bfloat162_rn(a[2 * c], a[2 * c + 1]);
+        pw[c] = *reinterpret_cast<uint32_t*>(&h2);
+    }
+    uint4* d = reinterpret_cast<uint4*>(p);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) d[c] = pk[c];
+}
+
+// BF16 copies of the 32 -> 32 weights: forward [tap][o][i] and, for the
+// input gradient, the tap-reversed transpose wt[tap][i][o] = w[26 - tap][o][i].
+__global__ void k_prep_weights(const float* __restrict__ prm, __nv_bfloat16* __restrict__ w2, __nv_bfloat16* w2t,
+                               __nv_bfloat16* __restrict__ w3, __nv_bfloat16* w3t) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 27 * C * C) return;
+    const int tap = idx / (C * C), o = (idx / C) % C, i = idx % C;
+    const int tidx = (26 - tap) * C * C + i * C + o;
+    w2[idx] = __float2bfloat16_rn(prm[kW2 + idx]);
+    w3[idx] = __float2bfloat16_rn(prm[kW3 + idx]);
+    if (w2t) w2t[tidx] = __float2bfloat16_rn(prm[kW2 + idx]);
+    if (w3t) w3t[tidx] = __float2bfloat16_rn(prm[kW3 + idx]);
+}
+
+// layer 1 (1 -> 32) + ReLU: one thread per voxel.  Weights are rounded to
+// BF16 like the other layers' operands.
+__global__ void k_conv_in(const float* __restrict__ x, const float* __restrict__ prm, Vol g,
+                          __nv_bfloat16* __restrict__ act1) {
+    __shared__ float sw[27 * C + C];
+    for (int i = threadIdx.x; i < 27 * C; i += blockDim.x)
+        sw[i] = __bfloat162float(__float2bfloat16_rn(prm[kW1 + i]));
+    for (int i = threadIdx.x; i < C; i += blockDim.x) sw[27 * C + i] = prm[kB1 + i];
+    __syncthreads();
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= g.V) return;
+    int n, z, y, xx;
+    decomp(g, v, n, z, y, xx);
+    float acc[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) acc[c] = sw[27 * C + c];
+    for (int t = 0; t < 27; ++t) {
+        const long long u = nb(g, n, z, y, xx, t);
+        if (u < 0) continue;
+        const float xv = __bfloat162float(__float2bfloat16_rn(x[u]));
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc[c] = fmaf(sw[t * C + c], xv, acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 32; ++c) acc[c] = fmaxf(acc[c], 0.f);
+    store32(act1 + v * C, acc);
+}
+
+// layer 4 (32 -> 1) and the residual output theta = x + f.  With a target,
+// also g = d loss / d f = 2 (theta - target) / n and per-block FP64 partial
+// sums of (theta - target)^2.
+__global__ void k_conv_out(const __nv_bfloat16* __restrict__ act3, const float* __restrict__ prm, Vol g,
+                           const float* __restrict__ x, float* __restrict__ theta, const float* __restrict__ target,
+                           float* __restrict__ g4, double* __restrict__ partials) {
+    __shared__ float sw[27 * C + 1];
+    for (int i = threadIdx.x; i < 27 * C; i += blockDim.x)
+        sw[i] = __bfloat162float(__float2bfloat16_rn(prm[kW4 + i]));
+    if (threadIdx.x == 0) sw[27 * C] = prm[kB4];
+    __syncthreads();
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double d2 = 0.0;
+    if (v < g.V) {
+        int n, z, y, xx;
+        decomp(g, v, n, z, y, xx);
+        float acc = sw[27 * C];
+        for (int t = 0; t < 27; ++t) {
+            const long long u = nb(g, n, z, y, xx, t);
+            if (u < 0) continue;
+            float a[32];
+            load32(act3 + u * C, a);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) acc = fmaf(sw[t * C + c], a[c], acc);
+        }
+        const float th = x[v] + acc;
+        if (theta) theta[v] = th;
+        if (target) {
+            const float d = th - target[v];
+            g4[v] = 2.f * d / (float)g.V;
+            d2 = (double)d * (double)d;
+        }
+    }
+    if (partials) {
+        d2 = block_sum(d2);
+        if (threadIdx.x == 0) partials[blockIdx.x] = d2;
+    }
+}
+
+// d loss / d act3 through layer 4, masked by act3's ReLU:
+// g3[u][i] = (act3[u][i] > 0) sum_tap w4[tap][i] g4[u - offset(tap)]
+__global__ void k_dgrad_out(const float* __restrict__ g4, const float* __restrict__ prm, Vol g,
+                            const __nv_bfloat16* __restrict__ act3, __nv_bfloat16* __restrict__ g3) {
+    __shared__ float sw[27 * C];
+    for (int i = threadIdx.x; i < 27 * C; i += blockDim.x)
+        sw[i] = __bfloat162float(__float2bfloat16_rn(prm[kW4 + i]));
+    __syncthreads();
+    const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= g.V) return;
+    int n, z, y, xx;
+    decomp(g, u, n, z, y, xx);
+    float acc[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) acc[c] = 0.f;
+    for (int t = 0; t < 27; ++t) {
+        const long long v = nb(g, n, z, y, xx, 26 - t);  // u - offset(t)
+        if (v < 0) continue;
+        const float gv = g4[v];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc[c] = fmaf(sw[t * C + c], gv, acc[c]);
+    }
+    float a[32];
+    load32(act3 + u * C, a);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) acc[c] = a[c] > 0.f ? acc[c] : 0.f;
+    store32(g3 + u * C, acc);
+}
+
+// Weight and bias gradients of a 32 -> 32 layer:
+//   dw[tap][o][i] += sum_v gout[v][o] * ain[v + offset(tap)][i],  db[o] += sum_v gout[v][o]
+// Thread (o, i-quad) keeps 27 x 4 accumulators; a persistent grid walks the
+// voxels and each CTA adds its totals once (FP32 atomics).
+__global__ void __launch_bounds__(256) k_wgrad_c32(const __nv_bfloat16* __restrict__ gout,
+                                                   const __nv_bfloat16* __restrict__ ain, Vol g,
+                                                   float* __restrict__ dw, float* __restrict__ db) {
+    const int o = threadIdx.x >> 3, iq = (threadIdx.x & 7) * 4;
+    float acc[27][4];
+#pragma unroll
+    for (int t = 0; t < 27; ++t)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[t][k] = 0.f;
+    float bacc = 0.f;
+    for (long long v = blockIdx.x; v < g.V; v += gridDim.x) {
+        int n, z, y, xx;
+        decomp(g, v, n, z, y, xx);
+        const float go = __bfloat162float(gout[v * C + o]);
+        bacc += go;
+        if (go == 0.f) continue;
+#pragma unroll
+        for (int t = 0; t < 27; ++t) {
+            const long long u = nb(g, n, z, y, xx, t);
+            if (u < 0) continue;
+            const uint2 raw = *reinterpret_cast<const uint2*>(ain + u * C + iq);
+            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&raw);
+            const float2 f0 = __bfloat1622float2(h[0]), f1 = __bfloat1622float2(h[1]);
+            acc[t][0] = fmaf(go, f0.x, acc[t][0]);
+            acc[t][1] = fmaf(go, f0.y, acc[t][1]);
+            acc[t][2] = fmaf(go, f1.x, acc[t][2]);
+            acc[t][3] = fmaf(go, f1.y, acc[t][3]);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 27; ++t)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) atomicAdd(dw + (t * C + o) * C + iq + k, acc[t][k]);
+    if ((threadIdx.x & 7) == 0) atomicAdd(db + o, bacc);
+}
+
+// Weight and bias gradients of layer 1 (input x, one channel) and layer 4
+// (output one channel): thread t < 27*32 owns one weight.
+__global__ void k_wgrad_in(const __nv_bfloat16* __restrict__ g1, const float* __restrict__ x, Vol g,
+                           float* __restrict__ dw1, float* __restrict__ db1) {
+    const int idx = threadIdx.x;  // blockDim 32 * 28: rows 0..26 taps, row 27 bias
+    const int t = idx / C, o = idx % C;
+    float acc = 0.f;
+    for (long long v = blockIdx.x; v < g.V; v += gridDim.x) {
+        const float go = __bfloat162float(g1[v * C + o]);
+        if (t == 27) { acc += go; continue; }
+        int n, z, y, xx;
+        decomp(g, v, n, z, y, xx);
+        const long long u = nb(g, n, z, y, xx, t);
+        if (u >= 0) acc = fmaf(go, __bfloat162float(__float2bfloat16_rn(x[u])), acc);
+    }
+    if (t < 27) atomicAdd(dw1 + t * C + o, acc);
+    else atomicAdd(db1 + o, acc);
+}
+
+__global__ void k_wgrad_out(const float* __restrict__ g4, const __nv_bfloat16* __restrict__ act3, Vol g,
+                            float* __restrict__ dw4, float* __restrict__ db4) {
+    const int idx = threadIdx.x;  // rows 0..26 taps x 32 channels, then one bias thread
+    const int t = idx / C, i = idx % C;
+    float acc = 0.f;
+    for (long long v = blockIdx.x; v < g.V; v += gridDim.x) {
+        const float go = g4[v];
+        if (t == 27) { if (i == 0) acc += go; continue; }
+        int n, z, y, xx;
+        decomp(g, v, n, z, y, xx);
+        const long long u = nb(g, n, z, y, xx, t);
+        if (u >= 0) acc = fmaf(go, __bfloat162float(act3[u * C + i]), acc);
+    }
+    if (t < 27) atomicAdd(dw4 + t * C + i, acc);
+    else if (i == 0) atomicAdd(db4, acc);
+}
+
+// Adam on the FP32 master parameters (bias-corrected step size).
+__global__ void k_adam(float* __restrict__ prm, const float* __restrict__ grad, float* __restrict__ m,
+                       float* __restrict__ v, long long n, float lr_t, float b1, float b2, float eps) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = grad[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        prm[i] -= lr_t * mi / (sqrtf(vi) + eps);
+    }
+}
+
+struct LWork {
+    __nv_bfloat16 *a1, *a2, *a3, *ga, *gb, *w2, *w2t, *w3, *w3t;
+    float *g4, *grad;
+    double* partials;
+    int* err;
+    size_t total;
+};
+
+LWork lwork_layout(long long V, bool training, void* base) {
+    LWork L{};
+    size_t off = 0;
+    char* b = static_cast<char*>(base);
+    auto take = [&](size_t bytes) { char* p = b ? b + off : nullptr; off += align256(bytes); return p; };
+    L.a1 = reinterpret_cast<__nv_bfloat16*>(take((size_t)V * C * 2));
+    L.a2 = reinterpret_cast<__nv_bfloat16*>(take((size_t)V * C * 2));
+    L.a3 = reinterpret_cast<__nv_bfloat16*>(take((size_t)V * C * 2));
+    L.w2 = reinterpret_cast<__nv_bfloat16*>(take(27 * C * C * 2));
+    L.w3 = reinterpret_cast<__nv_bfloat16*>(take(27 * C * C * 2));
+    L.err = reinterpret_cast<int*>(take(256));
+    L.partials = reinterpret_cast<double*>(take((size_t)((V + 255) / 256 + 1) * 8));
+    if (training) {
+        L.ga = reinterpret_cast<__nv_bfloat16*>(take((size_t)V * C * 2));
+        L.gb = reinterpret_cast<__nv_bfloat16*>(take((size_t)V * C * 2));
+        L.w2t = reinterpret_cast<__nv_bfloat16*>(take(27 * C * C * 2));
+        L.w3t = reinterpret_cast<__nv_bfloat16*>(take(27 * C * C * 2));
+        L.g4 = reinterpret_cast<float*>(take((size_t)V * 4));
+        L.grad = reinterpret_cast<float*>(take(kParams * 4));
+    }
+    L.total = off;
+    return L;
+}
+
+int grid_for(long long V) { return (int)((V + 255) / 256); }
+
+// forward through the four layers; theta = x + f(x)
+bool enqueue_forward(const float* prm, const float* x, Vol g, const LWork& L, float* theta, const float* target,
+                     cudaStream_t s) {
+    k_prep_weights<<<(27 * C * C + 255) / 256, 256, 0, s>>>(prm, L.w2, L.w2t, L.w3, L.w3t);
+    k_conv_in<<<grid_for(g.V), 256, 0, s>>>(x, prm, g, L.a1);
+    if (!launch_conv3d_c32_tc(L.a1, L.w2, prm + kB2, nullptr, 0, g.nvol, g.D, g.H, g.W, L.a2, L.err, s))
+        return false;
+    if (!launch_conv3d_c32_tc(L.a2, L.w3, prm + kB3, nullptr, 0, g.nvol, g.D, g.H, g.W, L.a3, L.err, s))
+        return false;
+    k_conv_out<<<grid_for(g.V), 256, 0, s>>>(L.a3, prm, g, x, theta, target, target ? L.g4 : nullptr,
+                                             target ? L.partials : nullptr);
+    return true;
+}
+
+bool vol_ok(int nx, int ny, int B, int count) {
+    return nx > 0 && ny > 0 && B > 0 && count > 0 && (double)nx * ny * B * count < 2.0e9;
+}
+
+}  // namespace
+
+}  // namespace sci
+
+using namespace sci;
+
+extern "C" {
+
+size_t sci_lprox_param_count(void) { return kParams; }
+
+size_t sci_lprox_workspace(int nx, int ny, int B, int count, int training) {
+    if (!vol_ok(nx, ny, B, count)) return 0;
+    return lwork_layout((long long)nx * ny * B * count, training != 0, nullptr).total;
+}
+
+sci_status sci_lprox_apply(const float* params, const float* x, int nx, int ny, int B, int count, float* theta,
+                           void* work, size_t work_bytes, sci_stream_t stream) {
+    if (params == nullptr || x == nullptr || theta == nullptr || x == theta || !vol_ok(nx, ny, B, count))
+        return SCI_ERR_ARG;
+    const Vol g{count, B, nx, ny, (long long)nx * ny * B * count};
+    const LWork need = lwork_layout(g.V, false, nullptr);
+    if (work == nullptr || work_bytes < need.total || ((uintptr_t)work & 255u) != 0) return SCI_ERR_WORKSPACE;
+    const LWork L = lwork_layout(g.V, false, work);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaMemsetAsync(L.err, 0, sizeof(int), s);
+    if (!enqueue_forward(params, x, g, L, theta, nullptr, s)) return SCI_ERR_CUDA;
+    return check_launch();
+}
+
+sci_status sci_lprox_train_step(float* params, float* adam_m, float* adam_v, int step, float lr, const float* x,
+                                const float* target, int nx, int ny, int B, int count, double* loss,
+                                void* work, size_t work_bytes, sci_stream_t stream) {
+    if (params == nullptr || adam_m == nullptr || adam_v == nullptr || x == nullptr || target == nullptr ||
+        !vol_ok(nx, ny, B, count) || step < 1)
+        return SCI_ERR_ARG;
+    if (!std::isfinite(lr) || !(lr > 0.f)) return SCI_ERR_ARG;
+    const Vol g{count, B, nx, ny, (long long)nx * ny * B * count};
+    const LWork need = lwork_layout(g.V, true, nullptr);
+    if (work == nullptr || work_bytes < need.total || ((uintptr_t)work & 255u) != 0) return SCI_ERR_WORKSPACE;
+    const LWork L = lwork_layout(g.V, true, work);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaMemsetAsync(L.err, 0, sizeof(int), s);
+    if (!enqueue_forward(params, x, g, L, nullptr, target, s)) return SCI_ERR_CUDA;
+    if (loss != nullptr) launch_sum_partials(L.partials, grid_for(g.V), loss, s);
+    cudaMemsetAsync(L.grad, 0, kParams * 4, s);
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int wg = sms * 4;
+    // layer 4
+    k_wgrad_out<<<wg, 27 * C + C, 0, s>>>(L.g4, L.a3, g, L.grad + kW4, L.grad + kB4);
+    k_dgrad_out<<<grid_for(g.V), 256, 0, s>>>(L.g4, params, g, L.a3, L.ga);  // ga = g3
+    // layer 3
+    k_wgrad_c32<<<wg, 256, 0, s>>>(L.ga, L.a2, g, L.grad + kW3, L.grad + kB3);
+    if (!launch_conv3d_c32_tc(L.ga, L.w3t, nullptr, L.a2, 1, g.nvol, g.D, g.H, g.W, L.gb, L.err, s))
+        return SCI_ERR_CUDA;  // gb = g2
+    // layer 2
+    k_wgrad_c32<<<wg, 256, 0, s>>>(L.gb, L.a1, g, L.grad + kW2, L.grad + kB2);
+    if (!launch_conv3d_c32_tc(L.gb, L.w2t, nullptr, L.a1, 1, g.nvol, g.D, g.H, g.W, L.ga, L.err, s))
+        return SCI_ERR_CUDA;  // ga = g1
+    // layer 1
+    k_wgrad_in<<<wg, 28 * C, 0, s>>>(L.ga, x, g, L.grad + kW1, L.grad + kB1);
+    // Adam (beta1 0.9, beta2 0.999, eps 1e-8), bias-corrected step size
+    const double b1 = 0.9, b2 = 0.999;
+    const double lr_t = (double)lr * std::sqrt(1.0 - std::pow(b2, step)) / (1.0 - std::pow(b1, step));
+    k_adam<<<64, 256, 0, s>>>(params, L.grad, adam_m, adam_v, (long long)kParams, (float)lr_t, 0.9f, 0.999f, 1e-8f);
+    return check_launch();
+}
+
+// Gradients only (no update): grad[kParams] receives d loss / d params.
+sci_status sci_lprox_grads(const float* params, const float* x, const float* target, int nx, int ny, int B,
+                           int count, float* grad, double* loss, void* work, size_t work_bytes,
+                           sci_stream_t stream) {
+    if (params == nullptr || x == nullptr || target == nullptr || grad == nullptr || !vol_ok(nx, ny, B, count))
+        return SCI_ERR_ARG;
+    const Vol g{count, B, nx, ny, (long long)nx * ny * B * count};
+    const LWork need = lwork_layout(g.V, true, nullptr);
+    if (work == nullptr || work_bytes < need.total || ((uintptr_t)work & 255u) != 0) return SCI_ERR_WORKSPACE;
+    LWork L = lwork_layout(g.V, true, work);
+    L.grad = grad;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaMemsetAsync(L.err, 0, sizeof(int), s);
+    if (!enqueue_forward(params, x, g, L, nullptr, target, s)) return SCI_ERR_CUDA;
+    if (loss != nullptr) launch_sum_partials(L.partials, grid_for(g.V), loss, s);
+    cudaMemsetAsync(grad, 0, kParams * 4, s);
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int wg = sms * 4;
+    k_wgrad_out<<<wg, 27 * C + C, 0, s>>>(L.g4, L.a3, g, grad + kW4, grad + kB4);
+    k_dgrad_out<<<grid_for(g.V), 256, 0, s>>>(L.g4, params, g, L.a3, L.ga);
+    k_wgrad_c32<<<wg, 256, 0, s>>>(L.ga, L.a2, g, grad + kW3, grad + kB3);
+    if (!launch_conv3d_c32_tc(L.ga, L.w3t, nullptr, L.a2, 1, g.nvol, g.D, g.H, g.W, L.gb, L.err, s))
+        return SCI_ERR_CUDA;
+    k_wgrad_c32<<<wg, 256, 0, s>>>(L.gb, L.a1, g, grad + kW2, grad + kB2);
+    if (!launch_conv3d_c32_tc(L.gb, L.w2t, nullptr, L.a1, 1, g.nvol, g.D, g.H, g.W, L.ga, L.err, s))
+        return SCI_ERR_CUDA;
+    k_wgrad_in<<<wg, 28 * C, 0, s>>>(L.ga, x, g, grad + kW1, grad + kB1);
+    return check_launch();
+}
+
+// Device word that the tensor-core kernel sets if one of its bounded waits
+// gave up (0 = fine).  Read it after a synchronisation.
+sci_status sci_lprox_error_word(void* work, size_t work_bytes, int nx, int ny, int B, int count, int training,
+                                int** out) {
+    if (out == nullptr || !vol_ok(nx, ny, B, count)) return SCI_ERR_ARG;
+    const LWork need = lwork_layout((long long)nx * ny * B * count, training != 0, nullptr);
+    if (work == nullptr || work_bytes < need.total) return SCI_ERR_WORKSPACE;
+    *out = lwork_layout((long long)nx * ny * B * count, training != 0, work).err;
+    return SCI_OK;
+}
+
+}  // extern "C"

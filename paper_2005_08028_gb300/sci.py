@@ -16,7 +16,8 @@ __all__ = [
     "SciError", "TV", "DTYPE", "load", "sci_masks_pack", "sci_forward", "sci_adjoint",
     "sci_project", "sci_tv_prox", "sci_gap_tv", "sci_admm_tv", "sci_sqdiff_f64",
     "sci_residual_f64", "sci_graph_cache_clear", "sci_tv_prox_noalloc", "sci_last_solve_launches", "sci_fused_updates", "Batch", "SciProblem",
-    "sci_gap_tv_batched", "sci_last_batch_launches", "Workspace", "SciParams",
+    "sci_gap_tv_batched", "sci_last_batch_launches",
+    "sci_conv3d_c32_bf16", "LearnedProx", "Workspace", "SciParams",
 ]
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsci.so")
@@ -72,6 +73,13 @@ _SIGS = {
     "sci_gap_tv_batched": (_i, [C.POINTER(SciProblem), _i, C.POINTER(SciParams), _vp, _sz, _vp]),
     "sci_last_batch_launches": (C.c_longlong, []),
     "sci_batch_graph_cache_clear": (None, []),
+    "sci_lprox_param_count": (_sz, []),
+    "sci_lprox_workspace": (_sz, [_i, _i, _i, _i, _i]),
+    "sci_lprox_apply": (_i, [_vp, _vp, _i, _i, _i, _i, _vp, _vp, _sz, _vp]),
+    "sci_lprox_train_step": (_i, [_vp, _vp, _vp, _i, _f, _vp, _vp, _i, _i, _i, _i, _vp, _vp, _sz, _vp]),
+    "sci_lprox_grads": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp, _sz, _vp]),
+    "sci_lprox_error_word": (_i, [_vp, _sz, _i, _i, _i, _i, _i, C.POINTER(C.c_void_p)]),
+    "sci_conv3d_c32_bf16": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp]),
 }
 
 
@@ -299,6 +307,88 @@ def sci_gap_tv_batched(batch: Batch, tv, lam, outer, inner, storage="f32", init=
     _check("sci_gap_tv_batched", lib.sci_gap_tv_batched(batch.problems, n, C.byref(prm), _ptr(wbuf),
                                                         wbuf.numel(), _stream(batch.device)))
     return batch.x_outs, batch.thetas
+
+
+def sci_conv3d_c32_bf16(act: torch.Tensor, w: torch.Tensor, bias: torch.Tensor | None = None,
+                        relu: bool = False):
+    """3x3x3 conv, 32 -> 32 channels, on the tensor cores: act BF16 [n][D][H][W][32],
+    w BF16 [27][32][32] -> BF16 [n][D][H][W][32] (and the kernel's error word)."""
+    _need_cuda(act, w, bias)
+    if act.dtype != torch.bfloat16 or w.dtype != torch.bfloat16 or act.shape[-1] != 32:
+        raise ValueError("act and w must be bfloat16 with 32 channels")
+    n, D, H, W, _ = act.shape
+    out = torch.empty_like(act)
+    err = torch.zeros(1, dtype=torch.int32, device=act.device)
+    _check("sci_conv3d_c32_bf16", load().sci_conv3d_c32_bf16(_ptr(act), _ptr(w), _ptr(bias), int(relu), n, D,
+                                                             H, W, _ptr(out), _ptr(err), _stream(act.device)))
+    return out, err
+
+
+class LearnedProx:
+    """FP32 master parameters, Adam state and scratch of the learned prox."""
+
+    def __init__(self, device="cuda", params: torch.Tensor | None = None):
+        self.device = torch.device(device)
+        n = int(load().sci_lprox_param_count())
+        self.params = (params.clone() if params is not None
+                       else torch.zeros(n, dtype=torch.float32, device=self.device))
+        if self.params.numel() != n:
+            raise ValueError(f"expected {n} parameters")
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.step = 0
+        self.work = Workspace(self.device)
+
+    @staticmethod
+    def param_count() -> int:
+        return int(load().sci_lprox_param_count())
+
+    def apply(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """theta = x + f(x) for x float32 [count][B][nx][ny] (or [B][nx][ny])."""
+        _need_cuda(x)
+        xv = x if x.dim() == 4 else x.unsqueeze(0)
+        count, B, nx, ny = xv.shape
+        lib = load()
+        wbuf = self.work.get(lib.sci_lprox_workspace(nx, ny, B, count, 0))
+        theta = torch.empty_like(x) if out is None else out
+        _check("sci_lprox_apply", lib.sci_lprox_apply(_ptr(self.params), _ptr(x), nx, ny, B, count, _ptr(theta),
+                                                      _ptr(wbuf), wbuf.numel(), _stream(x.device)))
+        return theta
+
+    def train_step(self, x: torch.Tensor, target: torch.Tensor, lr: float) -> torch.Tensor:
+        """One Adam step; returns the pre-step sum of squared errors (device double)."""
+        _need_cuda(x, target)
+        count, B, nx, ny = x.shape
+        lib = load()
+        wbuf = self.work.get(lib.sci_lprox_workspace(nx, ny, B, count, 1))
+        loss = torch.zeros(1, dtype=torch.float64, device=x.device)
+        self.step += 1
+        _check("sci_lprox_train_step", lib.sci_lprox_train_step(
+            _ptr(self.params), _ptr(self.m), _ptr(self.v), self.step, float(lr), _ptr(x), _ptr(target), nx, ny,
+            B, count, _ptr(loss), _ptr(wbuf), wbuf.numel(), _stream(x.device)))
+        return loss
+
+    def grads(self, x: torch.Tensor, target: torch.Tensor):
+        _need_cuda(x, target)
+        count, B, nx, ny = x.shape
+        lib = load()
+        wbuf = self.work.get(lib.sci_lprox_workspace(nx, ny, B, count, 1))
+        g = torch.empty_like(self.params)
+        loss = torch.zeros(1, dtype=torch.float64, device=x.device)
+        _check("sci_lprox_grads", lib.sci_lprox_grads(_ptr(self.params), _ptr(x), _ptr(target), nx, ny, B, count,
+                                                      _ptr(g), _ptr(loss), _ptr(wbuf), wbuf.numel(),
+                                                      _stream(x.device)))
+        return g, loss
+
+    def error_word(self, x_shape, training: bool) -> int:
+        count, B, nx, ny = x_shape
+        lib = load()
+        wbuf = self.work.get(lib.sci_lprox_workspace(nx, ny, B, count, int(training)))
+        ptr = C.c_void_p()
+        _check("sci_lprox_error_word", lib.sci_lprox_error_word(_ptr(wbuf), wbuf.numel(), nx, ny, B, count,
+                                                                int(training), C.byref(ptr)))
+        off = int(ptr.value) - wbuf.data_ptr()
+        return int(wbuf[off:off + 4].view(torch.int32).item())
 
 
 def sci_last_batch_launches() -> int:
