@@ -219,6 +219,30 @@ sci_status sci_lprox_grads(const float* params, const float* x, const float* tar
                            int B, int count, float* grad, double* loss, void* work, size_t work_bytes,
                            sci_stream_t stream);
 
+/* Scratch bytes for sci_gap_tv_lprox. */
+size_t sci_gap_tv_lprox_workspace(int nx, int ny, int B, int count, const sci_params* plain);
+
+/*
+ * GAP-TV with the learned prox in place of FGP: T iterations of
+ *   x = GAP projection of theta (Eq. 21);  theta = x + f(x)
+ * on `count` measurements of the same size (y, bits: [count][nx][ny];
+ * theta, x_out: [count][B][nx][ny]; init = 1 starts from Phi^T y).
+ * Fallback: when check_every > 0, after every check_every iterations the
+ * residual ||y - Phi theta||^2 of each measurement (written to resid_out,
+ * host [count][ceil(T/check_every)], nullable) is compared with
+ * fallback_ratio x resid_limit[c] (host, the plain method's residual at the
+ * same checkpoint, e.g. from a calibration run; nullable = never fall back).
+ * A measurement that exceeds it restarts from its last checkpoint with plain
+ * GAP-TV (params `plain`, e.g. FGP with S = 10) for the remaining iterations;
+ * fell_back (host [count], nullable) reports which did.  With check_every >
+ * 0 this call synchronises `stream` at every checkpoint.
+ */
+sci_status sci_gap_tv_lprox(const float* params, const float* y, const uint32_t* bits, int nx, int ny, int B,
+                            int count, int outer_iters, int init, float* theta, float* x_out, int check_every,
+                            const double* resid_limit, float fallback_ratio, const sci_params* plain,
+                            int* fell_back, double* resid_out, void* work, size_t work_bytes,
+                            sci_stream_t stream);
+
 /* Device int in `work` that the tensor-core kernel sets to 1 if a bounded wait
  * gave up (cleared at the start of each call above); read after a sync. */
 sci_status sci_lprox_error_word(void* work, size_t work_bytes, int nx, int ny, int B, int count,

@@ -16,8 +16,10 @@
 // b2 [32], w3 [27][32][32], b3 [32], w4 [27][1][32], b4 [1]; tap index
 // (dz+1)*9 + (dy+1)*3 + (dx+1); layer l computes
 // out[v][o] = b[o] + sum_tap sum_i w[tap][o][i] * in[v + offset(tap)][i].
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "sci_internal.cuh"
 
@@ -316,6 +318,31 @@ LWork lwork_layout(long long V, bool training, void* base) {
 
 int grid_for(long long V) { return (int)((V + 255) / 256); }
 
+// GAP projection for `count` volumes stored back to back:
+// xt = theta + c_k R^+ (y - sum_k c_k theta_k); also x_out = xt when given.
+__global__ void k_project_vols(const float* __restrict__ theta, const float* __restrict__ y,
+                               const uint32_t* __restrict__ bits, int nx, int ny, int B, float* __restrict__ xt,
+                               float* __restrict__ x_out) {
+    const long long n = (long long)nx * ny;
+    const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= n) return;
+    const int vol = blockIdx.y;
+    const long long vo = (long long)vol * B * n, po = (long long)vol * n;
+    const uint32_t w = bits[po + pix];
+    float acc = 0.f;
+    for (int k = 0; k < B; ++k) acc += mask_bit(w, k) * theta[vo + k * n + pix];
+    const uint32_t m = B >= 32 ? 0xffffffffu : ((1u << B) - 1u);
+    const double R = (double)__popc(w & m);
+    const float rinv = R == 0.0 ? 0.f : (float)(1.0 / R);
+    const float r = rinv * (y[po + pix] - acc);
+    for (int k = 0; k < B; ++k) {
+        const long long i = vo + k * n + pix;
+        const float v = theta[i] + mask_bit(w, k) * r;
+        xt[i] = v;
+        if (x_out) x_out[i] = v;
+    }
+}
+
 // forward through the four layers; theta = x + f(x)
 bool enqueue_forward(const float* prm, const float* x, Vol g, const LWork& L, float* theta, const float* target,
                      cudaStream_t s) {
@@ -432,6 +459,91 @@ sci_status sci_lprox_grads(const float* params, const float* x, const float* tar
     if (!launch_conv3d_c32_tc(L.gb, L.w2t, nullptr, L.a1, 1, g.nvol, g.D, g.H, g.W, L.ga, L.err, s))
         return SCI_ERR_CUDA;
     k_wgrad_in<<<wg, 28 * C, 0, s>>>(L.ga, x, g, grad + kW1, grad + kB1);
+    return check_launch();
+}
+
+size_t sci_gap_tv_lprox_workspace(int nx, int ny, int B, int count, const sci_params* plain) {
+    if (!vol_ok(nx, ny, B, count) || plain == nullptr) return 0;
+    const size_t N = (size_t)nx * ny * B * count;
+    return align256(N * 4) * 2 + align256((size_t)count * 8) + align256(sci_reduce_workspace()) +
+           std::max(lwork_layout((long long)N, false, nullptr).total, sci_solver_workspace(nx, ny, B, plain));
+}
+
+sci_status sci_gap_tv_lprox(const float* params, const float* y, const uint32_t* bits, int nx, int ny, int B,
+                            int count, int outer_iters, int init, float* theta, float* x_out, int check_every,
+                            const double* resid_limit, float fallback_ratio, const sci_params* plain,
+                            int* fell_back, double* resid_out, void* work, size_t work_bytes,
+                            sci_stream_t stream) {
+    if (params == nullptr || y == nullptr || bits == nullptr || theta == nullptr || plain == nullptr ||
+        !vol_ok(nx, ny, B, count) || outer_iters < 0 || check_every < 0)
+        return SCI_ERR_ARG;
+    if (B > 32) return SCI_ERR_SHAPE;
+    if (!std::isfinite(fallback_ratio) || fallback_ratio <= 0.f) return SCI_ERR_ARG;
+    const size_t need = sci_gap_tv_lprox_workspace(nx, ny, B, count, plain);
+    if (work == nullptr || work_bytes < need || ((uintptr_t)work & 255u) != 0) return SCI_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long n = (long long)nx * ny, Nv = n * B, N = Nv * count;
+    char* w = static_cast<char*>(work);
+    float* xt = reinterpret_cast<float*>(w);
+    float* ckpt = reinterpret_cast<float*>(w + align256(N * 4));
+    double* rdev = reinterpret_cast<double*>(w + 2 * align256(N * 4));
+    void* rwork = w + 2 * align256(N * 4) + align256((size_t)count * 8);
+    void* inner = static_cast<char*>(rwork) + align256(sci_reduce_workspace());
+    const size_t inner_bytes = work_bytes - (size_t)(static_cast<char*>(inner) - w);
+    const Vol g{count, B, nx, ny, N};
+    const LWork L = lwork_layout(N, false, inner);
+    cudaMemsetAsync(L.err, 0, sizeof(int), s);
+    if (init) {
+        for (int v = 0; v < count; ++v)
+            launch_adjoint<float>(y + v * n, bits + v * n, Geo{nx, ny, B, n}, theta + v * Nv, s);
+    }
+    std::vector<int> fell(count, 0), fall_t(count, 0);
+    const int chunk = check_every > 0 ? check_every : std::max(outer_iters, 1);
+    if (check_every > 0) cudaMemcpyAsync(ckpt, theta, (size_t)N * 4, cudaMemcpyDeviceToDevice, s);
+    const dim3 pgrid((unsigned)((n + 255) / 256), (unsigned)count);
+    int t = 0, c = 0;
+    while (t < outer_iters) {
+        const int it = std::min(chunk, outer_iters - t);
+        for (int i = 0; i < it; ++i) {
+            const bool last = t + i == outer_iters - 1;
+            k_project_vols<<<pgrid, 256, 0, s>>>(theta, y, bits, nx, ny, B, xt, last ? x_out : nullptr);
+            if (!enqueue_forward(params, xt, g, L, theta, nullptr, s)) return SCI_ERR_CUDA;
+        }
+        t += it;
+        if (check_every > 0) {
+            for (int v = 0; v < count; ++v)
+                launch_residual_norm<float>(theta + v * Nv, y + v * n, bits + v * n, Geo{nx, ny, B, n},
+                                            static_cast<double*>(rwork), rdev + v, s);
+            std::vector<double> r(count);
+            if (cudaMemcpyAsync(r.data(), rdev, (size_t)count * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return SCI_ERR_CUDA;
+            for (int v = 0; v < count; ++v) {
+                if (resid_out) resid_out[(size_t)v * ((outer_iters + check_every - 1) / check_every) + c] = r[v];
+                if (!fell[v] && resid_limit && r[v] > (double)fallback_ratio * resid_limit[c]) {
+                    fell[v] = 1;
+                    fall_t[v] = t - it;  // restart from the checkpoint before this chunk
+                }
+                if (!fell[v])
+                    cudaMemcpyAsync(ckpt + v * Nv, theta + v * Nv, (size_t)Nv * 4, cudaMemcpyDeviceToDevice, s);
+            }
+            ++c;
+        }
+    }
+    // measurements whose residual left the plain run's band: plain GAP-TV from their checkpoint
+    for (int v = 0; v < count; ++v) {
+        if (fell_back) fell_back[v] = fell[v];
+        if (!fell[v]) continue;
+        cudaMemcpyAsync(theta + v * Nv, ckpt + v * Nv, (size_t)Nv * 4, cudaMemcpyDeviceToDevice, s);
+        sci_params p = *plain;
+        p.outer_iters = outer_iters - fall_t[v];
+        p.init = 0;
+        p.use_graph = 0;
+        const sci_status st = sci_gap_tv(y + v * n, bits + v * n, nx, ny, B, &p, theta + v * Nv,
+                                         x_out ? x_out + v * Nv : nullptr, nullptr, 0, inner, inner_bytes,
+                                         stream);
+        if (st != SCI_OK) return st;
+    }
     return check_launch();
 }
 

@@ -17,7 +17,7 @@ __all__ = [
     "sci_project", "sci_tv_prox", "sci_gap_tv", "sci_admm_tv", "sci_sqdiff_f64",
     "sci_residual_f64", "sci_graph_cache_clear", "sci_tv_prox_noalloc", "sci_last_solve_launches", "sci_fused_updates", "Batch", "SciProblem",
     "sci_gap_tv_batched", "sci_last_batch_launches",
-    "sci_conv3d_c32_bf16", "LearnedProx", "Workspace", "SciParams",
+    "sci_conv3d_c32_bf16", "LearnedProx", "sci_gap_tv_lprox", "Workspace", "SciParams",
 ]
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsci.so")
@@ -80,6 +80,9 @@ _SIGS = {
     "sci_lprox_grads": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _vp, _vp, _vp, _sz, _vp]),
     "sci_lprox_error_word": (_i, [_vp, _sz, _i, _i, _i, _i, _i, C.POINTER(C.c_void_p)]),
     "sci_conv3d_c32_bf16": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp]),
+    "sci_gap_tv_lprox_workspace": (_sz, [_i, _i, _i, _i, C.POINTER(SciParams)]),
+    "sci_gap_tv_lprox": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _vp, _i, _vp, _f,
+                              C.POINTER(SciParams), _vp, _vp, _vp, _sz, _vp]),
 }
 
 
@@ -389,6 +392,43 @@ class LearnedProx:
                                                                 int(training), C.byref(ptr)))
         off = int(ptr.value) - wbuf.data_ptr()
         return int(wbuf[off:off + 4].view(torch.int32).item())
+
+
+def sci_gap_tv_lprox(net: "LearnedProx", y: torch.Tensor, bits: torch.Tensor, B: int, outer: int,
+                     plain_tv: str = "vtv", plain_lam: float = 0.05, plain_inner: int = 10,
+                     check_every: int = 0, resid_limit=None, ratio: float = 1.05, theta=None, x_out=None,
+                     work: Workspace | None = None):
+    """GAP-TV with the learned prox on y [count][nx][ny] (bits likewise).
+
+    Returns (x^(T), theta^(T), fell_back list, residual history [count][checks]).
+    With check_every > 0 and resid_limit (the plain method's residual at each
+    checkpoint), measurements whose residual exceeds ratio x limit restart
+    from their last checkpoint with plain GAP-TV (plain_tv, plain_lam,
+    plain_inner FGP updates).
+    """
+    _need_cuda(y, bits, theta, x_out)
+    count, nx, ny = y.shape
+    dev = y.device
+    init = theta is None
+    if theta is None:
+        theta = torch.empty((count, B, nx, ny), dtype=torch.float32, device=dev)
+    if x_out is None:
+        x_out = torch.empty_like(theta)
+    plain = _params(plain_tv, plain_lam, 0.0, outer, plain_inner, "f32", 0, 0, 0)
+    lib = load()
+    need = lib.sci_gap_tv_lprox_workspace(nx, ny, B, count, C.byref(plain))
+    wbuf = (work or Workspace(dev)).get(need)
+    nchk = (outer + check_every - 1) // check_every if check_every > 0 else 0
+    lim = None
+    if resid_limit is not None:
+        lim = (C.c_double * len(resid_limit))(*[float(v) for v in resid_limit])
+    fell = (C.c_int * count)()
+    rout = (C.c_double * max(1, count * nchk))()
+    _check("sci_gap_tv_lprox", lib.sci_gap_tv_lprox(
+        _ptr(net.params), _ptr(y), _ptr(bits), nx, ny, B, count, int(outer), int(init), _ptr(theta), _ptr(x_out),
+        int(check_every), lim, float(ratio), C.byref(plain), fell, rout, _ptr(wbuf), wbuf.numel(), _stream(dev)))
+    hist = [[rout[v * nchk + c] for c in range(nchk)] for v in range(count)]
+    return x_out, theta, [int(f) for f in fell], hist
 
 
 def sci_last_batch_launches() -> int:
