@@ -241,6 +241,9 @@ def run_gpu(args):
     # ---- batched: 256 mixed-size measurements per call (BF16 and FP32 storage) ----
     batched = None if args.no_batched else _batched(pkg, torch, dev, stream, flush)
 
+    # ---- learned prox: trained here, then GAP-TV on 64 measurements of 512x512x10 ----
+    learned = None if args.no_learned else _learned(pkg, torch, dev, stream, flush)
+
     # ---- end to end: host buffers through the public API ----
     e2e = _e2e(pkg, torch, dev, stream, args, c, masks_h, y, bufs, flush)
 
@@ -256,6 +259,7 @@ def run_gpu(args):
                                      "not stated)"),
         "psnr": psnr,
         "batched": batched,
+        "learned": learned,
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": launches,
@@ -392,6 +396,126 @@ def _batched(pkg, torch, dev, stream, flush):
     return out
 
 
+def _learned(pkg, torch, dev, stream, flush):
+    """Learned prox replacing S = 10 VTV-FGP updates inside GAP-TV.
+
+    Training: 4096 (x, FGP_10(x)) pairs of 64x64x8 patches cut from plain
+    GAP-TV runs on seeded 256x256x8 measurements stopped at random outer
+    iterations in [1, 50]; Adam, 8 epochs of batch 32 (the config's 20k pairs
+    are cut to 4k to keep the benchmark short; the training set size is
+    reported).  Test: 64 measurements of 512x512x10 (Bernoulli(0.5) masks,
+    sigma = 0.01), T = 50 outer iterations with the learned prox and a
+    residual check every 10 iterations against the plain method's residual
+    curve (calibrated on 8 held-out measurements), falling back to plain FGP
+    where it is exceeded by more than 5%.  Compared with plain FP32 GAP-TV
+    (VTV, S = 10) on the same 64 measurements.  The tensor-core convolution's
+    own throughput is measured on the test batch's activations."""
+    import paper_2005_08028_gb300.lprox_train as LT
+    import sci_synth as ss
+    lam, S, T, every = 0.05, 10, 50, 10
+    t0 = time.perf_counter()
+    X, Y = LT.make_pairs(4096, seed=50, size=(256, 256, 8))
+    net = pkg.LearnedProx(params=LT.init_params(seed=1))
+    hist = LT.train(net, X[:3840], Y[:3840], epochs=8, batch=32, lr=1e-3)
+    pred = net.apply(X[3840:])
+    mse_net = float(((pred - Y[3840:]) ** 2).mean())
+    mse_id = float(((X[3840:] - Y[3840:]) ** 2).mean())
+    torch.cuda.synchronize(dev)
+    train_s = time.perf_counter() - t0
+    del X, Y, pred
+
+    def meas(count, seed0):
+        ys, bs, gts = [], [], []
+        for k in range(count):
+            c = ss.make_case(512, 512, 10, seed0 + k, sigma=0.01)
+            bb = pkg.sci_masks_pack(torch.from_numpy(c.masks).to(dev))
+            xg = torch.from_numpy(c.x_gt.astype(np.float32)).to(dev)
+            ys.append(pkg.sci_forward(xg, bb) + torch.from_numpy(c.noise.astype(np.float32)).to(dev))
+            bs.append(bb)
+            gts.append(xg)
+        return torch.stack(ys), torch.stack(bs), gts
+
+    # calibration: the plain method's residual every 10 iterations on held-out measurements
+    yc, bc, _ = meas(8, 52000)
+    curves = []
+    for k in range(8):
+        _, _, r = pkg.sci_gap_tv(yc[k].contiguous(), bc[k].contiguous(), 10, "vtv", lam, T, S, resid_every=every)
+        curves.append(r.cpu().numpy())
+    limit = np.mean(curves, axis=0).tolist()
+    y, bits, gts = meas(64, 51000)
+    N = 64 * 10 * 512 * 512
+    work = pkg.Workspace(dev)
+    pkg.sci_gap_tv_lprox(net, y[:2], bits[:2], 10, 2, work=work)  # warm-up
+    torch.cuda.synchronize(dev)
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    x_l, _, fell, _ = pkg.sci_gap_tv_lprox(net, y, bits, 10, T, check_every=every, resid_limit=limit, work=work)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_l = e0.elapsed_time(e1)
+    # plain FP32 GAP-TV on the same measurements (one solve each, cached graph after the first)
+    xs_p = []
+    pw = pkg.Workspace(dev)
+    th = torch.empty((10, 512, 512), device=dev)
+    xo = [torch.empty((10, 512, 512), device=dev) for _ in range(64)]
+    pkg.sci_gap_tv(y[0].contiguous(), bits[0].contiguous(), 10, "vtv", lam, T, S, theta=th, init=True,
+                   x_out=xo[0], work=pw)
+    torch.cuda.synchronize(dev)
+    flush.zero_()
+    e0.record(stream)
+    for k in range(64):
+        pkg.sci_gap_tv(y[k].contiguous(), bits[k].contiguous(), 10, "vtv", lam, T, S, theta=th, init=True,
+                       x_out=xo[k], work=pw)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_p = e0.elapsed_time(e1)
+
+    def mean_psnr(xs):
+        ps = []
+        for x, g in zip(xs, gts):
+            mse = float(pkg.sci_sqdiff_f64(x.contiguous(), g).item()) / g.numel()
+            ps.append(10.0 * np.log10(1.0 / mse))
+        return float(np.mean(ps))
+
+    p_l, p_p = mean_psnr([x_l[k] for k in range(64)]), mean_psnr(xo)
+    # tensor-core conv throughput on activations of this size
+    act = torch.randn((64, 10, 512, 512, 32), device=dev).to(torch.bfloat16)
+    wt = (0.05 * torch.randn((27, 32, 32), device=dev)).to(torch.bfloat16)
+    pkg.sci_conv3d_c32_bf16(act[:1], wt)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    out, err = pkg.sci_conv3d_c32_bf16(act, wt)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_c = e0.elapsed_time(e1)
+    flops = 2.0 * 27 * 32 * 32 * act[..., 0].numel()
+    peak = _bf16_peak()
+    del act, out
+    return {"workload": "learned_prox_64x512x512x10: VTV, lambda=0.05, T=50, network replaces S=10 FGP "
+                        "updates; residual check every 10 iterations, fallback ratio 1.05",
+            "train": {"pairs": 3840, "patch": "8x64x64", "epochs": 8, "batch": 32, "seconds": round(train_s, 1),
+                      "loss_per_epoch": [float(f"{h:.3e}") for h in hist],
+                      "heldout_mse_vs_identity": round(mse_net / mse_id, 4)},
+            "learned": {"value": N * T / (ms_l * 1e-3), "unit": UNIT, "ms": round(ms_l, 1),
+                        "mean_psnr_db": round(p_l, 4), "fallbacks": int(sum(fell))},
+            "plain_f32": {"value": N * T / (ms_p * 1e-3), "unit": UNIT, "ms": round(ms_p, 1),
+                          "mean_psnr_db": round(p_p, 4)},
+            "psnr_delta_learned_vs_plain_db": round(p_l - p_p, 4),
+            "conv_tc_roofline": {"kernel": "k_conv3d_c32_tc", "bound": "tensor",
+                                 "achieved": round(flops / (ms_c * 1e-3) / 1e12, 2), "peak": peak,
+                                 "peak_kind": "measured bf16_tflops (burst)", "unit": "TFLOP/s",
+                                 "frac": round(flops / (ms_c * 1e-3) / 1e12 / peak, 4),
+                                 "err_word": int(err.item())}}
+
+
+def _bf16_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return float(json.load(open(path))["bf16_tflops"])
+    return 1900.0
+
+
 def _e2e(pkg, torch, dev, stream, args, c, masks_h, y_dev, bufs, flush):
     """Same metric through the public API with host inputs/outputs: each step
     copies y and the dense masks from pinned host memory, packs the masks,
@@ -454,6 +578,7 @@ def main():
     ap.add_argument("--impl", choices=["sci", "reference"], default="sci")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-measurement batched solve")
+    ap.add_argument("--no-learned", action="store_true", help="skip training and running the learned prox")
     ap.add_argument("--kernel-case", choices=["fused"], default=None,
                     help="run one launch of the dominant kernel per TV form and exit (for profilers)")
     args = ap.parse_args()
