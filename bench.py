@@ -579,7 +579,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-measurement batched solve")
     ap.add_argument("--no-learned", action="store_true", help="skip training and running the learned prox")
-    ap.add_argument("--kernel-case", choices=["fused"], default=None,
+    ap.add_argument("--kernel-case", choices=["fused", "conv"], default=None,
                     help="run one launch of the dominant kernel per TV form and exit (for profilers)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -590,7 +590,9 @@ def main():
 
 
 def run_kernel_case(args):
-    """One temporally blocked FGP launch per TV form on the 512x512x10 size."""
+    """fused: one temporally blocked FGP launch per TV form on the 512x512x10
+    size.  conv: one tensor-core 32->32 conv over 8 x 10 x 512 x 512 voxels
+    (1.3 GB of BF16 activations, larger than L2)."""
     import torch
     from paper_2005_08028_gb300 import build as b
     if not os.path.exists(b.LIB_PATH):
@@ -598,6 +600,13 @@ def run_kernel_case(args):
     import paper_2005_08028_gb300 as pkg
     c = _cfg()
     dev = torch.device("cuda")
+    if args.kernel_case == "conv":
+        act = torch.randn((8, 10, 512, 512, 32), device=dev).to(torch.bfloat16)
+        wt = (0.05 * torch.randn((27, 32, 32), device=dev)).to(torch.bfloat16)
+        out, err = pkg.sci_conv3d_c32_bf16(act, wt)
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel_case": "conv", "ok": int(err.item()) == 0}))
+        return 0 if int(err.item()) == 0 else 1
     x = torch.rand((c["B"], c["nx"], c["ny"]), device=dev)
     work = pkg.Workspace(dev)
     for tv in ("atv", "itv2d", "vtv"):
