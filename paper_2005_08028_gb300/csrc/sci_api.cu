@@ -220,13 +220,14 @@ int enqueue_solve(const SolveArgs& A, cudaStream_t s) {
             if (metric) { launch_residual_norm<T>(theta, A.y, A.bits, g, partials, resid_slot, s); nk += 2; }
             continue;
         }
-        launch_fgp_first<T>(A.prm.tv, mode, nullptr, theta, r, A.bits, g, lam, xt, P[0], s);
+        launch_fgp_stream<T>(A.prm.tv, mode, 1, nullptr, theta, r, A.bits, g, lam, 0.f, xt, nullptr, nullptr,
+                             P[0], s);
         ++nk;
         int cur = 0, prev = -1;
         for (int it = 1; it < S; ++it) {
             const int out = 3 - cur - (prev < 0 ? (cur == 0 ? 1 : 0) : prev);
-            launch_fgp_iter<T>(A.prm.tv, xt, P[cur], prev >= 0 ? P[prev] : nullptr, coef[(size_t)it - 1],
-                               g, lam, P[out], s);
+            launch_fgp_stream<T>(A.prm.tv, mode, 0, nullptr, theta, r, A.bits, g, lam, coef[(size_t)it - 1], xt,
+                                 P[cur], prev >= 0 ? P[prev] : nullptr, P[out], s);
             ++nk;
             prev = cur;
             cur = out;
@@ -443,12 +444,13 @@ sci_status sci_tv_prox(const float* x, int nx, int ny, int B, int tv, float lamb
             return SCI_ERR_CUDA;
         return check_launch();
     }
-    launch_fgp_first<float>(tv, OuterMode::Prox, x, nullptr, nullptr, nullptr, g, lambda, nullptr, P[0], s);
+    launch_fgp_stream<float>(tv, OuterMode::Prox, 1, x, nullptr, nullptr, nullptr, g, lambda, 0.f, nullptr,
+                             nullptr, nullptr, P[0], s);
     int cur = 0, prev = -1;
     for (int it = 1; it < inner_iters; ++it) {
         const int out = 3 - cur - (prev < 0 ? (cur == 0 ? 1 : 0) : prev);
-        launch_fgp_iter<float>(tv, x, P[cur], prev >= 0 ? P[prev] : nullptr, coef[(size_t)it - 1], g, lambda,
-                               P[out], s);
+        launch_fgp_stream<float>(tv, OuterMode::Prox, 0, x, nullptr, nullptr, nullptr, g, lambda,
+                                 coef[(size_t)it - 1], nullptr, P[cur], prev >= 0 ? P[prev] : nullptr, P[out], s);
         prev = cur;
         cur = out;
     }

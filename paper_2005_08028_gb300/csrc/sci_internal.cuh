@@ -49,6 +49,14 @@ void launch_fgp_first(int tv, OuterMode mode, const float* xin, const T* theta,
 template <typename T>
 void launch_fgp_iter(int tv, const T* xt, const T* p, const T* q, float coef, Geo g,
                      float lambda, T* p_out, cudaStream_t s);
+// One dual update streamed through 32x8 shared-memory halo tiles
+// (sci_stream.cu): first = 1 starts from w = 0 and forms x-tilde (Prox: from
+// xin; otherwise theta + c_k r, written to xt); later updates read xt and
+// w = p + coef (p - q) (q may be null).
+template <typename T>
+void launch_fgp_stream(int tv, OuterMode mode, int first, const float* xin, const T* theta, const float* r,
+                       const uint32_t* bits, Geo g, float lambda, float coef, T* xt, const T* p, const T* q,
+                       T* pout, cudaStream_t s);
 // Output theta = xt - lambda D^T p and the outer-loop epilogue.
 struct OutArgs {
     OuterMode mode;
