@@ -3,21 +3,24 @@
 // Used by the learned TV prox (its two hidden 32->32 layers, forward and
 // input-gradient passes).
 //
-// Implicit GEMM: an output tile is 128 voxels (BH rows x BW columns of one
+// Implicit GEMM: an output tile is 128 voxels (4 rows x 32 columns of one
 // frame of one volume) x 32 output channels.  For each of the 27 taps the
-// A operand is the 128 x 32 block of input activations shifted by the tap --
-// one TMA box of a 5-D tensor map over the channels-last activations
-// [volume][frame][row][column][channel]; out-of-range voxels arrive as zeros,
+// A operand is the 128 x 32 block of input activations shifted by the tap,
+// taken from TMA boxes of a 5-D tensor map over the channels-last
+// activations [volume][frame][row][column][channel] -- one 6-row box per
+// (dz, dx) serves the three dy taps; out-of-range voxels arrive as zeros,
 // which is the convolution's zero padding -- and the B operand is that tap's
 // 32 x 32 weight block, resident in shared memory for the whole kernel.  Each
 // tap is two tcgen05.mma (M = 128, N = 32, K = 16) accumulating into one
 // 128-lane x 32-column FP32 tile of tensor memory.
 //
-// One thread drives a ring of A stages (TMA load -> MMA -> commit frees the
-// stage); four warps then read the accumulator with tcgen05.ld (warp w owns
+// Warp-specialised and persistent: one lane issues TMA loads into a ring of
+// A stages, one lane issues the MMAs (a commit frees each stage), and four
+// warps read the double-buffered accumulator with tcgen05.ld (warp w owns
 // lanes 32w..32w+31, i.e. voxels 32w..32w+31 of the tile) and apply the
-// epilogue.  Every mbarrier wait is bounded: on timeout the kernel records
-// an error code, stops issuing work, frees its tensor memory and returns.
+// epilogue while the next tile accumulates.  Every mbarrier wait is
+// bounded: on timeout the kernel records an error code, stops issuing work,
+// drains what it issued, frees its tensor memory and returns.
 #include <cuda.h>
 
 #include <algorithm>
@@ -33,7 +36,13 @@ namespace {
 constexpr int kStages = 4;
 constexpr int kTileM = 128;
 constexpr int kC = 32;
-constexpr uint32_t kABytes = kTileM * kC * 2;      // 8 KB per A stage
+// A stage: one TMA box of 32 columns x 6 rows (the tile's 4 rows plus one
+// above and one below) of one frame; the three row taps (dy = -1, 0, +1) of a
+// (dz, dx) pair are 128-row windows of it starting 32 rows (2 KB) apart, which
+// keeps every window aligned to the 512-byte period of the 64-byte swizzle.
+constexpr int kBW = 32, kBH = 4;
+constexpr uint32_t kRowBytes = kC * 2;                       // 64 B per voxel
+constexpr uint32_t kABytes = kBW * (kBH + 2) * kRowBytes;    // 12 KB per A stage
 constexpr uint32_t kWTapBytes = kC * kC * 2;       // 2 KB per tap
 constexpr uint32_t kWBytes = 27 * kWTapBytes;      // 54 KB
 constexpr long long kSpinLimit = 1LL << 26;        // bounded mbarrier waits
@@ -139,37 +148,50 @@ struct ConvTcArgs {
     int* err;               // set to 1 on a wait timeout
 };
 
-__global__ void __launch_bounds__(128, 1)
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Warp roles: warps 0-3 run the epilogue (warp w reads tensor-memory lanes
+// 32w..32w+31, i.e. tile voxels 32w..32w+31); lane 0 of warp 4 issues the
+// TMA loads; lane 0 of warp 5 issues the MMAs.  The accumulator is double
+// buffered in tensor memory (2 x 32 columns), so the epilogue of tile j
+// overlaps the MMAs of tile j + 1 and the loads run ahead across tiles.
+constexpr int kThreads = 192;
+
+__global__ void __launch_bounds__(kThreads, 1)
 k_conv3d_c32_tc(const __grid_constant__ CUtensorMap act_map, const __grid_constant__ CUtensorMap w_map,
                 ConvTcArgs a) {
     extern __shared__ __align__(1024) unsigned char dsmem[];
-    // 1024-byte aligned carve-up: weights, A stages, barriers
     unsigned char* base = (unsigned char*)(((uintptr_t)dsmem + 1023) & ~(uintptr_t)1023);
-    unsigned char* s_w = base;                       // 27 x 2 KB
-    unsigned char* s_a = base + kWBytes;             // kStages x 8 KB (kWBytes is a multiple of 1024)
+    unsigned char* s_w = base;                        // 27 x 2 KB weights
+    unsigned char* s_a = base + kWBytes;              // kStages x 8 KB A ring
     uint64_t* bars = reinterpret_cast<uint64_t*>(s_a + kStages * kABytes);
-    // bars: [0, kStages) full, [kStages, 2 kStages) empty, then weights, accumulator, drain
-    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 3);
+    // bars: full[kStages], empty[kStages], acc_full[2], acc_empty[2], weights, drain
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 6);
     volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t bar_full = smem_u32(bars), bar_empty = smem_u32(bars + kStages);
-    const uint32_t bar_w = smem_u32(bars + 2 * kStages), bar_acc = smem_u32(bars + 2 * kStages + 1);
-    const uint32_t bar_drain = smem_u32(bars + 2 * kStages + 2);
+    const uint32_t bar_accf = smem_u32(bars + 2 * kStages), bar_acce = smem_u32(bars + 2 * kStages + 2);
+    const uint32_t bar_w = smem_u32(bars + 2 * kStages + 4), bar_drain = smem_u32(bars + 2 * kStages + 5);
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(bar_full + 8 * s, 1);
             mbar_init(bar_empty + 8 * s, 1);
         }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(bar_accf + 8 * b, 1);
+            mbar_init(bar_acce + 8 * b, 4);  // one arrival per epilogue warp
+        }
         mbar_init(bar_w, 1);
-        mbar_init(bar_acc, 1);
         mbar_init(bar_drain, 1);
         *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(s_tmem))
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(s_tmem))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -177,84 +199,93 @@ k_conv3d_c32_tc(const __grid_constant__ CUtensorMap act_map, const __grid_consta
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *s_tmem;
+    const long long my_tiles = a.ntiles > blockIdx.x ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
-    // weights: 27 TMA boxes of 32 x 32
-    if (tid == 0) {
+    if (warp == 4 && lane == 0) {
+        // ---------------- TMA producer ----------------
         mbar_expect_tx(bar_w, kWBytes);
         for (int t = 0; t < 27; ++t) tma_load_3d(smem_u32(s_w + t * kWTapBytes), &w_map, bar_w, 0, 0, t);
-        if (!mbar_wait(bar_w, 0)) {
+        uint32_t q = 0;
+        long long issued_tiles = 0;
+        for (long long j = 0; j < my_tiles && !*s_abort; ++j) {
+            long long tr = blockIdx.x + j * gridDim.x;
+            const int tw = (int)(tr % a.tiles_w); tr /= a.tiles_w;
+            const int th = (int)(tr % a.tiles_h); tr /= a.tiles_h;
+            const int z = (int)(tr % a.D), vol = (int)(tr / a.D);
+            const int w0 = tw * a.BW, h0 = th * a.BH;
+            bool ok = true;
+            for (int k = 0; k < 9; ++k, ++q) {  // (dz, dx) pairs
+                const uint32_t s = q % kStages, use = q / kStages;
+                if (use > 0 && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1)) { ok = false; break; }
+                const int dz = k / 3 - 1, dx = k % 3 - 1;
+                mbar_expect_tx(bar_full + 8 * s, kABytes);
+                tma_load_5d(smem_u32(s_a + s * kABytes), &act_map, bar_full + 8 * s, 0, w0 + dx, h0 - 1, z + dz,
+                            vol);
+            }
+            if (!ok) { *s_abort = 1; atomicExch(a.err, 1); break; }
+            ++issued_tiles;
+        }
+        // drain: every load issued must have landed before the CTA exits
+        for (uint32_t k = (q >= kStages ? q - kStages : 0); k < q; ++k)
+            mbar_wait(bar_full + 8 * (k % kStages), (k / kStages) & 1);
+        (void)issued_tiles;
+    }
+    if (warp == 5 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        bool ok = mbar_wait(bar_w, 0);
+        uint32_t q = 0;
+        for (long long j = 0; j < my_tiles && ok && !*s_abort; ++j) {
+            const uint32_t b = (uint32_t)(j & 1), use_b = (uint32_t)(j >> 1);
+            if (use_b > 0 && !mbar_wait(bar_acce + 8 * b, (use_b - 1) & 1)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t d = tmem + b * 32;
+            for (int k = 0; k < 9; ++k, ++q) {
+                const uint32_t s = q % kStages, use = q / kStages;
+                if (!mbar_wait(bar_full + 8 * s, use & 1)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const int dz = k / 3 - 1, dx = k % 3 - 1;
+#pragma unroll
+                for (int dyi = 0; dyi < 3; ++dyi) {
+                    const int t = (dz + 1) * 9 + dyi * 3 + (dx + 1);
+                    const uint32_t abase = smem_u32(s_a + s * kABytes) + (uint32_t)dyi * kBW * kRowBytes;
+                    const uint32_t bbase = smem_u32(s_w + t * kWTapBytes);
+                    umma_bf16(d, smem_desc_sw64(abase), smem_desc_sw64(bbase), (k > 0 || dyi > 0) ? 1u : 0u);
+                    umma_bf16(d, smem_desc_sw64(abase + 32), smem_desc_sw64(bbase + 32), 1u);
+                }
+                umma_commit(bar_empty + 8 * s);
+            }
+            if (!ok) break;
+            umma_commit(bar_accf + 8 * b);
+        }
+        if (!ok) {
+            // every MMA issued so far must finish before tensor memory is freed
+            umma_commit(bar_drain);
+            mbar_wait(bar_drain, 0);
             *s_abort = 1;
             atomicExch(a.err, 1);
         }
     }
-    __syncthreads();
-
-    uint32_t q = 0;          // A loads issued so far (ring sequence number)
-    uint32_t acc_phase = 0;  // accumulator barrier phase
-    for (long long tile = blockIdx.x; tile < a.ntiles && !*s_abort; tile += gridDim.x) {
-        long long tr = tile;
-        const int tw = (int)(tr % a.tiles_w); tr /= a.tiles_w;
-        const int th = (int)(tr % a.tiles_h); tr /= a.tiles_h;
-        const int z = (int)(tr % a.D);
-        const int vol = (int)(tr / a.D);
-        const int w0 = tw * a.BW, h0 = th * a.BH;
-
-        if (tid == 0) {
-            bool ok = true;
-            int produced = 0, consumed = 0;
-            // software pipeline: load tap t + kStages - 1 while the MMAs of tap t run
-            for (int step = 0; step < 27 + kStages - 1 && ok; ++step) {
-                if (step < 27) {  // produce tap `step`
-                    const uint32_t qq = q + step, s = qq % kStages, use = qq / kStages;
-                    if (use > 0 && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1)) { ok = false; break; }
-                    const int dz = step / 9 - 1, dy = (step / 3) % 3 - 1, dx = step % 3 - 1;
-                    mbar_expect_tx(bar_full + 8 * s, kABytes);
-                    tma_load_5d(smem_u32(s_a + s * kABytes), &act_map, bar_full + 8 * s, 0, w0 + dx, h0 + dy,
-                                z + dz, vol);
-                    produced = step + 1;
-                }
-                const int t = step - (kStages - 1);
-                if (t >= 0) {  // consume tap t
-                    const uint32_t qq = q + t, s = qq % kStages, use = qq / kStages;
-                    if (!mbar_wait(bar_full + 8 * s, use & 1)) { ok = false; break; }
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t abase = smem_u32(s_a + s * kABytes), bbase = smem_u32(s_w + t * kWTapBytes);
-                    umma_bf16(tmem, smem_desc_sw64(abase), smem_desc_sw64(bbase), t > 0 ? 1u : 0u);
-                    umma_bf16(tmem, smem_desc_sw64(abase + 32), smem_desc_sw64(bbase + 32), 1u);
-                    umma_commit(bar_empty + 8 * s);
-                    consumed = t + 1;
-                }
+    if (warp < 4) {
+        // ---------------- epilogue ----------------
+        for (long long j = 0; j < my_tiles; ++j) {
+            const uint32_t b = (uint32_t)(j & 1), use_b = (uint32_t)(j >> 1);
+            const bool got = __all_sync(0xffffffffu, mbar_wait(bar_accf + 8 * b, use_b & 1));
+            if (!got) {
+                if (lane == 0) { *s_abort = 1; atomicExch(a.err, 1); }
+                break;
             }
-            if (ok) {
-                umma_commit(bar_acc);
-            } else {
-                // drain before giving up: copies still in flight, then every issued MMA
-                for (int t = consumed; t < produced; ++t) {
-                    const uint32_t qq = q + t;
-                    mbar_wait(bar_full + 8 * (qq % kStages), (qq / kStages) & 1);
-                }
-                umma_commit(bar_drain);
-                mbar_wait(bar_drain, 0);
-                *s_abort = 1;
-                atomicExch(a.err, 1);
-            }
-            q += 27;
-        }
-        __syncthreads();
-        if (*s_abort) break;
-        // every thread waits for the accumulator, then reads its row
-        const bool got = mbar_wait(bar_acc, acc_phase & 1);
-        acc_phase++;
-        if (!got) {
-            *s_abort = 1;
-            atomicExch(a.err, 1);
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (got) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             float v[32];
-            tmem_ld_32cols(tmem + ((uint32_t)(warp * 32) << 16), v);
+            tmem_ld_32cols(tmem + b * 32 + ((uint32_t)(warp * 32) << 16), v);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_acce + 8 * b);  // this warp's lanes of buffer b are free
+            long long tr = blockIdx.x + j * gridDim.x;
+            const int tw = (int)(tr % a.tiles_w); tr /= a.tiles_w;
+            const int th = (int)(tr % a.tiles_h); tr /= a.tiles_h;
+            const int z = (int)(tr % a.D), vol = (int)(tr / a.D);
             const int r = tid;  // tile row = voxel
-            const int hh = h0 + r / a.BW, ww = w0 + r % a.BW;
+            const int hh = th * a.BH + r / a.BW, ww = tw * a.BW + r % a.BW;
             if (hh < a.H && ww < a.W) {
                 const long long vox = (((long long)vol * a.D + z) * a.H + hh) * a.W + ww;
                 __nv_bfloat16* dst = a.out + vox * kC;
@@ -278,15 +309,11 @@ k_conv3d_c32_tc(const __grid_constant__ CUtensorMap act_map, const __grid_consta
                 for (int c = 0; c < 4; ++c) d4[c] = pk[c];
             }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
     }
-    // drain: the last MMAs' commits may still be pending on the empty barriers;
-    // the accumulator barrier covered them on the success path.
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+    if (warp == 5) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
     }
 }
 
@@ -310,7 +337,7 @@ EncodeFn encode_fn() {
 
 }  // namespace
 
-size_t conv3d_c32_tc_smem() { return kWBytes + kStages * kABytes + 1024 + 256; }
+size_t conv3d_c32_tc_smem() { return kWBytes + kStages * kABytes + 1024 + 256; }  // 2 CTAs per SM
 
 // out[vol][z][h][w][:] = epilogue(sum_tap W[tap] * act[vol][z+dz][h+dy][w+dx][:]).
 // act, out: BF16 [nvol][D][H][W][32]; w: BF16 [27][32 out][32 in].
@@ -325,8 +352,8 @@ bool launch_conv3d_c32_tc(const __nv_bfloat16* act, const __nv_bfloat16* w, cons
     a.D = D;
     a.H = H;
     a.W = W;
-    a.BW = W <= 64 ? 64 : 128;
-    a.BH = kTileM / a.BW;
+    a.BW = kBW;
+    a.BH = kBH;
     a.tiles_w = (W + a.BW - 1) / a.BW;
     a.tiles_h = (H + a.BH - 1) / a.BH;
     a.ntiles = (long long)nvol * D * a.tiles_h * a.tiles_w;
@@ -343,7 +370,7 @@ bool launch_conv3d_c32_tc(const __nv_bfloat16* act, const __nv_bfloat16* w, cons
     const cuuint64_t adims[5] = {(cuuint64_t)kC, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)nvol};
     const cuuint64_t astr[4] = {(cuuint64_t)kC * 2, (cuuint64_t)W * kC * 2, (cuuint64_t)H * W * kC * 2,
                                 (cuuint64_t)D * H * W * kC * 2};
-    const cuuint32_t abox[5] = {(cuuint32_t)kC, (cuuint32_t)a.BW, (cuuint32_t)a.BH, 1, 1};
+    const cuuint32_t abox[5] = {(cuuint32_t)kC, (cuuint32_t)kBW, (cuuint32_t)(kBH + 2), 1, 1};
     const cuuint32_t ones[5] = {1, 1, 1, 1, 1};
     if (enc(&amap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(act), adims, astr, abox, ones,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -369,7 +396,7 @@ bool launch_conv3d_c32_tc(const __nv_bfloat16* act, const __nv_bfloat16* w, cons
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long grid = std::min<long long>(a.ntiles, (long long)sms * 2);
-    k_conv3d_c32_tc<<<(unsigned)grid, 128, smem, s>>>(amap, wmap, a);
+    k_conv3d_c32_tc<<<(unsigned)grid, kThreads, smem, s>>>(amap, wmap, a);
     return true;
 }
 
