@@ -134,7 +134,7 @@ sci_status make_plan(const sci_problem* probs, int count, const sci_params* prm,
         run.halo = K + 1;
         int EH = 0, EW = 0;
         fused_class_dims(c, &EH, &EW);
-        const int TI = EH - 2 * run.halo, TJ = EW - 2 * run.halo;
+        const int TI = fused_interior(EH, run.halo), TJ = fused_interior(EW, run.halo);
         if (TI < 1 || TJ < 1) return SCI_ERR_SHAPE;
         long long tc = 0;
         for (int k = j; k < e; ++k) {

@@ -1,12 +1,13 @@
 // Temporally blocked FGP: K dual updates per launch on a shared-memory tile
 // with a halo (Algorithm 1, ATV-FGP box; Eqs. 29-32 for ITV2D / VTV).
 //
-// A CTA owns an "extended" tile of EH x EW pixels (its interior plus a halo
-// of H pixels on every side) for F frames.  One dual update moves
-// information by one pixel in each direction (theta needs w at the left/up
-// neighbours, the gradient of theta needs the right/down ones), so after K
-// updates the interior widened by H - K >= 1 pixels is exact; the extra pixel
-// feeds D^T p in the output theta = xt - lambda D^T p.
+// A CTA owns an "extended" tile of EH x EW pixels (its interior plus a halo)
+// for F frames.  One dual update moves information by one pixel in each
+// direction (theta needs w at the left/up neighbours, the gradient of theta
+// needs the right/down ones), so after K updates p is exact K pixels in from
+// every tile edge.  The output theta = xt - lambda D^T p also reads p at the
+// left/up neighbour, so the halo is H = K + 1 pixels on the top and left
+// sides and H - 1 = K on the bottom and right (fused_interior).
 //
 // Thread mapping: the tile is cut into NS = NT/EW horizontal strips of Q
 // rows; thread t owns column t % EW of strip t / EW -- Q vertically adjacent
@@ -25,6 +26,7 @@
 // interior are skipped: the band that matters shrinks by one row per update.
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 
 #include "sci_internal.cuh"
 
@@ -37,6 +39,15 @@ __device__ __forceinline__ float rt(float v) {
     T tmp;
     st<T>(&tmp, 0, v);
     return ld<T>(&tmp, 0);
+}
+
+// 1/sqrt(x) by the hardware approximation (relative error below 2^-22),
+// flushing subnormal inputs to zero: only min(1, 1/|a|) is formed from it,
+// which is 1 for every |a| <= 1 either way.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 template <typename T> __device__ __forceinline__ float ldg(const T* p, long long i);
@@ -60,9 +71,14 @@ struct FusedCfg {
     static constexpr int EH = NS * Q;         // tile height (rows)
     static constexpr bool REG = REG_;         // x-tilde and theta of owned slots in registers
     static constexpr bool SKIP = SKIP_;       // skip rows that can no longer reach the interior
-    // shared memory: theta, w_h [F][EH][EW]; w_v [F][NS][EW]; x-tilde [F][EH][EW] unless REG
-    static constexpr size_t SMEM =
-        ((size_t)F * EH * EW * (REG ? 2 : 3) + (size_t)F * NS * EW) * sizeof(float);
+    // Slot arrays (theta, w_h, and x-tilde unless REG) store each frame as one
+    // leading pad word followed by EH rows of EW slots and a trailing pad word:
+    // slot (r, c) sits at 1 + r * LD + c, so its left neighbour at c = 0 and its
+    // right neighbour at c = EW - 1 are pad words, which hold zero.
+    static constexpr int LD = EW + 1;
+    static constexpr int FPP = EH * LD + 1;
+    // shared memory: slot arrays [F][FPP]; w_v [F][NS][EW]
+    static constexpr size_t SMEM = ((size_t)F * FPP * (REG ? 2 : 3) + (size_t)F * NS * EW) * sizeof(float);
     static_assert(NT % EW == 0, "a CTA must cover whole rows");
     static_assert(EW % 32 == 0, "a warp must stay inside one strip row");
 };
@@ -114,15 +130,15 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
                                            float* smem) {
     constexpr int Q = Cfg::Q, F = Cfg::F, EW = Cfg::EW, EH = Cfg::EH, NS = Cfg::NS;
     constexpr bool REG = Cfg::REG, SKIP = Cfg::SKIP;
-    constexpr int FP = EH * EW;  // slots per frame
-    float* s_th = smem;                      // [F][EH][EW]
-    float* s_wh = s_th + F * FP;             // [F][EH][EW]
+    constexpr int LD = Cfg::LD, FP = Cfg::FPP;  // row stride, frame stride (padded)
+    float* s_th = smem;                      // [F][FPP]
+    float* s_wh = s_th + F * FP;             // [F][FPP]
     float* s_wv = s_wh + F * FP;             // [F][NS][EW]: last row of each strip
-    float* s_xt = s_wv + F * NS * EW;        // [F][EH][EW] (only when !REG)
+    float* s_xt = s_wv + F * NS * EW;        // [F][FPP] (only when !REG)
 
     const Geo g = p.g();
     const int H = a.halo;
-    const int TI = EH - 2 * H, TJ = EW - 2 * H;  // interior size
+    const int TI = fused_interior(EH, H), TJ = fused_interior(EW, H);  // interior size
     const int gi0 = by * TI - H, gj0 = bx * TJ - H;
     const int nfr = (F == 1) ? 1 : g.B;          // frames this CTA updates
     const int f0 = (F == 1) ? bz : 0;            // global frame of slot f = 0
@@ -132,7 +148,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
     const int r0 = strip * Q;                    // first row of the strip
     const int gj = gj0 + col;
     const bool col_in = gj >= 0 && gj < g.ny;
-    const bool col_int = col >= H && col < EW - H;
+    const bool col_int = col >= H && col < EW - H + 1;
     const int gi_top = gi0 + r0;
 
     // per-row flags as bit masks (bit q: row r0 + q)
@@ -145,6 +161,14 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
         ah_m |= (unsigned)(in && gj < g.ny - 1) << q;
         av_m |= (unsigned)(in && gi < g.nx - 1) << q;
     }
+    // Strips whose rows all lie inside the image and above its last row need
+    // no row masks (warp-uniform): the column conditions fold into per-thread
+    // steps, zero where the gradient component is defined as zero.  w stays
+    // zero there (it starts at zero and a = w + 0 * (difference) projects to
+    // zero), so the masked and unmasked forms agree.
+    const bool rows_inner = gi_top >= 0 && gi_top + Q - 1 < g.nx - 1;
+    const float step_h = (col_in && gj < g.ny - 1) ? a.step : 0.f;
+    const float step_v = col_in ? a.step : 0.f;
 
     float ph[F][Q], pv[F][Q], wh[F][Q], wv[F][Q];
     float xr[REG ? F : 1][REG ? Q : 1], thr[REG ? F : 1][REG ? Q : 1];
@@ -176,7 +200,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
                     a_wv = ldg<T>(p.st_in(3), gidx);
                 }
             }
-            const int o = f * FP + (r0 + q) * EW + col;
+            const int o = f * FP + 1 + (r0 + q) * LD + col;
             if (REG) xr[REG ? f : 0][REG ? q : 0] = x;
             else s_xt[o] = x;
             s_wh[o] = a_wh;
@@ -186,6 +210,11 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
             wh[f][q] = a_wh;
             wv[f][q] = a_wv;
         }
+    }
+    for (int e = tid; e < F * (EH + 1); e += Cfg::NT) {  // pad words
+        const int f = e / (EH + 1), k = e - f * (EH + 1);
+        s_th[f * FP + k * LD] = 0.f;
+        s_wh[f * FP + k * LD] = 0.f;
     }
     __syncthreads();
 
@@ -204,10 +233,10 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 if (f >= nfr) break;
-                const int o = f * FP + (r0 + q) * EW + col;
+                const int o = f * FP + 1 + (r0 + q) * LD + col;
                 float th = REG ? xr[REG ? f : 0][REG ? q : 0] : s_xt[o];
                 if (!skip_theta) {
-                    const float wl = col > 0 ? s_wh[o - 1] : 0.f;
+                    const float wl = s_wh[o - 1];
                     float wu;
                     if (q > 0) wu = wv[f][q > 0 ? q - 1 : 0];
                     else wu = strip > 0 ? s_wv[(f * NS + strip - 1) * EW + col] : 0.f;
@@ -220,53 +249,64 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
         __syncthreads();
         // ---- a = w + step * D theta (kept in the w registers), projection, momentum ----
         const float c = a.coef[s];
+        auto dual_step = [&](auto masked_c) {
+            constexpr bool MASKED = decltype(masked_c)::value;
 #pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            if (q < qlo || q >= qhi_p) continue;
-            const bool mh = (ah_m >> q) & 1u, mv = (av_m >> q) & 1u;
-            float n2 = 0.f;
+            for (int q = 0; q < Q; ++q) {
+                if (q < qlo || q >= qhi_p) continue;
+                const bool mh = (ah_m >> q) & 1u, mv = (av_m >> q) & 1u;
+                float n2 = 0.f;
 #pragma unroll
-            for (int f = 0; f < F; ++f) {
-                if (f >= nfr) break;
-                const int o = f * FP + (r0 + q) * EW + col;
-                const float t0 = REG ? thr[REG ? f : 0][REG ? q : 0] : s_th[o];
-                const float tr = col < EW - 1 ? s_th[o + 1] : t0;
-                float td;
-                if (q < Q - 1) td = REG ? thr[REG ? f : 0][REG && q < Q - 1 ? q + 1 : 0] : s_th[o + EW];
-                else td = (r0 + q < EH - 1) ? s_th[o + EW] : t0;
-                const float ah = mh ? fmaf(tr - t0, step, wh[f][q]) : 0.f;
-                const float av = mv ? fmaf(td - t0, step, wv[f][q]) : 0.f;
-                wh[f][q] = ah;
-                wv[f][q] = av;
-                if (TV == SCI_TV_VTV) n2 = fmaf(ah, ah, fmaf(av, av, n2));
-            }
-            const float vscale = (TV == SCI_TV_VTV) ? fminf(1.f, rsqrtf(n2)) : 1.f;
-#pragma unroll
-            for (int f = 0; f < F; ++f) {
-                if (f >= nfr) break;
-                float nh = wh[f][q], nv = wv[f][q];
-                if (TV == SCI_TV_ATV) {
-                    nh = fminf(fmaxf(nh, -1.f), 1.f);
-                    nv = fminf(fmaxf(nv, -1.f), 1.f);
-                } else if (TV == SCI_TV_ITV2D) {
-                    // a / max(1, |a|) = a * min(1, 1/|a|); rsqrtf(0) = inf gives 1
-                    const float sc = fminf(1.f, rsqrtf(fmaf(nh, nh, nv * nv)));
-                    nh *= sc;
-                    nv *= sc;
-                } else {
-                    nh *= vscale;
-                    nv *= vscale;
+                for (int f = 0; f < F; ++f) {
+                    if (f >= nfr) break;
+                    const int o = f * FP + 1 + (r0 + q) * LD + col;
+                    const float t0 = REG ? thr[REG ? f : 0][REG ? q : 0] : s_th[o];
+                    const float tr = s_th[o + 1];
+                    float td;
+                    if (q < Q - 1) td = REG ? thr[REG ? f : 0][REG && q < Q - 1 ? q + 1 : 0] : s_th[o + LD];
+                    else td = (r0 + q < EH - 1) ? s_th[o + LD] : t0;
+                    float ah, av;
+                    if (MASKED) {
+                        ah = mh ? fmaf(tr - t0, step, wh[f][q]) : 0.f;
+                        av = mv ? fmaf(td - t0, step, wv[f][q]) : 0.f;
+                    } else {
+                        ah = fmaf(tr - t0, step_h, wh[f][q]);
+                        av = fmaf(td - t0, step_v, wv[f][q]);
+                    }
+                    wh[f][q] = ah;
+                    wv[f][q] = av;
+                    if (TV == SCI_TV_VTV) n2 = fmaf(ah, ah, fmaf(av, av, n2));
                 }
-                const float wnh = fmaf(c, nh - ph[f][q], nh);
-                const float wnv = fmaf(c, nv - pv[f][q], nv);
-                ph[f][q] = nh;
-                pv[f][q] = nv;
-                wh[f][q] = wnh;
-                wv[f][q] = wnv;
-                s_wh[f * FP + (r0 + q) * EW + col] = wnh;
-                if (q == Q - 1) s_wv[(f * NS + strip) * EW + col] = wnv;
+                const float vscale = (TV == SCI_TV_VTV) ? fminf(1.f, rsqrt_ftz(n2)) : 1.f;
+#pragma unroll
+                for (int f = 0; f < F; ++f) {
+                    if (f >= nfr) break;
+                    float nh = wh[f][q], nv = wv[f][q];
+                    if (TV == SCI_TV_ATV) {
+                        nh = fminf(fmaxf(nh, -1.f), 1.f);
+                        nv = fminf(fmaxf(nv, -1.f), 1.f);
+                    } else if (TV == SCI_TV_ITV2D) {
+                        // a / max(1, |a|) = a * min(1, 1/|a|); 1/sqrt(0) = inf gives 1
+                        const float sc = fminf(1.f, rsqrt_ftz(fmaf(nh, nh, nv * nv)));
+                        nh *= sc;
+                        nv *= sc;
+                    } else {
+                        nh *= vscale;
+                        nv *= vscale;
+                    }
+                    const float wnh = fmaf(c, nh - ph[f][q], nh);
+                    const float wnv = fmaf(c, nv - pv[f][q], nv);
+                    ph[f][q] = nh;
+                    pv[f][q] = nv;
+                    wh[f][q] = wnh;
+                    wv[f][q] = wnv;
+                    s_wh[f * FP + 1 + (r0 + q) * LD + col] = wnh;
+                    if (q == Q - 1) s_wv[(f * NS + strip) * EW + col] = wnv;
+                }
             }
-        }
+        };
+        if (rows_inner) dual_step(std::false_type{});
+        else dual_step(std::true_type{});
         __syncthreads();
     }
 
@@ -276,14 +316,14 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const int r = r0 + q;
-            if (!((in_m >> q) & 1u) || !col_int || r < H || r >= EH - H) continue;
+            if (!((in_m >> q) & 1u) || !col_int || r < H || r >= EH - H + 1) continue;
             const long long pix = (long long)(gi_top + q) * g.ny + gj;
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 if (f >= nfr) break;
                 const long long gidx = (long long)(f0 + f) * g.n + pix;
                 if (a.first && a.mode != OuterMode::Prox)
-                    st<T>(p.xt(), gidx, REG ? xr[REG ? f : 0][REG ? q : 0] : s_xt[f * FP + r * EW + col]);
+                    st<T>(p.xt(), gidx, REG ? xr[REG ? f : 0][REG ? q : 0] : s_xt[f * FP + 1 + r * LD + col]);
                 st<T>(p.st_out(0), gidx, ph[f][q]);
                 st<T>(p.st_out(1), gidx, pv[f][q]);
                 st<T>(p.st_out(2), gidx, wh[f][q]);
@@ -299,7 +339,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
 #pragma unroll
         for (int f = 0; f < F; ++f) {
             if (f >= nfr) break;
-            s_wh[f * FP + (r0 + q) * EW + col] = ph[f][q];
+            s_wh[f * FP + 1 + (r0 + q) * LD + col] = ph[f][q];
             if (q == Q - 1) s_wv[(f * NS + strip) * EW + col] = pv[f][q];
         }
     }
@@ -310,12 +350,12 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const int r = r0 + q;
-            const bool mine = ((in_m >> q) & 1u) && col_int && r >= H && r < EH - H;
+            const bool mine = ((in_m >> q) & 1u) && col_int && r >= H && r < EH - H + 1;
             const long long pix = mine ? (long long)(gi_top + q) * g.ny + gj : 0;
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 if (f >= nfr) break;
-                s_th[f * FP + r * EW + col] = mine ? ldg<T>(p.u_in(), (long long)(f0 + f) * g.n + pix) : 0.f;
+                s_th[f * FP + 1 + r * LD + col] = mine ? ldg<T>(p.u_in(), (long long)(f0 + f) * g.n + pix) : 0.f;
             }
         }
     }
@@ -323,13 +363,13 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int r = r0 + q;
-        if (!((in_m >> q) & 1u) || !col_int || r < H || r >= EH - H) continue;
+        if (!((in_m >> q) & 1u) || !col_int || r < H || r >= EH - H + 1) continue;
         const long long pix = (long long)(gi_top + q) * g.ny + gj;
 #pragma unroll
         for (int f = 0; f < F; ++f) {
             if (f >= nfr) break;
-            const int o = f * FP + r * EW + col;
-            const float pl = col > 0 ? s_wh[o - 1] : 0.f;
+            const int o = f * FP + 1 + r * LD + col;
+            const float pl = s_wh[o - 1];
             float pu;
             if (q > 0) pu = pv[f][q > 0 ? q - 1 : 0];
             else pu = strip > 0 ? s_wv[(f * NS + strip - 1) * EW + col] : 0.f;
@@ -403,7 +443,7 @@ std::atomic<unsigned long long> g_attr_done[64];
 
 template <typename T, int TV, class Cfg>
 bool launch_cfg(int slot, const FusedArgs& a, const FusedBufs<T>& b, cudaStream_t s) {
-    const int TI = Cfg::EH - 2 * a.halo, TJ = Cfg::EW - 2 * a.halo;
+    const int TI = fused_interior(Cfg::EH, a.halo), TJ = fused_interior(Cfg::EW, a.halo);
     if (TI < 1 || TJ < 1 || a.halo < a.K + 1 || a.K < 1 || a.K > kMaxFuse) return false;
     const dim3 grid((unsigned)((a.g.ny + TJ - 1) / TJ), (unsigned)((a.g.nx + TI - 1) / TI),
                     (unsigned)(Cfg::F == 1 ? a.g.B : 1));

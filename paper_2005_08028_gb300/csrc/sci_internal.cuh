@@ -81,7 +81,7 @@ struct FusedArgs {
     Geo g;
     OuterMode mode;
     int K;                  // dual updates in this launch
-    int halo;               // tile halo, >= K + 1
+    int halo;               // top / left tile halo, >= K + 1 (bottom / right: halo - 1)
     int first;              // 1: w = p = 0 and x-tilde formed here (from theta, r or xin)
     int last;               // 1: write theta (and u, x_out); 0: carry p, w (and x-tilde)
     float lambda, step;     // lambda and 1/(8 lambda)
@@ -124,6 +124,10 @@ struct BatchItem {
     T* xt;
     T* st[2][4];             // ping-pong carried duals (p_h, p_v, w_h, w_v)
 };
+// Interior rows (columns) of a fused tile of `extent` rows (columns) whose
+// top (left) halo is `halo` and bottom (right) halo is halo - 1.
+__host__ __device__ inline int fused_interior(int extent, int halo) { return extent - 2 * halo + 1; }
+
 // Largest halo the fused kernel supports for this TV / frame count (0: none).
 int fused_max_halo(int tv, int B);
 // Tile configuration class for this TV / frame count (0: none) and its tile size.
