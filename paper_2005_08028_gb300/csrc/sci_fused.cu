@@ -174,41 +174,93 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
     float xr[REG ? F : 1][REG ? Q : 1], thr[REG ? F : 1][REG ? Q : 1];
 
     // ---- load x-tilde (and the carried duals) for the whole extended tile ----
+    // Every load is issued unconditionally -- a pixel outside the image reads
+    // pixel 0 of its frame and is zeroed afterwards -- and none is consumed
+    // before all are issued, so a thread's loads are in flight together
+    // rather than one row at a time.
+    auto pix_of = [&](int q) -> long long {
+        return ((in_m >> q) & 1u) ? (long long)(gi_top + q) * g.ny + gj : 0;
+    };
+    if (!a.first) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const long long pix = pix_of(q);
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                if (f >= nfr) break;
+                const long long gidx = (long long)(f0 + f) * g.n + pix;
+                ph[f][q] = ldg<T>(p.st_in(0), gidx);
+                pv[f][q] = ldg<T>(p.st_in(1), gidx);
+                wh[f][q] = ldg<T>(p.st_in(2), gidx);
+                wv[f][q] = ldg<T>(p.st_in(3), gidx);
+            }
+        }
+    }
+    // x-tilde as loaded: straight into the x-tilde registers of REG tiles,
+    // into staging registers otherwise
+    float xs[REG ? 1 : F][REG ? 1 : Q];
+    auto xq = [&](int f, int q) -> float& { return REG ? xr[REG ? f : 0][REG ? q : 0] : xs[REG ? 0 : f][REG ? 0 : q]; };
+    if (a.mode == OuterMode::Prox) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const long long pix = pix_of(q);
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                if (f >= nfr) break;
+                xq(f, q) = __ldg(p.xin() + (long long)(f0 + f) * g.n + pix);
+            }
+        }
+    } else if (a.first) {
+        uint32_t word[Q];
+        float rv[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const long long pix = pix_of(q);
+            word[q] = __ldg(p.bits() + pix);
+            rv[q] = __ldg(p.r() + pix);
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                if (f >= nfr) break;
+                xq(f, q) = ldg<T>(p.theta_in(), (long long)(f0 + f) * g.n + pix);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                if (f >= nfr) break;
+                xq(f, q) = rt<T>(xq(f, q) + mask_bit(word[q], f0 + f) * rv[q]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const long long pix = pix_of(q);
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                if (f >= nfr) break;
+                xq(f, q) = ldg<T>(p.xt(), (long long)(f0 + f) * g.n + pix);
+            }
+        }
+    }
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const bool in = (in_m >> q) & 1u;
-        const long long pix = in ? (long long)(gi_top + q) * g.ny + gj : 0;
-        uint32_t word = 0;
-        float rv = 0.f;
-        if (in && a.first && a.mode != OuterMode::Prox) {
-            word = __ldg(p.bits() + pix);
-            rv = __ldg(p.r() + pix);
-        }
 #pragma unroll
         for (int f = 0; f < F; ++f) {
             if (f >= nfr) break;
-            const long long gidx = (long long)(f0 + f) * g.n + pix;
-            float x = 0.f, a_ph = 0.f, a_pv = 0.f, a_wh = 0.f, a_wv = 0.f;
-            if (in) {
-                if (a.mode == OuterMode::Prox) x = __ldg(p.xin() + gidx);
-                else if (a.first) x = rt<T>(ldg<T>(p.theta_in(), gidx) + mask_bit(word, f0 + f) * rv);
-                else x = ldg<T>(p.xt(), gidx);
-                if (!a.first) {
-                    a_ph = ldg<T>(p.st_in(0), gidx);
-                    a_pv = ldg<T>(p.st_in(1), gidx);
-                    a_wh = ldg<T>(p.st_in(2), gidx);
-                    a_wv = ldg<T>(p.st_in(3), gidx);
-                }
+            const float x = in ? xq(f, q) : 0.f;
+            if (a.first || !in) {
+                ph[f][q] = 0.f;
+                pv[f][q] = 0.f;
+                wh[f][q] = 0.f;
+                wv[f][q] = 0.f;
             }
             const int o = f * FP + 1 + (r0 + q) * LD + col;
             if (REG) xr[REG ? f : 0][REG ? q : 0] = x;
             else s_xt[o] = x;
-            s_wh[o] = a_wh;
-            if (q == Q - 1) s_wv[(f * NS + strip) * EW + col] = a_wv;
-            ph[f][q] = a_ph;
-            pv[f][q] = a_pv;
-            wh[f][q] = a_wh;
-            wv[f][q] = a_wv;
+            s_wh[o] = wh[f][q];
+            if (q == Q - 1) s_wv[(f * NS + strip) * EW + col] = wv[f][q];
         }
     }
     for (int e = tid; e < F * (EH + 1); e += Cfg::NT) {  // pad words
