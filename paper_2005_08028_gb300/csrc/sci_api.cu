@@ -107,9 +107,7 @@ int choose_fuse(int tv, int B, int S, int fuse_k) {
     if (fuse_k < 0) return 0;
     const int maxh = fused_max_halo(tv, B);
     if (maxh < 2) return 0;
-    int K = maxh - 1;
-    if (tv == SCI_TV_VTV) K = std::min(K, 4);  // 32x32 tiles: a small halo wins (measured)
-    else K = std::min(K, 10);
+    int K = std::min(maxh - 1, default_fuse(tv));
     if (fuse_k > 0) K = std::min(fuse_k, maxh - 1);
     K = std::min(K, kMaxFuse);
     return std::max(1, std::min(K, S));

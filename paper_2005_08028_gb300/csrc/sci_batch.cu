@@ -16,6 +16,11 @@
 
 namespace sci {
 
+// Default dual updates per fused launch (measured on 512x512x10: one-frame
+// tiles run all 10 updates of an outer iteration in one launch; the 32 x 32
+// VTV tiles are fastest at 6, i.e. launches of 6 + 4).
+int default_fuse(int tv) { return tv == SCI_TV_VTV ? 6 : 10; }
+
 namespace {
 
 template <typename T>
@@ -91,8 +96,6 @@ size_t per_problem_bytes(const sci_problem& p, size_t es) {
     const size_t n = (size_t)p.nx * p.ny, N = n * (size_t)p.B;
     return align256(n * 4) * 2 + align256(N * es) * 11;  // rinv, r; xt, theta x2, duals x8
 }
-
-int default_fuse(int tv) { return tv == SCI_TV_VTV ? 4 : 10; }
 
 sci_status make_plan(const sci_problem* probs, int count, const sci_params* prm, BatchPlan* plan) {
     if (probs == nullptr || count < 1 || prm == nullptr) return SCI_ERR_ARG;

@@ -178,9 +178,8 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
     // pixel 0 of its frame and is zeroed afterwards -- and none is consumed
     // before all are issued, so a thread's loads are in flight together
     // rather than one row at a time.
-    auto pix_of = [&](int q) -> long long {
-        return ((in_m >> q) & 1u) ? (long long)(gi_top + q) * g.ny + gj : 0;
-    };
+    const long long pix_top = (long long)gi_top * g.ny + gj;
+    auto pix_of = [&](int q) -> long long { return ((in_m >> q) & 1u) ? pix_top + (long long)q * g.ny : 0; };
     if (!a.first) {
 #pragma unroll
         for (int q = 0; q < Q; ++q) {

@@ -124,6 +124,9 @@ struct BatchItem {
     T* xt;
     T* st[2][4];             // ping-pong carried duals (p_h, p_v, w_h, w_v)
 };
+// Default dual updates per fused launch for this TV form (sci_batch.cu).
+int default_fuse(int tv);
+
 // Interior rows (columns) of a fused tile of `extent` rows (columns) whose
 // top (left) halo is `halo` and bottom (right) halo is halo - 1.
 __host__ __device__ inline int fused_interior(int extent, int halo) { return extent - 2 * halo + 1; }
