@@ -302,6 +302,13 @@ def _peaks():
 
 ALU_OPS_PER_UPDATE = 20  # FP32 operations per voxel per FGP dual update (FMA = 1)
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per k_fgp_fused
+# launch of the roofline case below (one prox launch on 10 x 512 x 512 FP32,
+# default updates per launch), from one ncu capture of the current kernel
+# (profiles/k_fgp_fused_sci512x512x10.md).  The launch must move at least the
+# 10.49 MB input; its 10.49 MB output stays in L2.
+NCU_DRAM_BYTES_PER_LAUNCH = {"atv": 14286848, "itv2d": 11173888, "vtv": 10554368}
+
 
 def _alu_peak():
     """FP32 lane-operations per second: 152 SMs x 128 FP32 lanes x the max SM clock."""
@@ -319,7 +326,7 @@ def _roofline(pkg, torch, dev, stream, c, B, nx, ny):
     N = B * nx * ny
     x = torch.rand((B, nx, ny), device=dev)
     work = pkg.Workspace(dev)
-    per_tv, ops, ms_total = {}, 0.0, 0.0
+    per_tv, ops, ms_total, traffic = {}, 0.0, 0.0, []
     for tv in ("atv", "itv2d", "vtv"):
         K = pkg.sci_fused_updates(tv, B, c["inner"], 0)
         if K <= 0:
@@ -334,7 +341,9 @@ def _roofline(pkg, torch, dev, stream, c, B, nx, ny):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1) / reps
-        per_tv[tv] = {"updates_per_launch": K, "launch_ms": round(ms, 5)}
+        per_tv[tv] = {"updates_per_launch": K, "launch_ms": round(ms, 5),
+                      "dram_bytes_ncu": NCU_DRAM_BYTES_PER_LAUNCH.get(tv)}
+        traffic.append(NCU_DRAM_BYTES_PER_LAUNCH.get(tv))
         ops += ALU_OPS_PER_UPDATE * N * K
         ms_total += ms
     achieved = ops / (ms_total * 1e-3) / 1e12
@@ -342,7 +351,10 @@ def _roofline(pkg, torch, dev, stream, c, B, nx, ny):
     return {"kernel": "k_fgp_fused (temporally blocked FGP dual updates)", "bound": "alu",
             "achieved": round(achieved, 3), "peak": round(peak, 3),
             "peak_kind": "derived: 152 SMs x 128 FP32 lanes x max SM clock", "unit": "T FP32-op/s",
-            "frac": round(achieved / peak, 4), "traffic": None,
+            "frac": round(achieved / peak, 4),
+            "traffic": (round(sum(traffic) / len(traffic)) if traffic and None not in traffic
+                        and (B, nx, ny) == (10, 512, 512) else None),
+            "traffic_unit": "bytes per launch (mean over the TV forms, ncu)",
             "alg_ops_per_voxel_update": ALU_OPS_PER_UPDATE, "per_tv": per_tv}
 
 
