@@ -35,6 +35,24 @@ template <> __device__ __forceinline__ void st<__half>(__half* p, long long i, f
     p[i] = __float2half_rn(v);
 }
 
+// Two-step read-only load: ldraw issues the load and leaves a 16-bit field's
+// bits in a float register; cvraw converts them.  Kernels that read many
+// values issue every ldraw before the first cvraw: the 16-bit conversion,
+// placed right after each load, kept the loads from overlapping.  FP32 fields
+// pass through both steps unchanged.
+template <typename T> __device__ __forceinline__ float ldraw(const T* p, long long i) {
+    return __uint_as_float((unsigned)__ldg(reinterpret_cast<const unsigned short*>(p) + i));
+}
+template <> __device__ __forceinline__ float ldraw<float>(const float* p, long long i) { return __ldg(p + i); }
+template <typename T> __device__ __forceinline__ float cvraw(float r);
+template <> __device__ __forceinline__ float cvraw<float>(float r) { return r; }
+template <> __device__ __forceinline__ float cvraw<__half>(float r) {
+    return __half2float(__ushort_as_half((unsigned short)__float_as_uint(r)));
+}
+template <> __device__ __forceinline__ float cvraw<__nv_bfloat16>(float r) {
+    return __bfloat162float(__ushort_as_bfloat16((unsigned short)__float_as_uint(r)));
+}
+
 template <typename T> struct dtype_of;
 template <> struct dtype_of<float> { static constexpr int value = SCI_F32; };
 template <> struct dtype_of<__nv_bfloat16> { static constexpr int value = SCI_BF16; };

@@ -52,12 +52,17 @@ __device__ __forceinline__ float rsqrt_ftz(float x) {
 
 template <typename T> __device__ __forceinline__ float ldg(const T* p, long long i);
 template <> __device__ __forceinline__ float ldg<float>(const float* p, long long i) { return __ldg(p + i); }
+// 16-bit fields are read as raw unsigned shorts through the compiler's own
+// read-only load, which the scheduler can batch like any other load (the
+// __half / __nv_bfloat16 overloads of __ldg are inline assembly, and their
+// loads were waited on one at a time).
 template <> __device__ __forceinline__ float ldg<__nv_bfloat16>(const __nv_bfloat16* p, long long i) {
-    return __bfloat162float(__ldg(p + i));
+    return __bfloat162float(__ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short*>(p) + i)));
 }
 template <> __device__ __forceinline__ float ldg<__half>(const __half* p, long long i) {
-    return __half2float(__ldg(p + i));
+    return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p) + i)));
 }
+
 
 // Compile-time tile configuration.
 template <int NT_, int Q_, int F_, int EW_LOG2_, bool REG_, bool SKIP_>
@@ -188,10 +193,10 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
             for (int f = 0; f < F; ++f) {
                 if (f >= nfr) break;
                 const long long gidx = (long long)(f0 + f) * g.n + pix;
-                ph[f][q] = ldg<T>(p.st_in(0), gidx);
-                pv[f][q] = ldg<T>(p.st_in(1), gidx);
-                wh[f][q] = ldg<T>(p.st_in(2), gidx);
-                wv[f][q] = ldg<T>(p.st_in(3), gidx);
+                ph[f][q] = ldraw<T>(p.st_in(0), gidx);
+                pv[f][q] = ldraw<T>(p.st_in(1), gidx);
+                wh[f][q] = ldraw<T>(p.st_in(2), gidx);
+                wv[f][q] = ldraw<T>(p.st_in(3), gidx);
             }
         }
     }
@@ -220,7 +225,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 if (f >= nfr) break;
-                xq(f, q) = ldg<T>(p.theta_in(), (long long)(f0 + f) * g.n + pix);
+                xq(f, q) = ldraw<T>(p.theta_in(), (long long)(f0 + f) * g.n + pix);
             }
         }
 #pragma unroll
@@ -228,7 +233,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 if (f >= nfr) break;
-                xq(f, q) = rt<T>(xq(f, q) + mask_bit(word[q], f0 + f) * rv[q]);
+                xq(f, q) = rt<T>(cvraw<T>(xq(f, q)) + mask_bit(word[q], f0 + f) * rv[q]);
             }
         }
     } else {
@@ -238,7 +243,28 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 if (f >= nfr) break;
-                xq(f, q) = ldg<T>(p.xt(), (long long)(f0 + f) * g.n + pix);
+                xq(f, q) = ldraw<T>(p.xt(), (long long)(f0 + f) * g.n + pix);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                if (f >= nfr) break;
+                xq(f, q) = cvraw<T>(xq(f, q));
+            }
+        }
+    }
+    if (!a.first) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                if (f >= nfr) break;
+                ph[f][q] = cvraw<T>(ph[f][q]);
+                pv[f][q] = cvraw<T>(pv[f][q]);
+                wh[f][q] = cvraw<T>(wh[f][q]);
+                wv[f][q] = cvraw<T>(wv[f][q]);
             }
         }
     }
