@@ -490,28 +490,35 @@ k_fgp_fused(const __grid_constant__ FusedArgs a, const __grid_constant__ FusedBu
 
 // Many problems of one tile class in one launch: work item w is a tile of
 // the problem whose [cta_begin, next cta_begin) range holds w.  A persistent
-// grid walks the work items (largest problems first).  Each class has its own
-// kernel: one kernel holding every class's tile code needs more registers
-// than an SM has and spills.
-template <typename T, int TV, class Cfg>
+// grid walks the work items (largest problems first), or each CTA takes one
+// work item (PERSIST = false), where the loop's own live values would push the
+// tile code into spilling.
+// Each class has its own kernel: one kernel holding every class's tile code
+// needs more registers than an SM has and spills.
+template <typename T, int TV, class Cfg, bool PERSIST>
 __global__ void __launch_bounds__(Cfg::NT, 1)
 k_fgp_fused_batched(const __grid_constant__ FusedArgs a, const BatchItem<T>* __restrict__ items, int nitems,
                     int total, int tpar, int spar, int want_x) {
     extern __shared__ float smem[];
-    for (int w = blockIdx.x; w < total; w += gridDim.x) {
-        int lo = 0, hi = nitems - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (items[mid].cta_begin <= w) lo = mid;
-            else hi = mid - 1;
+    __shared__ int s_item;
+    for (int w = blockIdx.x; w < total; w += (PERSIST ? gridDim.x : total)) {
+        // The problem whose work-item range holds w: every thread tests a few
+        // entries (one round of loads, where a binary search takes log2(nitems)
+        // dependent ones before the tile's own loads can start).
+        for (int i = threadIdx.x; i < nitems; i += Cfg::NT) {
+            const int b = items[i].cta_begin;
+            const int e = i + 1 < nitems ? items[i + 1].cta_begin : total;
+            if (b <= w && w < e) s_item = i;
         }
-        const BatchItem<T>* it = items + lo;
+        __syncthreads();
+        const BatchItem<T>* it = items + s_item;
         const int local = w - it->cta_begin;
         const int tiles_x = it->tiles_x, per_frame = tiles_x * it->tiles_y;
         const int bz = local / per_frame, rem = local - bz * per_frame;
         const int by = rem / tiles_x, bx = rem - by * tiles_x;
         const BatchProb<T> p{it, tpar, spar, want_x};
         fused_tile<T, TV, Cfg>(a, p, bx, by, bz, smem);
+        if (!PERSIST) break;
         __syncthreads();  // shared memory is reused by the next work item
     }
 }
@@ -599,10 +606,19 @@ void fused_class_dims(int cls, int* EH, int* EW) {
 namespace {
 std::atomic<unsigned long long> g_battr_done[64];
 
+// VTV tiles run one work item per CTA: with the persistent loop their
+// kernels spill (the 24-frame tile by about 0.8 KB a thread); one-frame tiles
+// spill less with it.
+template <class Cfg>
+constexpr bool batched_persist() {
+    return Cfg::F == 1;
+}
+
 template <typename T, int TV, class Cfg>
 bool launch_batched_cfg(int slot, const FusedArgs& a, const BatchItem<T>* items, int nitems, int total,
                         int tpar, int spar, int want_x, cudaStream_t s) {
-    auto k = k_fgp_fused_batched<T, TV, Cfg>;
+    constexpr bool persist = batched_persist<Cfg>();
+    auto k = k_fgp_fused_batched<T, TV, Cfg, persist>;
     int dev = 0;
     cudaGetDevice(&dev);
     const unsigned long long bit = 1ull << (dev & 63);
@@ -613,7 +629,7 @@ bool launch_batched_cfg(int slot, const FusedArgs& a, const BatchItem<T>* items,
     }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = std::max(1, std::min(sms, total));
+    const int grid = persist ? std::max(1, std::min(sms, total)) : std::max(1, total);
     k<<<grid, Cfg::NT, Cfg::SMEM, s>>>(a, items, nitems, total, tpar, spar, want_x);
     return true;
 }
