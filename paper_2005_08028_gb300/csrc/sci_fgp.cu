@@ -154,13 +154,14 @@ __global__ void k_fgp_out(OutArgs a, const T* __restrict__ xt, const T* __restri
         float acc = 0.f, acc_theta = 0.f;
         for (int k = 0; k < g.B; ++k) {
             const long long base = k * g.n + pix;
-            float div = 0.f;
-            if (j >= 1) div += ld<T>(p, base - 1);
-            if (j < g.ny - 1) div -= ld<T>(p, base);
-            if (i >= 1) div += ld<T>(p + N, base - g.ny);
-            if (i < g.nx - 1) div -= ld<T>(p + N, base);
+            // D^T p grouped as (p_h left - p_h) + (p_v up - p_v), the order the
+            // dual-update kernels use, so both FGP paths round alike
+            const float pl = j >= 1 ? ld<T>(p, base - 1) : 0.f;
+            const float ph = j < g.ny - 1 ? ld<T>(p, base) : 0.f;
+            const float pu = i >= 1 ? ld<T>(p + N, base - g.ny) : 0.f;
+            const float pv = i < g.nx - 1 ? ld<T>(p + N, base) : 0.f;
             const float x0 = a.mode == OuterMode::Prox ? a.xin[base] : ld<T>(xt, base);
-            const float th = x0 - lambda * div;
+            const float th = x0 - lambda * ((pl - ph) + (pu - pv));
             if (a.mode == OuterMode::Prox) {
                 a.theta_f32[base] = th;
                 continue;
