@@ -3,16 +3,22 @@
 // Used by the learned TV prox (its two hidden 32->32 layers, forward and
 // input-gradient passes).
 //
-// Implicit GEMM: an output tile is 128 voxels (4 rows x 32 columns of one
-// frame of one volume) x 32 output channels.  For each of the 27 taps the
-// A operand is the 128 x 32 block of input activations shifted by the tap,
-// taken from TMA boxes of a 5-D tensor map over the channels-last
-// activations [volume][frame][row][column][channel] -- one 6-row box per
-// (dz, dx) serves the three dy taps; out-of-range voxels arrive as zeros,
-// which is the convolution's zero padding -- and the B operand is that tap's
-// 32 x 32 weight block, resident in shared memory for the whole kernel.  Each
-// tap is two tcgen05.mma (M = 128, N = 32, K = 16) accumulating into one
-// 128-lane x 32-column FP32 tile of tensor memory.
+// Implicit GEMM with the three column taps side by side.  A tile covers 4
+// rows x 30 output columns of one frame of one volume.  Its A operand is a
+// 128-voxel window (4 rows x 32 columns, starting one column left of the
+// tile) of the channels-last activations [volume][frame][row][column]
+// [channel], taken from TMA boxes of a 5-D tensor map -- one 6-row box per dz
+// serves the three dy windows (rows 2 KB apart); out-of-range voxels arrive
+// as zeros, which is the convolution's zero padding.  Its B operand for a
+// (dz, dy) pair is the 96 x 32 block of the three dx taps' weights (output
+// channel blocks for dx = -1, 0, +1), resident in shared memory for the whole
+// kernel.  Two tcgen05.mma (M = 128, N = 96, K = 16) per (dz, dy) accumulate
+// G_dx[v][c] = sum over dz, dy of act[v + (dz, dy)] . W[dz, dy, dx][c] in a
+// 128-lane x 96-column FP32 tile of tensor memory, and the epilogue forms
+// out[x] = G_-1[x - 1] + G_0[x] + G_+1[x + 1] with two warp shuffles per
+// channel (a warp holds one row of the window).  Eighteen N = 96 MMAs replace
+// 54 N = 32 ones per tile: with 32 output channels the MMA issue rate, not
+// the tensor datapath, bounds the narrow form.
 //
 // Warp-specialised and persistent: one lane issues TMA loads into a ring of
 // A stages, one lane issues the MMAs (a commit frees each stage), and four
@@ -40,7 +46,10 @@ constexpr int kC = 32;
 // above and one below) of one frame; the three row taps (dy = -1, 0, +1) of a
 // (dz, dx) pair are 128-row windows of it starting 32 rows (2 KB) apart, which
 // keeps every window aligned to the 512-byte period of the 64-byte swizzle.
-constexpr int kBW = 32, kBH = 4;
+constexpr int kBW = 32, kBH = 4;                             // A window: 4 rows x 32 columns
+constexpr int kOutW = kBW - 2;                               // output columns per tile
+constexpr int kN = 3 * kC;                                   // MMA N: three dx taps x 32 channels
+constexpr uint32_t kAccCols = 128;                           // tensor-memory columns per accumulator
 constexpr uint32_t kRowBytes = kC * 2;                       // 64 B per voxel
 constexpr uint32_t kABytes = kBW * (kBH + 2) * kRowBytes;    // 12 KB per A stage
 constexpr uint32_t kWTapBytes = kC * kC * 2;       // 2 KB per tap
@@ -104,8 +113,8 @@ __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
     return d;
 }
 
-// kind::f16 instruction descriptor: D = FP32, A = B = BF16, both K-major, M = 128, N = 32.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kC >> 3) << 17) |
+// kind::f16 instruction descriptor: D = FP32, A = B = BF16, both K-major, M = 128, N = 96.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
                             ((uint32_t)(kTileM >> 4) << 24);
 
 __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
@@ -138,7 +147,7 @@ __device__ __forceinline__ void tmem_ld_32cols(uint32_t taddr, float (&v)[32]) {
 
 struct ConvTcArgs {
     int nvol, D, H, W;      // volumes and their frames x rows x columns
-    int BW, BH;             // tile: BH rows x BW columns (BW * BH = 128)
+    int BW, BH;             // tile: BH rows x BW output columns
     int tiles_w, tiles_h;   // tiles per row block / per frame
     long long ntiles;
     int mode;               // ConvEpilogue
@@ -153,9 +162,9 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 }
 
 // Warp roles: warps 0-3 run the epilogue (warp w reads tensor-memory lanes
-// 32w..32w+31, i.e. tile voxels 32w..32w+31); lane 0 of warp 4 issues the
-// TMA loads; lane 0 of warp 5 issues the MMAs.  The accumulator is double
-// buffered in tensor memory (2 x 32 columns), so the epilogue of tile j
+// 32w..32w+31, i.e. window row w); lane 0 of warp 4 issues the TMA loads;
+// lane 0 of warp 5 issues the MMAs.  The accumulator is double buffered in
+// tensor memory (2 x 128 columns, 96 used), so the epilogue of tile j
 // overlaps the MMAs of tile j + 1 and the loads run ahead across tiles.
 constexpr int kThreads = 192;
 
@@ -191,7 +200,7 @@ k_conv3d_c32_tc(const __grid_constant__ CUtensorMap act_map, const __grid_consta
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 5) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(s_tmem))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(s_tmem))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -214,12 +223,11 @@ k_conv3d_c32_tc(const __grid_constant__ CUtensorMap act_map, const __grid_consta
             const int z = (int)(tr % a.D), vol = (int)(tr / a.D);
             const int w0 = tw * a.BW, h0 = th * a.BH;
             bool ok = true;
-            for (int k = 0; k < 9; ++k, ++q) {  // (dz, dx) pairs
+            for (int k = 0; k < 3; ++k, ++q) {  // dz = k - 1
                 const uint32_t s = q % kStages, use = q / kStages;
                 if (use > 0 && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1)) { ok = false; break; }
-                const int dz = k / 3 - 1, dx = k % 3 - 1;
                 mbar_expect_tx(bar_full + 8 * s, kABytes);
-                tma_load_5d(smem_u32(s_a + s * kABytes), &act_map, bar_full + 8 * s, 0, w0 + dx, h0 - 1, z + dz,
+                tma_load_5d(smem_u32(s_a + s * kABytes), &act_map, bar_full + 8 * s, 0, w0 - 1, h0 - 1, z + k - 1,
                             vol);
             }
             if (!ok) { *s_abort = 1; atomicExch(a.err, 1); break; }
@@ -238,15 +246,15 @@ k_conv3d_c32_tc(const __grid_constant__ CUtensorMap act_map, const __grid_consta
             const uint32_t b = (uint32_t)(j & 1), use_b = (uint32_t)(j >> 1);
             if (use_b > 0 && !mbar_wait(bar_acce + 8 * b, (use_b - 1) & 1)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t d = tmem + b * 32;
-            for (int k = 0; k < 9; ++k, ++q) {
+            const uint32_t d = tmem + b * kAccCols;
+            for (int k = 0; k < 3; ++k, ++q) {  // dz = k - 1
                 const uint32_t s = q % kStages, use = q / kStages;
                 if (!mbar_wait(bar_full + 8 * s, use & 1)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const int dz = k / 3 - 1, dx = k % 3 - 1;
 #pragma unroll
                 for (int dyi = 0; dyi < 3; ++dyi) {
-                    const int t = (dz + 1) * 9 + dyi * 3 + (dx + 1);
+                    // taps (dz, dy, dx = -1..+1) are consecutive 2 KB blocks: one N = 96 operand
+                    const int t = k * 9 + dyi * 3;
                     const uint32_t abase = smem_u32(s_a + s * kABytes) + (uint32_t)dyi * kBW * kRowBytes;
                     const uint32_t bbase = smem_u32(s_w + t * kWTapBytes);
                     umma_bf16(d, smem_desc_sw64(abase), smem_desc_sw64(bbase), (k > 0 || dyi > 0) ? 1u : 0u);
@@ -275,18 +283,26 @@ k_conv3d_c32_tc(const __grid_constant__ CUtensorMap act_map, const __grid_consta
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            float v[32];
-            tmem_ld_32cols(tmem + b * 32 + ((uint32_t)(warp * 32) << 16), v);
+            // lane x of warp w holds window voxel (row w, column x); the output
+            // at tile column i = x is G_-1[x] + G_0[x + 1] + G_+1[x + 2]
+            float v[32], g[32];
+            const uint32_t lanes = (uint32_t)(warp * 32) << 16;
+            tmem_ld_32cols(tmem + b * kAccCols + lanes, v);
+            tmem_ld_32cols(tmem + b * kAccCols + 32 + lanes, g);
+#pragma unroll
+            for (int c = 0; c < 32; ++c) v[c] += __shfl_down_sync(0xffffffffu, g[c], 1);
+            tmem_ld_32cols(tmem + b * kAccCols + 64 + lanes, g);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(bar_acce + 8 * b);  // this warp's lanes of buffer b are free
+#pragma unroll
+            for (int c = 0; c < 32; ++c) v[c] += __shfl_down_sync(0xffffffffu, g[c], 2);
             long long tr = blockIdx.x + j * gridDim.x;
             const int tw = (int)(tr % a.tiles_w); tr /= a.tiles_w;
             const int th = (int)(tr % a.tiles_h); tr /= a.tiles_h;
             const int z = (int)(tr % a.D), vol = (int)(tr / a.D);
-            const int r = tid;  // tile row = voxel
-            const int hh = th * a.BH + r / a.BW, ww = tw * a.BW + r % a.BW;
-            if (hh < a.H && ww < a.W) {
+            const int hh = th * a.BH + warp, ww = tw * a.BW + lane;
+            if (lane < kOutW && hh < a.H && ww < a.W) {
                 const long long vox = (((long long)vol * a.D + z) * a.H + hh) * a.W + ww;
                 __nv_bfloat16* dst = a.out + vox * kC;
                 if (a.mode == 0) {  // forward: bias + ReLU
@@ -313,7 +329,7 @@ k_conv3d_c32_tc(const __grid_constant__ CUtensorMap act_map, const __grid_consta
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp == 5) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
     }
 }
 
@@ -352,7 +368,7 @@ bool launch_conv3d_c32_tc(const __nv_bfloat16* act, const __nv_bfloat16* w, cons
     a.D = D;
     a.H = H;
     a.W = W;
-    a.BW = kBW;
+    a.BW = kOutW;
     a.BH = kBH;
     a.tiles_w = (W + a.BW - 1) / a.BW;
     a.tiles_h = (H + a.BH - 1) / a.BH;
