@@ -154,6 +154,8 @@ struct ConvTcArgs {
     const float* bias;      // [32] (forward)
     const __nv_bfloat16* mask_act;  // input-gradient mode: zero where this activation is <= 0
     __nv_bfloat16* out;     // [nvol][D][H][W][32]
+    const float* xres;      // mode 3: residual input x [nvol][D][H][W]
+    float* out1;            // mode 3: x + bias + output channel 0, FP32 [nvol][D][H][W]
     int* err;               // set to 1 on a wait timeout
 };
 
@@ -287,16 +289,25 @@ k_conv3d_c32_tc(const __grid_constant__ CUtensorMap act_map, const __grid_consta
             // at tile column i = x is G_-1[x] + G_0[x + 1] + G_+1[x + 2]
             float v[32], g[32];
             const uint32_t lanes = (uint32_t)(warp * 32) << 16;
+            const bool one = a.mode == 3;  // only output channel 0 is used
             tmem_ld_32cols(tmem + b * kAccCols + lanes, v);
             tmem_ld_32cols(tmem + b * kAccCols + 32 + lanes, g);
+            if (one) {
+                v[0] += __shfl_down_sync(0xffffffffu, g[0], 1);
+            } else {
 #pragma unroll
-            for (int c = 0; c < 32; ++c) v[c] += __shfl_down_sync(0xffffffffu, g[c], 1);
+                for (int c = 0; c < 32; ++c) v[c] += __shfl_down_sync(0xffffffffu, g[c], 1);
+            }
             tmem_ld_32cols(tmem + b * kAccCols + 64 + lanes, g);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(bar_acce + 8 * b);  // this warp's lanes of buffer b are free
+            if (one) {
+                v[0] += __shfl_down_sync(0xffffffffu, g[0], 2);
+            } else {
 #pragma unroll
-            for (int c = 0; c < 32; ++c) v[c] += __shfl_down_sync(0xffffffffu, g[c], 2);
+                for (int c = 0; c < 32; ++c) v[c] += __shfl_down_sync(0xffffffffu, g[c], 2);
+            }
             long long tr = blockIdx.x + j * gridDim.x;
             const int tw = (int)(tr % a.tiles_w); tr /= a.tiles_w;
             const int th = (int)(tr % a.tiles_h); tr /= a.tiles_h;
@@ -304,6 +315,10 @@ k_conv3d_c32_tc(const __grid_constant__ CUtensorMap act_map, const __grid_consta
             const int hh = th * a.BH + warp, ww = tw * a.BW + lane;
             if (lane < kOutW && hh < a.H && ww < a.W) {
                 const long long vox = (((long long)vol * a.D + z) * a.H + hh) * a.W + ww;
+                if (one) {  // 32 -> 1 output layer: theta = x + (bias + f)
+                    a.out1[vox] = a.xres[vox] + (v[0] + a.bias[0]);
+                    continue;
+                }
                 __nv_bfloat16* dst = a.out + vox * kC;
                 if (a.mode == 0) {  // forward: bias + ReLU
 #pragma unroll
@@ -355,29 +370,17 @@ EncodeFn encode_fn() {
 
 size_t conv3d_c32_tc_smem() { return kWBytes + kStages * kABytes + 1024 + 256; }  // 2 CTAs per SM
 
-// out[vol][z][h][w][:] = epilogue(sum_tap W[tap] * act[vol][z+dz][h+dy][w+dx][:]).
-// act, out: BF16 [nvol][D][H][W][32]; w: BF16 [27][32 out][32 in].
-// mode 0: + bias, ReLU; mode 1: x (mask_act > 0); mode 2: plain.
-bool launch_conv3d_c32_tc(const __nv_bfloat16* act, const __nv_bfloat16* w, const float* bias,
-                          const __nv_bfloat16* mask_act, int mode, int nvol, int D, int H, int W,
-                          __nv_bfloat16* out, int* err, cudaStream_t s) {
+namespace {
+
+bool launch_conv(const __nv_bfloat16* act, const __nv_bfloat16* w, ConvTcArgs a, cudaStream_t s) {
     EncodeFn enc = encode_fn();
     if (enc == nullptr) return false;
-    ConvTcArgs a{};
-    a.nvol = nvol;
-    a.D = D;
-    a.H = H;
-    a.W = W;
+    const int nvol = a.nvol, D = a.D, H = a.H, W = a.W;
     a.BW = kOutW;
     a.BH = kBH;
     a.tiles_w = (W + a.BW - 1) / a.BW;
     a.tiles_h = (H + a.BH - 1) / a.BH;
     a.ntiles = (long long)nvol * D * a.tiles_h * a.tiles_w;
-    a.mode = mode;
-    a.bias = bias;
-    a.mask_act = mask_act;
-    a.out = out;
-    a.err = err;
     if (((uintptr_t)act & 15) != 0 || ((uintptr_t)w & 15) != 0) return false;
 
     CUtensorMap amap, wmap;
@@ -414,6 +417,46 @@ bool launch_conv3d_c32_tc(const __nv_bfloat16* act, const __nv_bfloat16* w, cons
     const long long grid = std::min<long long>(a.ntiles, (long long)sms * 2);
     k_conv3d_c32_tc<<<(unsigned)grid, kThreads, smem, s>>>(amap, wmap, a);
     return true;
+}
+
+}  // namespace
+
+// out[vol][z][h][w][:] = epilogue(sum_tap W[tap] * act[vol][z+dz][h+dy][w+dx][:]).
+// act, out: BF16 [nvol][D][H][W][32]; w: BF16 [27][32 out][32 in].
+// mode 0: + bias, ReLU; mode 1: x (mask_act > 0); mode 2: plain.
+bool launch_conv3d_c32_tc(const __nv_bfloat16* act, const __nv_bfloat16* w, const float* bias,
+                          const __nv_bfloat16* mask_act, int mode, int nvol, int D, int H, int W,
+                          __nv_bfloat16* out, int* err, cudaStream_t s) {
+    ConvTcArgs a{};
+    a.nvol = nvol;
+    a.D = D;
+    a.H = H;
+    a.W = W;
+    a.mode = mode;
+    a.bias = bias;
+    a.mask_act = mask_act;
+    a.out = out;
+    a.err = err;
+    return launch_conv(act, w, a, s);
+}
+
+// The 32 -> 1 output layer with the residual: theta = x + bias[0] + sum_tap
+// W[tap][0] . act[voxel + tap], on the same tensor-core kernel with the
+// weights zero-padded to 32 output channels (w: BF16 [27][32][32], only
+// output channel 0 nonzero); x, theta: FP32 [nvol][D][H][W].
+bool launch_conv3d_c32_to1_tc(const __nv_bfloat16* act, const __nv_bfloat16* w, const float* bias, const float* x,
+                              float* theta, int nvol, int D, int H, int W, int* err, cudaStream_t s) {
+    ConvTcArgs a{};
+    a.nvol = nvol;
+    a.D = D;
+    a.H = H;
+    a.W = W;
+    a.mode = 3;
+    a.bias = bias;
+    a.xres = x;
+    a.out1 = theta;
+    a.err = err;
+    return launch_conv(act, w, a, s);
 }
 
 }  // namespace sci
