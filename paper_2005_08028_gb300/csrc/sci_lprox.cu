@@ -199,13 +199,27 @@ __global__ void k_dgrad_out(const float* __restrict__ g4, const float* __restric
     store32(g3 + u * C, acc);
 }
 
-// Weight and bias gradients of a 32 -> 32 layer:
-//   dw[tap][o][i] += sum_v gout[v][o] * ain[v + offset(tap)][i],  db[o] += sum_v gout[v][o]
-// Thread (o, i-quad) keeps 27 x 4 accumulators; a persistent grid walks the
-// voxels and each CTA adds its totals once (FP32 atomics).
-__global__ void __launch_bounds__(256) k_wgrad_c32(const __nv_bfloat16* __restrict__ gout,
-                                                   const __nv_bfloat16* __restrict__ ain, Vol g,
-                                                   float* __restrict__ dw, float* __restrict__ db) {
+// Weight and bias gradients of a 32 -> 32 layer, tiled:
+//   dw[tap][o][i] = sum_v gout[v][o] * ain[v + offset(tap)][i],  db[o] = sum_v gout[v][o].
+// A tile is kWgTile voxels of one row.  The CTA stages, as FP32, the nine
+// (dz, dy) neighbour rows of ain over columns x0 - 1 .. x0 + kWgTile (zero
+// outside the volume) and gout over the tile with a zero border.  Thread
+// (o, i-quad) walks the ain columns c with the gout values of columns c - 1,
+// c, c + 1 in registers: one 16-byte shared load of ain[row][c][i..i+3] feeds
+// the three column taps (output voxel c - dx for tap dx), 12 FMAs.  Each CTA
+// writes its 27 x 32 x 32 + 32 totals to its own slot of `part`;
+// k_wgrad_reduce sums the slots in a fixed order (no atomics, so the
+// gradient is the same on every run).
+constexpr int kWgTile = 64, kWgCols = kWgTile + 2, kWgMaxBlocks = 256, kWgSlot = 27 * C * C + C;
+
+size_t wgrad_smem() { return (size_t)(9 * kWgCols + kWgCols + 2) * C * sizeof(float); }
+
+__global__ void __launch_bounds__(256, 1) k_wgrad_c32_tiled(const __nv_bfloat16* __restrict__ gout,
+                                                            const __nv_bfloat16* __restrict__ ain, Vol g,
+                                                            int tiles_x, float* __restrict__ part) {
+    extern __shared__ float4 wg_smem4[];
+    float* sA = reinterpret_cast<float*>(wg_smem4);  // [9][kWgCols][32]: ain rows (dz, dy), columns x0-1 ..
+    float* sG = sA + 9 * kWgCols * C;                // [kWgCols + 2][32]: gout at columns x0-2 .. x0+kWgTile+1
     const int o = threadIdx.x >> 3, iq = (threadIdx.x & 7) * 4;
     float acc[27][4];
 #pragma unroll
@@ -213,30 +227,100 @@ __global__ void __launch_bounds__(256) k_wgrad_c32(const __nv_bfloat16* __restri
 #pragma unroll
         for (int k = 0; k < 4; ++k) acc[t][k] = 0.f;
     float bacc = 0.f;
-    for (long long v = blockIdx.x; v < g.V; v += gridDim.x) {
-        int n, z, y, xx;
-        decomp(g, v, n, z, y, xx);
-        const float go = __bfloat162float(gout[v * C + o]);
-        bacc += go;
-        if (go == 0.f) continue;
+    const long long ntiles = (long long)g.nvol * g.D * g.H * tiles_x;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int tx = (int)(tile % tiles_x);
+        long long r = tile / tiles_x;
+        const int y = (int)(r % g.H);
+        r /= g.H;
+        const int z = (int)(r % g.D), n = (int)(r / g.D);
+        const int x0 = tx * kWgTile;
+        __syncthreads();  // the previous tile's reads are done
+        for (int e = threadIdx.x; e < 9 * kWgCols * 4; e += blockDim.x) {
+            const int q = e & 3, col = (e >> 2) % kWgCols, row = (e >> 2) / kWgCols;
+            const int zz = z + row / 3 - 1, yy = y + row % 3 - 1, xx = x0 - 1 + col;
+            float f[8];
 #pragma unroll
-        for (int t = 0; t < 27; ++t) {
-            const long long u = nb(g, n, z, y, xx, t);
-            if (u < 0) continue;
-            const uint2 raw = *reinterpret_cast<const uint2*>(ain + u * C + iq);
-            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&raw);
-            const float2 f0 = __bfloat1622float2(h[0]), f1 = __bfloat1622float2(h[1]);
-            acc[t][0] = fmaf(go, f0.x, acc[t][0]);
-            acc[t][1] = fmaf(go, f0.y, acc[t][1]);
-            acc[t][2] = fmaf(go, f1.x, acc[t][2]);
-            acc[t][3] = fmaf(go, f1.y, acc[t][3]);
+            for (int k = 0; k < 8; ++k) f[k] = 0.f;
+            if (zz >= 0 && zz < g.D && yy >= 0 && yy < g.H && xx >= 0 && xx < g.W) {
+                const long long u = (((long long)n * g.D + zz) * g.H + yy) * g.W + xx;
+                const uint4 raw = __ldg(reinterpret_cast<const uint4*>(ain + u * C + q * 8));
+                const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float2 v2 = __bfloat1622float2(h[k]);
+                    f[2 * k] = v2.x;
+                    f[2 * k + 1] = v2.y;
+                }
+            }
+            float4* d = reinterpret_cast<float4*>(sA + (row * kWgCols + col) * C + q * 8);
+            d[0] = make_float4(f[0], f[1], f[2], f[3]);
+            d[1] = make_float4(f[4], f[5], f[6], f[7]);
+        }
+        for (int e = threadIdx.x; e < (kWgCols + 2) * 4; e += blockDim.x) {
+            const int q = e & 3, col = e >> 2;  // column x0 - 2 + col
+            const int xx = x0 - 2 + col;
+            float f[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) f[k] = 0.f;
+            if (xx >= x0 && xx < x0 + kWgTile && xx < g.W) {
+                const long long v = (((long long)n * g.D + z) * g.H + y) * g.W + xx;
+                const uint4 raw = __ldg(reinterpret_cast<const uint4*>(gout + v * C + q * 8));
+                const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float2 v2 = __bfloat1622float2(h[k]);
+                    f[2 * k] = v2.x;
+                    f[2 * k + 1] = v2.y;
+                }
+            }
+            float4* d = reinterpret_cast<float4*>(sG + col * C + q * 8);
+            d[0] = make_float4(f[0], f[1], f[2], f[3]);
+            d[1] = make_float4(f[4], f[5], f[6], f[7]);
+        }
+        __syncthreads();
+        // ain column c is x0 - 1 + c; gout column c is sG[c + 1] (x0 - 1 + c)
+        float gm = sG[0 * C + o], g0 = sG[1 * C + o];  // columns c - 1, c for c = 0
+        for (int c = 0; c < kWgCols; ++c) {
+            const float gp = sG[(c + 2) * C + o];  // column c + 1
+            if (iq == 0) bacc += g0;
+#pragma unroll
+            for (int row = 0; row < 9; ++row) {
+                const float4 a = *reinterpret_cast<const float4*>(sA + (row * kWgCols + c) * C + iq);
+                // tap (row, dx): output voxel c - dx, i.e. gout column c - dx
+                acc[row * 3 + 0][0] = fmaf(gp, a.x, acc[row * 3 + 0][0]);  // dx = -1
+                acc[row * 3 + 0][1] = fmaf(gp, a.y, acc[row * 3 + 0][1]);
+                acc[row * 3 + 0][2] = fmaf(gp, a.z, acc[row * 3 + 0][2]);
+                acc[row * 3 + 0][3] = fmaf(gp, a.w, acc[row * 3 + 0][3]);
+                acc[row * 3 + 1][0] = fmaf(g0, a.x, acc[row * 3 + 1][0]);  // dx = 0
+                acc[row * 3 + 1][1] = fmaf(g0, a.y, acc[row * 3 + 1][1]);
+                acc[row * 3 + 1][2] = fmaf(g0, a.z, acc[row * 3 + 1][2]);
+                acc[row * 3 + 1][3] = fmaf(g0, a.w, acc[row * 3 + 1][3]);
+                acc[row * 3 + 2][0] = fmaf(gm, a.x, acc[row * 3 + 2][0]);  // dx = +1
+                acc[row * 3 + 2][1] = fmaf(gm, a.y, acc[row * 3 + 2][1]);
+                acc[row * 3 + 2][2] = fmaf(gm, a.z, acc[row * 3 + 2][2]);
+                acc[row * 3 + 2][3] = fmaf(gm, a.w, acc[row * 3 + 2][3]);
+            }
+            gm = g0;
+            g0 = gp;
         }
     }
+    float* dst = part + (size_t)blockIdx.x * kWgSlot;
 #pragma unroll
     for (int t = 0; t < 27; ++t)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) atomicAdd(dw + (t * C + o) * C + iq + k, acc[t][k]);
-    if ((threadIdx.x & 7) == 0) atomicAdd(db + o, bacc);
+        *reinterpret_cast<float4*>(dst + (t * C + o) * C + iq) = make_float4(acc[t][0], acc[t][1], acc[t][2], acc[t][3]);
+    if (iq == 0) dst[27 * C * C + o] = bacc;
+}
+
+// dw[j] += sum over CTA slots b of part[b][j] (and db), in slot order.
+__global__ void k_wgrad_reduce(const float* __restrict__ part, int nslots, float* __restrict__ dw,
+                               float* __restrict__ db) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= kWgSlot) return;
+    float s = 0.f;
+    for (int b = 0; b < nslots; ++b) s += part[(size_t)b * kWgSlot + j];
+    if (j < 27 * C * C) dw[j] += s;
+    else db[j - 27 * C * C] += s;
 }
 
 // Weight and bias gradients of layer 1 (input x, one channel) and layer 4
@@ -290,7 +374,7 @@ __global__ void k_adam(float* __restrict__ prm, const float* __restrict__ grad, 
 
 struct LWork {
     __nv_bfloat16 *a1, *a2, *a3, *ga, *gb, *w2, *w2t, *w3, *w3t, *w4p;
-    float *g4, *grad;
+    float *g4, *grad, *wpart;
     double* partials;
     int* err;
     size_t total;
@@ -316,12 +400,34 @@ LWork lwork_layout(long long V, bool training, void* base) {
         L.w3t = reinterpret_cast<__nv_bfloat16*>(take(27 * C * C * 2));
         L.g4 = reinterpret_cast<float*>(take((size_t)V * 4));
         L.grad = reinterpret_cast<float*>(take(kParams * 4));
+        L.wpart = reinterpret_cast<float*>(take((size_t)kWgMaxBlocks * kWgSlot * 4));
     }
     L.total = off;
     return L;
 }
 
 int grid_for(long long V) { return (int)((V + 255) / 256); }
+
+// Weight and bias gradients of a 32 -> 32 layer into dw / db (added).
+bool enqueue_wgrad_c32(const __nv_bfloat16* gout, const __nv_bfloat16* ain, Vol g, float* part, float* dw,
+                       float* db, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_wgrad_c32_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)wgrad_smem()) != cudaSuccess)
+            return false;
+        attr = true;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int tiles_x = (g.W + kWgTile - 1) / kWgTile;
+    const long long ntiles = (long long)g.nvol * g.D * g.H * tiles_x;
+    const int grid = (int)std::max(1LL, std::min<long long>({ntiles, (long long)sms, (long long)kWgMaxBlocks}));
+    k_wgrad_c32_tiled<<<grid, 256, wgrad_smem(), s>>>(gout, ain, g, tiles_x, part);
+    k_wgrad_reduce<<<(kWgSlot + 255) / 256, 256, 0, s>>>(part, grid, dw, db);
+    return true;
+}
 
 // GAP projection for `count` volumes stored back to back:
 // xt = theta + c_k R^+ (y - sum_k c_k theta_k); also x_out = xt when given.
@@ -424,11 +530,11 @@ sci_status sci_lprox_train_step(float* params, float* adam_m, float* adam_v, int
     k_wgrad_out<<<wg, 27 * C + C, 0, s>>>(L.g4, L.a3, g, L.grad + kW4, L.grad + kB4);
     k_dgrad_out<<<grid_for(g.V), 256, 0, s>>>(L.g4, params, g, L.a3, L.ga);  // ga = g3
     // layer 3
-    k_wgrad_c32<<<wg, 256, 0, s>>>(L.ga, L.a2, g, L.grad + kW3, L.grad + kB3);
+    if (!enqueue_wgrad_c32(L.ga, L.a2, g, L.wpart, L.grad + kW3, L.grad + kB3, s)) return SCI_ERR_CUDA;
     if (!launch_conv3d_c32_tc(L.ga, L.w3t, nullptr, L.a2, 1, g.nvol, g.D, g.H, g.W, L.gb, L.err, s))
         return SCI_ERR_CUDA;  // gb = g2
     // layer 2
-    k_wgrad_c32<<<wg, 256, 0, s>>>(L.gb, L.a1, g, L.grad + kW2, L.grad + kB2);
+    if (!enqueue_wgrad_c32(L.gb, L.a1, g, L.wpart, L.grad + kW2, L.grad + kB2, s)) return SCI_ERR_CUDA;
     if (!launch_conv3d_c32_tc(L.gb, L.w2t, nullptr, L.a1, 1, g.nvol, g.D, g.H, g.W, L.ga, L.err, s))
         return SCI_ERR_CUDA;  // ga = g1
     // layer 1
@@ -462,10 +568,10 @@ sci_status sci_lprox_grads(const float* params, const float* x, const float* tar
     const int wg = sms * 4;
     k_wgrad_out<<<wg, 27 * C + C, 0, s>>>(L.g4, L.a3, g, grad + kW4, grad + kB4);
     k_dgrad_out<<<grid_for(g.V), 256, 0, s>>>(L.g4, params, g, L.a3, L.ga);
-    k_wgrad_c32<<<wg, 256, 0, s>>>(L.ga, L.a2, g, grad + kW3, grad + kB3);
+    if (!enqueue_wgrad_c32(L.ga, L.a2, g, L.wpart, grad + kW3, grad + kB3, s)) return SCI_ERR_CUDA;
     if (!launch_conv3d_c32_tc(L.ga, L.w3t, nullptr, L.a2, 1, g.nvol, g.D, g.H, g.W, L.gb, L.err, s))
         return SCI_ERR_CUDA;
-    k_wgrad_c32<<<wg, 256, 0, s>>>(L.gb, L.a1, g, grad + kW2, grad + kB2);
+    if (!enqueue_wgrad_c32(L.gb, L.a1, g, L.wpart, grad + kW2, grad + kB2, s)) return SCI_ERR_CUDA;
     if (!launch_conv3d_c32_tc(L.gb, L.w2t, nullptr, L.a1, 1, g.nvol, g.D, g.H, g.W, L.ga, L.err, s))
         return SCI_ERR_CUDA;
     k_wgrad_in<<<wg, 28 * C, 0, s>>>(L.ga, x, g, grad + kW1, grad + kB1);
