@@ -312,51 +312,151 @@ __global__ void __launch_bounds__(256, 1) k_wgrad_c32_tiled(const __nv_bfloat16*
     if (iq == 0) dst[27 * C * C + o] = bacc;
 }
 
-// dw[j] += sum over CTA slots b of part[b][j] (and db), in slot order.
-__global__ void k_wgrad_reduce(const float* __restrict__ part, int nslots, float* __restrict__ dw,
-                               float* __restrict__ db) {
+// Slots of `len` values (the first nw weight gradients, then bias gradients):
+// dw[j] += sum over CTA slots b of part[b][j] (db likewise), in slot order.
+__global__ void k_wgrad_reduce(const float* __restrict__ part, int nslots, int len, int nw,
+                               float* __restrict__ dw, float* __restrict__ db) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= kWgSlot) return;
+    if (j >= len) return;
     float s = 0.f;
-    for (int b = 0; b < nslots; ++b) s += part[(size_t)b * kWgSlot + j];
-    if (j < 27 * C * C) dw[j] += s;
-    else db[j - 27 * C * C] += s;
+    for (int b = 0; b < nslots; ++b) s += part[(size_t)b * len + j];
+    if (j < nw) dw[j] += s;
+    else db[j - nw] += s;
 }
 
-// Weight and bias gradients of layer 1 (input x, one channel) and layer 4
-// (output one channel): thread t < 27*32 owns one weight.
-__global__ void k_wgrad_in(const __nv_bfloat16* __restrict__ g1, const float* __restrict__ x, Vol g,
-                           float* __restrict__ dw1, float* __restrict__ db1) {
-    const int idx = threadIdx.x;  // blockDim 32 * 28: rows 0..26 taps, row 27 bias
-    const int t = idx / C, o = idx % C;
-    float acc = 0.f;
-    for (long long v = blockIdx.x; v < g.V; v += gridDim.x) {
-        const float go = __bfloat162float(g1[v * C + o]);
-        if (t == 27) { acc += go; continue; }
-        int n, z, y, xx;
-        decomp(g, v, n, z, y, xx);
-        const long long u = nb(g, n, z, y, xx, t);
-        if (u >= 0) acc = fmaf(go, __bfloat162float(__float2bfloat16_rn(x[u])), acc);
-    }
-    if (t < 27) atomicAdd(dw1 + t * C + o, acc);
-    else atomicAdd(db1 + o, acc);
+// Tile staging shared by the one-channel layers' gradients: tile (n, z, y, x0)
+// of kWgTile voxels of one row.
+__device__ __forceinline__ void wg_tile(const Vol& g, int tiles_x, long long tile, int& n, int& z, int& y, int& x0) {
+    x0 = (int)(tile % tiles_x) * kWgTile;
+    long long r = tile / tiles_x;
+    y = (int)(r % g.H);
+    r /= g.H;
+    z = (int)(r % g.D);
+    n = (int)(r / g.D);
 }
 
-__global__ void k_wgrad_out(const float* __restrict__ g4, const __nv_bfloat16* __restrict__ act3, Vol g,
-                            float* __restrict__ dw4, float* __restrict__ db4) {
-    const int idx = threadIdx.x;  // rows 0..26 taps x 32 channels, then one bias thread
-    const int t = idx / C, i = idx % C;
-    float acc = 0.f;
-    for (long long v = blockIdx.x; v < g.V; v += gridDim.x) {
-        const float go = g4[v];
-        if (t == 27) { if (i == 0) acc += go; continue; }
-        int n, z, y, xx;
-        decomp(g, v, n, z, y, xx);
-        const long long u = nb(g, n, z, y, xx, t);
-        if (u >= 0) acc = fmaf(go, __bfloat162float(act3[u * C + i]), acc);
+// Layer 1 (input x, one channel): dw1[tap][o] = sum_v g1[v][o] x[v + offset(tap)],
+// db1[o] = sum_v g1[v][o].  x enters as BF16-rounded (the forward's operand).
+// Thread (row, o), 9 x 32 threads; sliding window of g1 over the x columns.
+__global__ void __launch_bounds__(288) k_wgrad_in_tiled(const __nv_bfloat16* __restrict__ g1,
+                                                        const float* __restrict__ x, Vol g, int tiles_x,
+                                                        float* __restrict__ part) {
+    __shared__ float sx[9][kWgCols];          // x rows (dz, dy), columns x0 - 1 ..
+    __shared__ float sG[kWgCols + 2][C];      // g1 at columns x0 - 2 .., zero outside the tile
+    const int row = threadIdx.x / C, o = threadIdx.x % C;
+    float acc[3] = {0.f, 0.f, 0.f}, bacc = 0.f;
+    const long long ntiles = (long long)g.nvol * g.D * g.H * tiles_x;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        int n, z, y, x0;
+        wg_tile(g, tiles_x, tile, n, z, y, x0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < 9 * kWgCols; e += blockDim.x) {
+            const int r = e / kWgCols, col = e % kWgCols;
+            const int zz = z + r / 3 - 1, yy = y + r % 3 - 1, xx = x0 - 1 + col;
+            float v = 0.f;
+            if (zz >= 0 && zz < g.D && yy >= 0 && yy < g.H && xx >= 0 && xx < g.W)
+                v = __bfloat162float(__float2bfloat16_rn(x[(((long long)n * g.D + zz) * g.H + yy) * g.W + xx]));
+            sx[r][col] = v;
+        }
+        for (int e = threadIdx.x; e < (kWgCols + 2) * C; e += blockDim.x) {
+            const int col = e / C, c = e % C, xx = x0 - 2 + col;
+            float v = 0.f;
+            if (xx >= x0 && xx < x0 + kWgTile && xx < g.W)
+                v = __bfloat162float(g1[((((long long)n * g.D + z) * g.H + y) * g.W + xx) * C + c]);
+            sG[col][c] = v;
+        }
+        __syncthreads();
+        float gm = sG[0][o], g0 = sG[1][o];
+        for (int c = 0; c < kWgCols; ++c) {
+            const float gp = sG[c + 2][o], xv = sx[row][c];
+            if (row == 0) bacc += g0;
+            acc[0] = fmaf(gp, xv, acc[0]);  // dx = -1
+            acc[1] = fmaf(g0, xv, acc[1]);  // dx = 0
+            acc[2] = fmaf(gm, xv, acc[2]);  // dx = +1
+            gm = g0;
+            g0 = gp;
+        }
     }
-    if (t < 27) atomicAdd(dw4 + t * C + i, acc);
-    else if (i == 0) atomicAdd(db4, acc);
+    float* dst = part + (size_t)blockIdx.x * (27 * C + C);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dst[(row * 3 + d) * C + o] = acc[d];
+    if (row == 0) dst[27 * C + o] = bacc;
+}
+
+// Layer 4 (one output channel): dw4[tap][i] = sum_v g4[v] a3[v + offset(tap)][i],
+// db4 = sum_v g4[v].  Thread (part, row, i-quad): three column ranges of the
+// tile in parallel, combined in shared memory in a fixed order at the end.
+__global__ void __launch_bounds__(256) k_wgrad_out_tiled(const float* __restrict__ g4,
+                                                         const __nv_bfloat16* __restrict__ a3, Vol g, int tiles_x,
+                                                         float* __restrict__ part) {
+    extern __shared__ float4 wo_smem4[];
+    float* sA = reinterpret_cast<float*>(wo_smem4);  // [9][kWgCols][32]
+    float* sg = sA + 9 * kWgCols * C;               // [kWgCols + 2]: g4 at columns x0 - 2 ..
+    float* red = sg + kWgCols + 2;                  // [3][27 * 32 + 1]
+    const int tid = threadIdx.x, cp = tid / 72, row = (tid % 72) / 8, iq = (tid % 8) * 4;
+    const bool active = tid < 216;
+    constexpr int kSpan = (kWgCols + 2) / 3;  // 22 columns per part
+    float acc[3][4] = {}, bacc = 0.f;
+    const long long ntiles = (long long)g.nvol * g.D * g.H * tiles_x;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        int n, z, y, x0;
+        wg_tile(g, tiles_x, tile, n, z, y, x0);
+        __syncthreads();
+        for (int e = tid; e < 9 * kWgCols * 4; e += blockDim.x) {
+            const int q = e & 3, col = (e >> 2) % kWgCols, r = (e >> 2) / kWgCols;
+            const int zz = z + r / 3 - 1, yy = y + r % 3 - 1, xx = x0 - 1 + col;
+            float f[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) f[k] = 0.f;
+            if (zz >= 0 && zz < g.D && yy >= 0 && yy < g.H && xx >= 0 && xx < g.W) {
+                const long long u = (((long long)n * g.D + zz) * g.H + yy) * g.W + xx;
+                const uint4 raw = __ldg(reinterpret_cast<const uint4*>(a3 + u * C + q * 8));
+                const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float2 v2 = __bfloat1622float2(h[k]);
+                    f[2 * k] = v2.x;
+                    f[2 * k + 1] = v2.y;
+                }
+            }
+            float4* d = reinterpret_cast<float4*>(sA + (r * kWgCols + col) * C + q * 8);
+            d[0] = make_float4(f[0], f[1], f[2], f[3]);
+            d[1] = make_float4(f[4], f[5], f[6], f[7]);
+        }
+        for (int col = tid; col < kWgCols + 2; col += blockDim.x) {
+            const int xx = x0 - 2 + col;
+            sg[col] = (xx >= x0 && xx < x0 + kWgTile && xx < g.W)
+                          ? g4[(((long long)n * g.D + z) * g.H + y) * g.W + xx] : 0.f;
+        }
+        __syncthreads();
+        if (active) {
+            const int c0 = cp * kSpan, c1 = min(c0 + kSpan, kWgCols);
+            for (int c = c0; c < c1; ++c) {
+                const float gp = sg[c + 2], g0 = sg[c + 1], gm = sg[c];
+                if (row == 0 && iq == 0) bacc += g0;
+                const float4 a = *reinterpret_cast<const float4*>(sA + (row * kWgCols + c) * C + iq);
+                const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    acc[0][k] = fmaf(gp, av[k], acc[0][k]);  // dx = -1
+                    acc[1][k] = fmaf(g0, av[k], acc[1][k]);  // dx = 0
+                    acc[2][k] = fmaf(gm, av[k], acc[2][k]);  // dx = +1
+                }
+            }
+        }
+    }
+    __syncthreads();
+    constexpr int kLen = 27 * C + 1;
+    if (active) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) red[cp * kLen + (row * 3 + d) * C + iq + k] = acc[d][k];
+        if (row == 0 && iq == 0) red[cp * kLen + 27 * C] = bacc;
+    }
+    __syncthreads();
+    float* dst = part + (size_t)blockIdx.x * kLen;
+    for (int j = tid; j < kLen; j += blockDim.x) dst[j] = (red[j] + red[kLen + j]) + red[2 * kLen + j];
 }
 
 // Adam on the FP32 master parameters (bias-corrected step size).
@@ -425,7 +525,36 @@ bool enqueue_wgrad_c32(const __nv_bfloat16* gout, const __nv_bfloat16* ain, Vol 
     const long long ntiles = (long long)g.nvol * g.D * g.H * tiles_x;
     const int grid = (int)std::max(1LL, std::min<long long>({ntiles, (long long)sms, (long long)kWgMaxBlocks}));
     k_wgrad_c32_tiled<<<grid, 256, wgrad_smem(), s>>>(gout, ain, g, tiles_x, part);
-    k_wgrad_reduce<<<(kWgSlot + 255) / 256, 256, 0, s>>>(part, grid, dw, db);
+    k_wgrad_reduce<<<(kWgSlot + 255) / 256, 256, 0, s>>>(part, grid, kWgSlot, 27 * C * C, dw, db);
+    return true;
+}
+
+size_t wgrad_out_smem() { return (size_t)(9 * kWgCols * C + kWgCols + 2 + 3 * (27 * C + 1)) * sizeof(float); }
+
+// Weight and bias gradients of layer 1 (from g1 and x) and layer 4 (from g4
+// and a3) into dw / db (added).
+bool enqueue_wgrad_1ch(bool layer1, const __nv_bfloat16* gact, const float* gx, const float* x,
+                       const __nv_bfloat16* a3, Vol g, float* part, float* dw, float* db, cudaStream_t s) {
+    static bool attr = false;
+    if (!layer1 && !attr) {
+        if (cudaFuncSetAttribute(k_wgrad_out_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)wgrad_out_smem()) != cudaSuccess)
+            return false;
+        attr = true;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int tiles_x = (g.W + kWgTile - 1) / kWgTile;
+    const long long ntiles = (long long)g.nvol * g.D * g.H * tiles_x;
+    const int grid = (int)std::max(1LL, std::min<long long>({ntiles, 2LL * sms, (long long)kWgMaxBlocks}));
+    if (layer1) {
+        k_wgrad_in_tiled<<<grid, 9 * C, 0, s>>>(gact, x, g, tiles_x, part);
+        k_wgrad_reduce<<<(27 * C + C + 255) / 256, 256, 0, s>>>(part, grid, 27 * C + C, 27 * C, dw, db);
+    } else {
+        k_wgrad_out_tiled<<<grid, 256, wgrad_out_smem(), s>>>(gx, a3, g, tiles_x, part);
+        k_wgrad_reduce<<<(27 * C + 1 + 255) / 256, 256, 0, s>>>(part, grid, 27 * C + 1, 27 * C, dw, db);
+    }
     return true;
 }
 
@@ -522,12 +651,9 @@ sci_status sci_lprox_train_step(float* params, float* adam_m, float* adam_v, int
     if (!enqueue_forward(params, x, g, L, nullptr, target, s)) return SCI_ERR_CUDA;
     if (loss != nullptr) launch_sum_partials(L.partials, grid_for(g.V), loss, s);
     cudaMemsetAsync(L.grad, 0, kParams * 4, s);
-    int sms = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int wg = sms * 4;
     // layer 4
-    k_wgrad_out<<<wg, 27 * C + C, 0, s>>>(L.g4, L.a3, g, L.grad + kW4, L.grad + kB4);
+    if (!enqueue_wgrad_1ch(false, nullptr, L.g4, nullptr, L.a3, g, L.wpart, L.grad + kW4, L.grad + kB4, s))
+        return SCI_ERR_CUDA;
     k_dgrad_out<<<grid_for(g.V), 256, 0, s>>>(L.g4, params, g, L.a3, L.ga);  // ga = g3
     // layer 3
     if (!enqueue_wgrad_c32(L.ga, L.a2, g, L.wpart, L.grad + kW3, L.grad + kB3, s)) return SCI_ERR_CUDA;
@@ -538,7 +664,8 @@ sci_status sci_lprox_train_step(float* params, float* adam_m, float* adam_v, int
     if (!launch_conv3d_c32_tc(L.gb, L.w2t, nullptr, L.a1, 1, g.nvol, g.D, g.H, g.W, L.ga, L.err, s))
         return SCI_ERR_CUDA;  // ga = g1
     // layer 1
-    k_wgrad_in<<<wg, 28 * C, 0, s>>>(L.ga, x, g, L.grad + kW1, L.grad + kB1);
+    if (!enqueue_wgrad_1ch(true, L.ga, nullptr, x, nullptr, g, L.wpart, L.grad + kW1, L.grad + kB1, s))
+        return SCI_ERR_CUDA;
     // Adam (beta1 0.9, beta2 0.999, eps 1e-8), bias-corrected step size
     const double b1 = 0.9, b2 = 0.999;
     const double lr_t = (double)lr * std::sqrt(1.0 - std::pow(b2, step)) / (1.0 - std::pow(b1, step));
@@ -562,11 +689,8 @@ sci_status sci_lprox_grads(const float* params, const float* x, const float* tar
     if (!enqueue_forward(params, x, g, L, nullptr, target, s)) return SCI_ERR_CUDA;
     if (loss != nullptr) launch_sum_partials(L.partials, grid_for(g.V), loss, s);
     cudaMemsetAsync(grad, 0, kParams * 4, s);
-    int sms = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int wg = sms * 4;
-    k_wgrad_out<<<wg, 27 * C + C, 0, s>>>(L.g4, L.a3, g, grad + kW4, grad + kB4);
+    if (!enqueue_wgrad_1ch(false, nullptr, L.g4, nullptr, L.a3, g, L.wpart, grad + kW4, grad + kB4, s))
+        return SCI_ERR_CUDA;
     k_dgrad_out<<<grid_for(g.V), 256, 0, s>>>(L.g4, params, g, L.a3, L.ga);
     if (!enqueue_wgrad_c32(L.ga, L.a2, g, L.wpart, grad + kW3, grad + kB3, s)) return SCI_ERR_CUDA;
     if (!launch_conv3d_c32_tc(L.ga, L.w3t, nullptr, L.a2, 1, g.nvol, g.D, g.H, g.W, L.gb, L.err, s))
@@ -574,7 +698,8 @@ sci_status sci_lprox_grads(const float* params, const float* x, const float* tar
     if (!enqueue_wgrad_c32(L.gb, L.a1, g, L.wpart, grad + kW2, grad + kB2, s)) return SCI_ERR_CUDA;
     if (!launch_conv3d_c32_tc(L.gb, L.w2t, nullptr, L.a1, 1, g.nvol, g.D, g.H, g.W, L.ga, L.err, s))
         return SCI_ERR_CUDA;
-    k_wgrad_in<<<wg, 28 * C, 0, s>>>(L.ga, x, g, grad + kW1, grad + kB1);
+    if (!enqueue_wgrad_1ch(true, L.ga, nullptr, x, nullptr, g, L.wpart, grad + kW1, grad + kB1, s))
+        return SCI_ERR_CUDA;
     return check_launch();
 }
 
