@@ -411,11 +411,10 @@ def _batched(pkg, torch, dev, stream, flush):
 def _learned(pkg, torch, dev, stream, flush):
     """Learned prox replacing S = 10 VTV-FGP updates inside GAP-TV.
 
-    Training: 4096 (x, FGP_10(x)) pairs of 64x64x8 patches cut from plain
-    GAP-TV runs on seeded 256x256x8 measurements stopped at random outer
-    iterations in [1, 50]; Adam, 8 epochs of batch 32 (the config's 20k pairs
-    are cut to 4k to keep the benchmark short; the training set size is
-    reported).  Test: 64 measurements of 512x512x10 (Bernoulli(0.5) masks,
+    Training: 20480 (x, FGP_10(x)) pairs of 64x64x8 patches (the config's
+    20k) cut from plain GAP-TV runs on seeded 256x256x8 measurements stopped
+    at random outer iterations in [1, 50], plus 512 held out; Adam, 8 epochs
+    of batch 32.  Test: 64 measurements of 512x512x10 (Bernoulli(0.5) masks,
     sigma = 0.01), T = 50 outer iterations with the learned prox and a
     residual check every 10 iterations against the plain method's residual
     curve (calibrated on 8 held-out measurements), falling back to plain FGP
@@ -426,12 +425,13 @@ def _learned(pkg, torch, dev, stream, flush):
     import sci_synth as ss
     lam, S, T, every = 0.05, 10, 50, 10
     t0 = time.perf_counter()
-    X, Y = LT.make_pairs(4096, seed=50, size=(256, 256, 8))
+    n_train, n_held = 20480, 512
+    X, Y = LT.make_pairs(n_train + n_held, seed=50, size=(256, 256, 8))
     net = pkg.LearnedProx(params=LT.init_params(seed=1))
-    hist = LT.train(net, X[:3840], Y[:3840], epochs=8, batch=32, lr=1e-3)
-    pred = net.apply(X[3840:])
-    mse_net = float(((pred - Y[3840:]) ** 2).mean())
-    mse_id = float(((X[3840:] - Y[3840:]) ** 2).mean())
+    hist = LT.train(net, X[:n_train], Y[:n_train], epochs=8, batch=32, lr=1e-3)
+    pred = net.apply(X[n_train:])
+    mse_net = float(((pred - Y[n_train:]) ** 2).mean())
+    mse_id = float(((X[n_train:] - Y[n_train:]) ** 2).mean())
     torch.cuda.synchronize(dev)
     train_s = time.perf_counter() - t0
     del X, Y, pred
@@ -506,7 +506,7 @@ def _learned(pkg, torch, dev, stream, flush):
     del act, out
     return {"workload": "learned_prox_64x512x512x10: VTV, lambda=0.05, T=50, network replaces S=10 FGP "
                         "updates; residual check every 10 iterations, fallback ratio 1.05",
-            "train": {"pairs": 3840, "patch": "8x64x64", "epochs": 8, "batch": 32, "seconds": round(train_s, 1),
+            "train": {"pairs": n_train, "held_out": n_held, "patch": "8x64x64", "epochs": 8, "batch": 32, "seconds": round(train_s, 1),
                       "loss_per_epoch": [float(f"{h:.3e}") for h in hist],
                       "heldout_mse_vs_identity": round(mse_net / mse_id, 4)},
             "learned": {"value": N * T / (ms_l * 1e-3), "unit": UNIT, "ms": round(ms_l, 1),
