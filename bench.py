@@ -58,7 +58,7 @@ def _workload_desc(c):
 # ====================================================================== reference arm
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
+    _, rank, _ = dist_env()
     if rank != 0:
         return 0
     import oracle as O
@@ -151,13 +151,30 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def dist_env():
+    """(world size, rank, local rank) from the launcher's environment (1, 0, 0 alone)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def job_time_and_value(t_ms, units_per_rank, world, device=None):
+    """Whole-job timing over independent replicas: the slowest rank's time
+    (max over ranks, one all_reduce) and the units all ranks processed per
+    second of it.  Every rank must call this when world > 1."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    return t_ms, units_per_rank * world / (t_ms * 1e-3)
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = dist_env()
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
@@ -216,13 +233,8 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in evs]
-    t_ms = sum(step_ms)
-    if world > 1:
-        tt = torch.tensor([t_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
     units_per_rank = args.steps * len(COMBOS) * N * c["outer"]
-    value = units_per_rank * world / (t_ms * 1e-3)
+    t_ms, value = job_time_and_value(sum(step_ms), units_per_rank, world, dev)
 
     # ---- PSNR of the final reconstructions, against the oracle's (stored) values ----
     psnr = {}
@@ -245,7 +257,7 @@ def run_gpu(args):
     learned = None if args.no_learned else _learned(pkg, torch, dev, stream, flush)
 
     # ---- end to end: host buffers through the public API ----
-    e2e = _e2e(pkg, torch, dev, stream, args, c, masks_h, y, bufs, flush)
+    e2e = _e2e(pkg, torch, dev, stream, args, c, masks_h, y, bufs, flush, world)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -528,7 +540,7 @@ def _bf16_peak():
     return 1900.0
 
 
-def _e2e(pkg, torch, dev, stream, args, c, masks_h, y_dev, bufs, flush):
+def _e2e(pkg, torch, dev, stream, args, c, masks_h, y_dev, bufs, flush, world=1):
     """Same metric through the public API with host inputs/outputs: each step
     copies y and the dense masks from pinned host memory, packs the masks,
     runs the six reconstructions and copies every x^(T) back."""
@@ -560,7 +572,8 @@ def _e2e(pkg, torch, dev, stream, args, c, masks_h, y_dev, bufs, flush):
         torch.cuda.synchronize(dev)
         total += e0.elapsed_time(e1)
     units = args.steps * len(bufs) * N * c["outer"]
-    return {"value": units / (total * 1e-3), "unit": UNIT,
+    _, value = job_time_and_value(total, units, world, dev)
+    return {"value": value, "unit": UNIT,
             "h2d_bytes_per_step": int(y_h.numel() * 4 + m_h.numel()),
             "d2h_bytes_per_step": int(len(bufs) * N * 4)}
 
