@@ -103,32 +103,70 @@ __global__ void k_prep_weights(const float* __restrict__ prm, __nv_bfloat16* __r
     if (w3t) w3t[tidx] = __float2bfloat16_rn(prm[kW3 + idx]);
 }
 
-// layer 1 (1 -> 32) + ReLU: one thread per voxel.  Weights are rounded to
-// BF16 like the other layers' operands.
-__global__ void k_conv_in(const float* __restrict__ x, const float* __restrict__ prm, Vol g,
-                          __nv_bfloat16* __restrict__ act1) {
-    __shared__ float sw[27 * C + C];
+// layer 1 (1 -> 32) + ReLU.  A CTA computes an 8-row x 64-column tile of one
+// frame.  x, rounded to BF16 like the other layers' operands, is staged in
+// shared memory with a one-voxel halo in all three directions; zeros outside
+// the volume are the convolution's zero padding, so no tap needs a bounds
+// test.  Thread t computes columns t % 32 and t % 32 + 32 of row t / 32: each
+// weight, broadcast from shared memory, feeds both voxels.  Taps accumulate in
+// the same order as a plain per-voxel loop (bias first, then tap 0..26).
+constexpr int kCiH = 8, kCiW = 64;
+
+__global__ void __launch_bounds__(256) k_conv_in(const float* __restrict__ x, const float* __restrict__ prm, Vol g,
+                                                 int tiles_w, int tiles_h, __nv_bfloat16* __restrict__ act1) {
+    __shared__ float4 sw4[(27 * C + C) / 4];          // weights [27][32], then bias [32]
+    __shared__ float sx[3][kCiH + 2][kCiW + 2];       // frames z-1..z+1, rows y0-1.., columns x0-1..
+    float* sw = reinterpret_cast<float*>(sw4);
     for (int i = threadIdx.x; i < 27 * C; i += blockDim.x)
         sw[i] = __bfloat162float(__float2bfloat16_rn(prm[kW1 + i]));
     for (int i = threadIdx.x; i < C; i += blockDim.x) sw[27 * C + i] = prm[kB1 + i];
+    long long r = blockIdx.x;
+    const int tw = (int)(r % tiles_w);
+    r /= tiles_w;
+    const int th = (int)(r % tiles_h);
+    r /= tiles_h;
+    const int z = (int)(r % g.D), n = (int)(r / g.D);
+    const int x0 = tw * kCiW, y0 = th * kCiH;
+    for (int e = threadIdx.x; e < 3 * (kCiH + 2) * (kCiW + 2); e += blockDim.x) {
+        const int f = e / ((kCiH + 2) * (kCiW + 2)), rem = e % ((kCiH + 2) * (kCiW + 2));
+        const int zz = z + f - 1, yy = y0 - 1 + rem / (kCiW + 2), xx = x0 - 1 + rem % (kCiW + 2);
+        float v = 0.f;
+        if (zz >= 0 && zz < g.D && yy >= 0 && yy < g.H && xx >= 0 && xx < g.W)
+            v = __bfloat162float(__float2bfloat16_rn(x[(((long long)n * g.D + zz) * g.H + yy) * g.W + xx]));
+        sx[f][rem / (kCiW + 2)][rem % (kCiW + 2)] = v;
+    }
     __syncthreads();
-    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= g.V) return;
-    int n, z, y, xx;
-    decomp(g, v, n, z, y, xx);
-    float acc[32];
+    const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
+    float a0[32], a1[32];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) acc[c] = sw[27 * C + c];
+    for (int c = 0; c < 32; ++c) a0[c] = a1[c] = sw[27 * C + c];
+#pragma unroll 3
     for (int t = 0; t < 27; ++t) {
-        const long long u = nb(g, n, z, y, xx, t);
-        if (u < 0) continue;
-        const float xv = __bfloat162float(__float2bfloat16_rn(x[u]));
+        const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;
+        const float xv0 = sx[dz][ty + dy][tx + dx], xv1 = sx[dz][ty + dy][tx + 32 + dx];
 #pragma unroll
-        for (int c = 0; c < 32; ++c) acc[c] = fmaf(sw[t * C + c], xv, acc[c]);
+        for (int c4 = 0; c4 < 8; ++c4) {
+            const float4 w = sw4[t * 8 + c4];
+            a0[4 * c4 + 0] = fmaf(w.x, xv0, a0[4 * c4 + 0]);
+            a0[4 * c4 + 1] = fmaf(w.y, xv0, a0[4 * c4 + 1]);
+            a0[4 * c4 + 2] = fmaf(w.z, xv0, a0[4 * c4 + 2]);
+            a0[4 * c4 + 3] = fmaf(w.w, xv0, a0[4 * c4 + 3]);
+            a1[4 * c4 + 0] = fmaf(w.x, xv1, a1[4 * c4 + 0]);
+            a1[4 * c4 + 1] = fmaf(w.y, xv1, a1[4 * c4 + 1]);
+            a1[4 * c4 + 2] = fmaf(w.z, xv1, a1[4 * c4 + 2]);
+            a1[4 * c4 + 3] = fmaf(w.w, xv1, a1[4 * c4 + 3]);
+        }
     }
 #pragma unroll
-    for (int c = 0; c < 32; ++c) acc[c] = fmaxf(acc[c], 0.f);
-    store32(act1 + v * C, acc);
+    for (int c = 0; c < 32; ++c) {
+        a0[c] = fmaxf(a0[c], 0.f);
+        a1[c] = fmaxf(a1[c], 0.f);
+    }
+    const int yy = y0 + ty;
+    if (yy >= g.H) return;
+    const long long row = (((long long)n * g.D + z) * g.H + yy) * g.W;
+    if (x0 + tx < g.W) store32(act1 + (row + x0 + tx) * C, a0);
+    if (x0 + tx + 32 < g.W) store32(act1 + (row + x0 + tx + 32) * C, a1);
 }
 
 // layer 4 (32 -> 1) and the residual output theta = x + f.  With a target,
@@ -587,7 +625,11 @@ __global__ void k_project_vols(const float* __restrict__ theta, const float* __r
 bool enqueue_forward(const float* prm, const float* x, Vol g, const LWork& L, float* theta, const float* target,
                      cudaStream_t s) {
     k_prep_weights<<<(27 * C * C + 255) / 256, 256, 0, s>>>(prm, L.w2, L.w2t, L.w3, L.w3t, L.w4p);
-    k_conv_in<<<grid_for(g.V), 256, 0, s>>>(x, prm, g, L.a1);
+    {
+        const int tiles_w = (g.W + kCiW - 1) / kCiW, tiles_h = (g.H + kCiH - 1) / kCiH;
+        const long long blocks = (long long)g.nvol * g.D * tiles_h * tiles_w;
+        k_conv_in<<<(unsigned)blocks, 256, 0, s>>>(x, prm, g, tiles_w, tiles_h, L.a1);
+    }
     if (!launch_conv3d_c32_tc(L.a1, L.w2, prm + kB2, nullptr, 0, g.nvol, g.D, g.H, g.W, L.a2, L.err, s))
         return false;
     if (!launch_conv3d_c32_tc(L.a2, L.w3, prm + kB3, nullptr, 0, g.nvol, g.D, g.H, g.W, L.a3, L.err, s))
