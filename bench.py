@@ -253,6 +253,9 @@ def run_gpu(args):
     # ---- batched: 256 mixed-size measurements per call (BF16 and FP32 storage) ----
     batched = None if args.no_batched else _batched(pkg, torch, dev, stream, flush)
 
+    # ---- precision: GAP-ITV2D on 2048x2048x32 with FP32 / FP16 / BF16 storage ----
+    precision = None if args.no_precision else _precision(pkg, torch, dev, stream, flush)
+
     # ---- learned prox: trained here, then GAP-TV on 64 measurements of 512x512x10 ----
     learned = None if args.no_learned else _learned(pkg, torch, dev, stream, flush)
 
@@ -271,6 +274,7 @@ def run_gpu(args):
                                      "not stated)"),
         "psnr": psnr,
         "batched": batched,
+        "precision": precision,
         "learned": learned,
         "roofline": roof,
         "e2e": e2e,
@@ -417,6 +421,62 @@ def _batched(pkg, torch, dev, stream, flush):
         del batch
         torch.cuda.empty_cache()
     out["psnr_delta_f16_vs_f32_db"] = round(out["f16"]["mean_psnr_db"] - out["f32"]["mean_psnr_db"], 4)
+    return out
+
+
+def _precision(pkg, torch, dev, stream, flush):
+    """GAP-ITV2D on 2048x2048x32 (Bernoulli(0.5) masks, noise-free), T = 100,
+    S = 10, with the solver's fields stored as FP32, FP16 and BF16 (FP32
+    arithmetic throughout).  Timed once per storage after a warm-up call; every
+    field (512 MiB in FP32) is larger than L2.  Reports voxel-iters/s, PSNR
+    against the ground truth and its change against FP32, and the whole solve's
+    two roofline fractions.  Bytes: what the method must move per voxel and
+    outer iteration, i.e. read and write theta (2 x the field width), y
+    (4 / B bytes) and the mask word (4 / B), against the measured HBM rate.
+    Operations: 20 FP32 operations per voxel per dual update plus 3 for the
+    projection, against the derived FP32 ALU peak."""
+    import sci_synth as ss
+    cfg = ss.CONFIGS["gap_itv2d_2048x2048x32"]
+    nx, ny, B, T, S = cfg["nx"], cfg["ny"], cfg["B"], cfg["outer"], cfg["inner"]
+    case = ss.make_case(nx, ny, B, cfg["seed"], mask=cfg["mask"], sigma=cfg["sigma"])
+    x_gt = torch.from_numpy(case.x_gt.astype(np.float32)).to(dev)
+    bits = pkg.sci_masks_pack(torch.from_numpy(case.masks).to(dev))
+    del case
+    y = pkg.sci_forward(x_gt, bits)
+    N = B * nx * ny
+    hbm, hbm_kind = _peaks()
+    alu = _alu_peak()
+    out = {"workload": f"gap_itv2d_2048x2048x32: GAP-ITV2D, {nx}x{ny}x{B}, T={T}, S={S}, "
+                       f"lambda={cfg['lam']}, Bernoulli(0.5) masks, noise-free"}
+    theta = torch.empty((B, nx, ny), device=dev)
+    x = torch.empty_like(theta)
+    work = pkg.Workspace(dev)
+    for storage in ("f32", "f16", "bf16"):
+        def run():
+            pkg.sci_gap_tv(y, bits, B, "itv2d", cfg["lam"], T, S, theta=theta, x_out=x, init=True, work=work,
+                           storage=storage)
+        run()
+        torch.cuda.synchronize(dev)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        mse = float(pkg.sci_sqdiff_f64(x, x_gt).item()) / N
+        width = 4 if storage == "f32" else 2
+        bytes_alg = (2 * width + 8.0 / B) * N * T
+        ops_alg = (ALU_OPS_PER_UPDATE * S + 3) * N * T
+        out[storage] = {"value": N * T / (ms * 1e-3), "unit": UNIT, "ms": round(ms, 2),
+                        "psnr_db": round(10.0 * np.log10(1.0 / mse), 4),
+                        "hbm_frac": round(bytes_alg / (ms * 1e-3) / (hbm * 1e9), 4),
+                        "alu_frac": round(ops_alg / (ms * 1e-3) / alu, 4)}
+    for storage in ("f16", "bf16"):
+        out[storage]["delta_db_vs_f32"] = round(out[storage]["psnr_db"] - out["f32"]["psnr_db"], 4)
+    out["peaks"] = {"hbm_gbs": hbm, "hbm_kind": hbm_kind, "alu_tops": round(alu / 1e12, 3)}
+    del theta, x, work, y, x_gt, bits
+    torch.cuda.empty_cache()
     return out
 
 
@@ -604,6 +664,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-measurement batched solve")
     ap.add_argument("--no-learned", action="store_true", help="skip training and running the learned prox")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the 2048x2048x32 FP32 / FP16 / BF16 storage solves")
     ap.add_argument("--kernel-case", choices=["fused", "conv"], default=None,
                     help="run one launch of the dominant kernel per TV form and exit (for profilers)")
     args = ap.parse_args()
