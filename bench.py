@@ -666,7 +666,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip training and running the learned prox")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the 2048x2048x32 FP32 / FP16 / BF16 storage solves")
-    ap.add_argument("--kernel-case", choices=["fused", "conv"], default=None,
+    ap.add_argument("--kernel-case", choices=["fused", "conv", "lprox"], default=None,
                     help="run one launch of the dominant kernel per TV form and exit (for profilers)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -679,7 +679,9 @@ def main():
 def run_kernel_case(args):
     """fused: one temporally blocked FGP launch per TV form on the 512x512x10
     size.  conv: one tensor-core 32->32 conv over 8 x 10 x 512 x 512 voxels
-    (1.3 GB of BF16 activations, larger than L2)."""
+    (1.3 GB of BF16 activations, larger than L2).  lprox: the learned prox from
+    its initial weights, five applies on 8 x 10 x 512 x 512 and five training
+    steps on 32 x 8 x 64 x 64 (two of each untimed), timed with CUDA events."""
     import torch
     from paper_2005_08028_gb300 import build as b
     if not os.path.exists(b.LIB_PATH):
@@ -687,6 +689,31 @@ def run_kernel_case(args):
     import paper_2005_08028_gb300 as pkg
     c = _cfg()
     dev = torch.device("cuda")
+    if args.kernel_case == "lprox":
+        import paper_2005_08028_gb300.lprox_train as LT
+        net = pkg.LearnedProx(dev, params=LT.init_params(seed=1, device=dev))
+        gen = torch.Generator(device=dev).manual_seed(2)
+        x = torch.rand((8, 10, 512, 512), generator=gen, device=dev)
+        xt = torch.rand((32, 8, 64, 64), generator=gen, device=dev)
+        yt = xt.clone()
+
+        def timed(fn, warm=2, reps=3):
+            for _ in range(warm):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        out = {"kernel_case": "lprox", "apply_8x10x512x512_ms": round(timed(lambda: net.apply(x)), 3),
+               "train_step_32x8x64x64_ms": round(timed(lambda: net.train_step(xt, yt, 1e-4)), 3)}
+        out["ok"] = net.error_word(tuple(x.shape), False) == 0
+        print(json.dumps(out))
+        return 0 if out["ok"] else 1
     if args.kernel_case == "conv":
         act = torch.randn((8, 10, 512, 512, 32), device=dev).to(torch.bfloat16)
         wt = (0.05 * torch.randn((27, 32, 32), device=dev)).to(torch.bfloat16)
