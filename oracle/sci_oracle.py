@@ -28,6 +28,10 @@ Readings where the paper is silent or garbled (each is listed in the design doc):
   * FGP starts from w = p = 0 and nu = 1 at every TVdenoise call and returns
     t = x - lam*D^T p after S dual updates (Beck & Teboulle's output).
   * Loops run exactly T outer and S inner iterations.
+  * The Chambolle box of Algorithm 1 is read with its D^T as the divergence
+    (minus the adjoint), as in Chambolle's derivation; with the adjoint its
+    update ascends.  It keeps the max(1, |.|) denominator the paper states it
+    used.
   * Pixels with R = sum_k C_k^2 = 0 use the pseudo-inverse (R^+ = 0).
   * ADMM's TVdenoise uses the same lam as GAP (Eq. 25 has no rho).
 """
@@ -38,7 +42,7 @@ import numpy as np
 __all__ = [
     "TV_TYPES", "forward", "adjoint", "mask_energy", "gap_project", "admm_xupdate",
     "grad_h", "grad_v", "grad_h_adj", "grad_v_adj", "div_adj", "tv_value",
-    "dual_project", "fgp_momentum_coeffs", "fgp_prox", "prox_objective",
+    "dual_project", "fgp_momentum_coeffs", "fgp_prox", "divergence", "cham_prox", "prox_objective",
     "dual_objective", "gap_tv", "admm_tv", "psnr", "residual_sq",
 ]
 
@@ -238,6 +242,49 @@ def fgp_prox(x: np.ndarray, lam: float, S: int, tv: str, *, momentum: bool = Tru
     return theta
 
 
+def divergence(wh: np.ndarray, wv: np.ndarray) -> np.ndarray:
+    """div w = -(D_h^T w_h + D_v^T w_v): the divergence, minus the adjoint of
+    the forward-difference gradient (the reading of D^T in the Chambolle box)."""
+    return -div_adj(wh, wv)
+
+
+def cham_prox(x: np.ndarray, lam: float, S: int, tv: str, *, return_dual: bool = False):
+    """S iterations of Chambolle's dual algorithm for argmin_t 1/2||t - x||^2 + lam*TV(t).
+
+    Algorithm 1, ATV-Cham box (ITV2D-Cham and the ITV3D dual take the norms
+    of Eqs. 29-32, as in dual_project), with delta t = 1/8, w = 0 and
+    p_d = 0 at the start.  Per iteration s:
+      z   = p_d - x / lam
+      z_h = D_h z,  z_v = D_v z
+      w   = (w + delta t z) / max(1, |w + delta t z|)
+      p_d = div w
+    Output theta = x - lam p_d.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    dt = 1.0 / 8.0
+    wh = np.zeros_like(x)
+    wv = np.zeros_like(x)
+    pd = np.zeros_like(x)
+    for _ in range(S):
+        z = pd - x / lam
+        zh, zv = grad_h(z), grad_v(z)
+        wh, wv = dual_project(wh + dt * zh, wv + dt * zv, tv)
+        pd = divergence(wh, wv)
+    theta = x - lam * pd
+    if return_dual:
+        return theta, (wh, wv)
+    return theta
+
+
+def _tv_denoise(dual: str):
+    """TVdenoise of Algorithm 1: the FGP box or the Chambolle box."""
+    if dual == "fgp":
+        return fgp_prox
+    if dual == "cham":
+        return cham_prox
+    raise ValueError(f"unknown dual solver {dual!r}")
+
+
 def prox_objective(theta: np.ndarray, x: np.ndarray, lam: float, tv: str) -> float:
     """Primal objective 1/2||theta - x||^2 + lam*TV(theta)."""
     d = np.asarray(theta, np.float64) - np.asarray(x, np.float64)
@@ -260,33 +307,36 @@ def dual_objective(ph: np.ndarray, pv: np.ndarray, x: np.ndarray, lam: float) ->
 # --------------------------------------------------------------------------
 
 def gap_tv(y: np.ndarray, C: np.ndarray, lam: float, T: int, S: int, tv: str,
-           theta0: np.ndarray | None = None):
+           theta0: np.ndarray | None = None, dual: str = "fgp"):
     """GAP-TV (Eqs. 21-22; Algorithm 1): returns (x^(T), theta^(T)).
 
     theta^(0) = Phi^T y unless ``theta0`` is given (resuming).  Each of the T
-    iterations projects onto {Phi x = y} and applies the S-step FGP prox.
+    iterations projects onto {Phi x = y} and applies the S-step TVdenoise
+    (``dual`` = 'fgp' or 'cham': the FGP or the Chambolle box).
     """
+    denoise = _tv_denoise(dual)
     theta = adjoint(y, C) if theta0 is None else np.array(theta0, dtype=np.float64)
     x = theta
     for _ in range(T):
         x = gap_project(theta, y, C)
-        theta = fgp_prox(x, lam, S, tv)
+        theta = denoise(x, lam, S, tv)
     return x, theta
 
 
 def admm_tv(y: np.ndarray, C: np.ndarray, lam: float, rho: float, T: int, S: int,
-            tv: str, theta0: np.ndarray | None = None, u0: np.ndarray | None = None):
+            tv: str, theta0: np.ndarray | None = None, u0: np.ndarray | None = None, dual: str = "fgp"):
     """ADMM-TV (Eqs. 24-26): returns (x^(T), theta^(T), u^(T)).
 
     theta^(0) = Phi^T y and u^(0) = 0 unless given.  Per iteration:
     x = admm_xupdate(theta, u), theta = TVdenoise(u + x), u = u + x - theta.
     """
+    denoise = _tv_denoise(dual)
     theta = adjoint(y, C) if theta0 is None else np.array(theta0, dtype=np.float64)
     u = np.zeros_like(theta) if u0 is None else np.array(u0, dtype=np.float64)
     x = theta
     for _ in range(T):
         x = admm_xupdate(theta, u, y, C, rho)
-        theta = fgp_prox(u + x, lam, S, tv)
+        theta = denoise(u + x, lam, S, tv)
         u = u + x - theta
     return x, theta, u
 
