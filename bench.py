@@ -253,6 +253,9 @@ def run_gpu(args):
     # ---- batched: 256 mixed-size measurements per call (BF16 and FP32 storage) ----
     batched = None if args.no_batched else _batched(pkg, torch, dev, stream, flush)
 
+    # ---- the Chambolle TVdenoise box on the same measurement ----
+    cham = _chambolle(pkg, torch, dev, stream, flush, c, y, bits, x_gt, psnr)
+
     # ---- precision: GAP-ITV2D on 2048x2048x32 with FP32 / FP16 / BF16 storage ----
     precision = None if args.no_precision else _precision(pkg, torch, dev, stream, flush)
 
@@ -273,6 +276,7 @@ def run_gpu(args):
                                      "i7 laptop (about 2.2e6 voxel-iters/s; real data, inner iterations "
                                      "not stated)"),
         "psnr": psnr,
+        "chambolle": cham,
         "batched": batched,
         "precision": precision,
         "learned": learned,
@@ -421,6 +425,38 @@ def _batched(pkg, torch, dev, stream, flush):
         del batch
         torch.cuda.empty_cache()
     out["psnr_delta_f16_vs_f32_db"] = round(out["f16"]["mean_psnr_db"] - out["f32"]["mean_psnr_db"], 4)
+    return out
+
+
+def _chambolle(pkg, torch, dev, stream, flush, c, y, bits, x_gt, psnr_fgp):
+    """The Chambolle TVdenoise box (Algorithm 1, ATV-Cham; ITV2D / ITV3D
+    norms) in GAP-TV on the same 512x512x10 measurement, T = 200, S = 10: one
+    timed solve per TV form after a warm-up, L2 flushed before.  PSNR beside
+    the FGP box's (the comparison of the paper's Table 1 columns)."""
+    B, nx, ny = c["B"], c["nx"], c["ny"]
+    N = B * nx * ny
+    theta = torch.empty((B, nx, ny), device=dev)
+    x = torch.empty_like(theta)
+    work = pkg.Workspace(dev)
+    out = {"workload": f"GAP-TV with the Chambolle box, {nx}x{ny}x{B}, T={c['outer']}, S={c['inner']}, "
+                       f"lambda={c['lam']}"}
+    for tv in ("atv", "itv2d", "vtv"):
+        def run():
+            pkg.sci_gap_tv(y, bits, B, tv, c["lam"], c["outer"], c["inner"], theta=theta, x_out=x, init=True,
+                           work=work, dual="cham")
+        run()
+        torch.cuda.synchronize(dev)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        mse = float(pkg.sci_sqdiff_f64(x, x_gt).item()) / N
+        out[tv] = {"value": N * c["outer"] / (ms * 1e-3), "unit": UNIT, "ms": round(ms, 2),
+                   "psnr_db": round(10.0 * np.log10(1.0 / mse), 4),
+                   "psnr_fgp_db": psnr_fgp.get(f"gap_{tv}", {}).get("gpu_db")}
     return out
 
 

@@ -56,6 +56,15 @@ typedef enum {
 typedef enum { SCI_TV_ATV = 0, SCI_TV_ITV2D = 1, SCI_TV_VTV = 2 } sci_tv_type;
 typedef enum { SCI_F32 = 0, SCI_BF16 = 1, SCI_F16 = 2 } sci_dtype;
 
+/* TVdenoise dual solver (Algorithm 1's boxes, Sec. 2.3).  FGP: the ATV-FGP
+ * box, accelerated with the nu recursion.  CHAM: the ATV-Cham box with
+ * delta t = 1/8 and the max(1, |.|) denominator the paper states it used,
+ * reading its D^T as the divergence (minus the adjoint; with the adjoint the
+ * printed update ascends).  It is then the same projected dual step as FGP
+ * without momentum (nu = 1 throughout), and the ITV2D / VTV forms take the
+ * paper's norms for ITV2D-Cham and the ITV3D dual (Eqs. 29-32). */
+typedef enum { SCI_DUAL_FGP = 0, SCI_DUAL_CHAM = 1 } sci_dual_solver;
+
 /* Solver parameters (Algorithm 1; Sec. 2.2). */
 typedef struct {
     int tv;           /* sci_tv_type: ATV (Eq. 8), ITV2D (Eq. 9) or VTV = ITV3D (Eq. 10) */
@@ -69,6 +78,7 @@ typedef struct {
                          allows), -1 = one launch per update (no temporal blocking) */
     int init;         /* 1: start from theta = Phi^T y (and u = 0); 0: resume from theta (and u) */
     int use_graph;    /* 1: run the T iterations as one cached CUDA graph; 0: plain launches */
+    int dual;         /* sci_dual_solver of TVdenoise; 0 (FGP) when zero-initialised */
 } sci_params;
 
 /* Human-readable name of a status code (static string). */
@@ -118,6 +128,17 @@ size_t sci_tv_prox_workspace(int nx, int ny, int B, int tv);
 sci_status sci_tv_prox(const float* x, int nx, int ny, int B, int tv, float lambda,
                        int inner_iters, float* theta, void* work, size_t work_bytes,
                        sci_stream_t stream);
+
+/*
+ * TVdenoise by Chambolle's dual projection (Algorithm 1, ATV-Cham box, with
+ * the reading stated at sci_dual_solver): inner_iters dual updates from
+ * w = 0, w <- proj(w + (1/(8 lambda)) D theta) with theta = x - lambda D^T w,
+ * then theta = x - lambda D^T w.  Same arguments, layouts, workspace
+ * (sci_tv_prox_workspace) and errors as sci_tv_prox.
+ */
+sci_status sci_tv_prox_cham(const float* x, int nx, int ny, int B, int tv, float lambda,
+                            int inner_iters, float* theta, void* work, size_t work_bytes,
+                            sci_stream_t stream);
 
 /* Bytes of scratch sci_gap_tv / sci_admm_tv need for these sizes and params. */
 size_t sci_solver_workspace(int nx, int ny, int B, const sci_params* params);

@@ -30,9 +30,12 @@ constexpr int kVersion = 10000;  // 1.0.0
 
 bool finite_pos(float v) { return std::isfinite(v) && v > 0.f; }
 
-// Momentum coefficients (nu_s - 1)/nu_{s+1}, nu_0 = 1, computed in FP64.
-std::vector<float> momentum_coeffs(int S) {
-    std::vector<float> c((size_t)std::max(S, 1));
+// Momentum coefficients (nu_s - 1)/nu_{s+1}, nu_0 = 1, computed in FP64
+// (Algorithm 1, ATV-FGP box); all zero for the Chambolle box, whose dual
+// update is the same projected step without momentum.
+std::vector<float> momentum_coeffs(int S, int dual = SCI_DUAL_FGP) {
+    std::vector<float> c((size_t)std::max(S, 1), 0.f);
+    if (dual == SCI_DUAL_CHAM) return c;
     double nu = 1.0;
     for (int s = 0; s < S; ++s) {
         const double nx = (1.0 + std::sqrt(1.0 + 4.0 * nu * nu)) / 2.0;
@@ -90,6 +93,7 @@ sci_status validate_params(const sci_params* p, bool admm) {
     if (p->outer_iters < 0 || p->inner_iters < 1) return SCI_ERR_ARG;
     if (p->storage < SCI_F32 || p->storage > SCI_F16) return SCI_ERR_ARG;
     if (p->fuse_k < -1) return SCI_ERR_ARG;
+    if (p->dual != SCI_DUAL_FGP && p->dual != SCI_DUAL_CHAM) return SCI_ERR_ARG;
     return SCI_OK;
 }
 
@@ -193,7 +197,7 @@ int enqueue_solve(const SolveArgs& A, cudaStream_t s) {
     const int T_outer = A.prm.outer_iters, S = A.prm.inner_iters;
     const float lam = A.prm.lambda;
     if (T_outer > 0) { launch_residual_field<T>(theta, u, A.y, A.bits, rinv, g, r, s); ++nk; }
-    const std::vector<float> coef = momentum_coeffs(S);
+    const std::vector<float> coef = momentum_coeffs(S, A.prm.dual);
     const OuterMode mode = A.admm ? OuterMode::Admm : OuterMode::Gap;
     const int nparts = out_partial_count(g);
     const int K = choose_fuse(A.prm.tv, A.B, S, A.prm.fuse_k);
@@ -414,8 +418,8 @@ size_t sci_tv_prox_workspace(int nx, int ny, int B, int tv) {
     return prox_layout(nx, ny, B).total;
 }
 
-sci_status sci_tv_prox(const float* x, int nx, int ny, int B, int tv, float lambda, int inner_iters,
-                       float* theta, void* work, size_t work_bytes, sci_stream_t stream) {
+static sci_status tv_prox_impl(const float* x, int nx, int ny, int B, int tv, float lambda, int inner_iters,
+                               float* theta, void* work, size_t work_bytes, sci_stream_t stream, int dual) {
     if (x == nullptr || theta == nullptr || x == theta || !sizes_ok(nx, ny, B)) return SCI_ERR_ARG;
     if (tv < SCI_TV_ATV || tv > SCI_TV_VTV || inner_iters < 1) return SCI_ERR_ARG;
     if (!std::isfinite(lambda)) return SCI_ERR_NONFINITE;
@@ -428,7 +432,7 @@ sci_status sci_tv_prox(const float* x, int nx, int ny, int B, int tv, float lamb
     char* w = static_cast<char*>(work);
     float* P[4] = {reinterpret_cast<float*>(w + L.p[0]), reinterpret_cast<float*>(w + L.p[1]),
                    reinterpret_cast<float*>(w + L.p[2]), reinterpret_cast<float*>(w + L.p[3])};
-    const std::vector<float> coef = momentum_coeffs(inner_iters);
+    const std::vector<float> coef = momentum_coeffs(inner_iters, dual);
     const int K = choose_fuse(tv, B, inner_iters, 0);
     if (K > 0) {
         FusedArgs base{};
@@ -458,6 +462,16 @@ sci_status sci_tv_prox(const float* x, int nx, int ny, int B, int tv, float lamb
     oa.theta_f32 = theta;
     launch_fgp_out<float>(oa, x, P[cur], g, lambda, nullptr, nullptr, s);
     return check_launch();
+}
+
+sci_status sci_tv_prox(const float* x, int nx, int ny, int B, int tv, float lambda, int inner_iters,
+                       float* theta, void* work, size_t work_bytes, sci_stream_t stream) {
+    return tv_prox_impl(x, nx, ny, B, tv, lambda, inner_iters, theta, work, work_bytes, stream, SCI_DUAL_FGP);
+}
+
+sci_status sci_tv_prox_cham(const float* x, int nx, int ny, int B, int tv, float lambda, int inner_iters,
+                            float* theta, void* work, size_t work_bytes, sci_stream_t stream) {
+    return tv_prox_impl(x, nx, ny, B, tv, lambda, inner_iters, theta, work, work_bytes, stream, SCI_DUAL_CHAM);
 }
 
 size_t sci_solver_workspace(int nx, int ny, int B, const sci_params* params) {

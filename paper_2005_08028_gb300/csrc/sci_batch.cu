@@ -103,6 +103,7 @@ sci_status make_plan(const sci_problem* probs, int count, const sci_params* prm,
     if (!std::isfinite(prm->lambda)) return SCI_ERR_NONFINITE;
     if (!(prm->lambda > 0.f) || prm->outer_iters < 0 || prm->inner_iters < 1) return SCI_ERR_ARG;
     if (prm->storage < SCI_F32 || prm->storage > SCI_F16 || prm->fuse_k < -1) return SCI_ERR_ARG;
+    if (prm->dual != SCI_DUAL_FGP && prm->dual != SCI_DUAL_CHAM) return SCI_ERR_ARG;
     for (int i = 0; i < count; ++i) {
         const sci_problem& p = probs[i];
         if (p.nx <= 0 || p.ny <= 0 || p.B <= 0 || p.y == nullptr || p.bits == nullptr || p.theta == nullptr)
@@ -220,8 +221,8 @@ int enqueue_batch(const BatchPlan& P, const sci_params* prm, const BatchItem<T>*
     const int T_outer = prm->outer_iters, S = prm->inner_iters;
     int tpar = 0;
     if (T_outer > 0) { k_batch_residual<T><<<pb, 256, 0, s>>>(d_items, nitems, tpar); ++nk; }
-    std::vector<double> nu_c((size_t)S);
-    {
+    std::vector<double> nu_c((size_t)S, 0.0);  // momentum coefficients; zero for the Chambolle box
+    if (prm->dual == SCI_DUAL_FGP) {
         double nu = 1.0;
         for (int i = 0; i < S; ++i) {
             const double nx = (1.0 + std::sqrt(1.0 + 4.0 * nu * nu)) / 2.0;

@@ -13,7 +13,7 @@ import threading
 import torch
 
 __all__ = [
-    "SciError", "TV", "DTYPE", "load", "sci_masks_pack", "sci_forward", "sci_adjoint",
+    "SciError", "TV", "DTYPE", "DUAL", "load", "sci_masks_pack", "sci_forward", "sci_adjoint",
     "sci_project", "sci_tv_prox", "sci_gap_tv", "sci_admm_tv", "sci_sqdiff_f64",
     "sci_residual_f64", "sci_graph_cache_clear", "sci_tv_prox_noalloc", "sci_last_solve_launches", "sci_fused_updates", "Batch", "SciProblem",
     "sci_gap_tv_batched", "sci_last_batch_launches",
@@ -39,7 +39,7 @@ class SciError(RuntimeError):
 class SciParams(C.Structure):
     _fields_ = [("tv", C.c_int), ("lam", C.c_float), ("rho", C.c_float),
                 ("outer_iters", C.c_int), ("inner_iters", C.c_int), ("storage", C.c_int),
-                ("fuse_k", C.c_int), ("init", C.c_int), ("use_graph", C.c_int)]
+                ("fuse_k", C.c_int), ("init", C.c_int), ("use_graph", C.c_int), ("dual", C.c_int)]
 
 
 class SciProblem(C.Structure):
@@ -57,6 +57,7 @@ _SIGS = {
     "sci_project": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _f, _vp, _vp]),
     "sci_tv_prox_workspace": (_sz, [_i, _i, _i, _i]),
     "sci_tv_prox": (_i, [_vp, _i, _i, _i, _i, _f, _i, _vp, _vp, _sz, _vp]),
+    "sci_tv_prox_cham": (_i, [_vp, _i, _i, _i, _i, _f, _i, _vp, _vp, _sz, _vp]),
     "sci_solver_workspace": (_sz, [_i, _i, _i, C.POINTER(SciParams)]),
     "sci_gap_tv": (_i, [_vp, _vp, _i, _i, _i, C.POINTER(SciParams), _vp, _vp, _vp, _i, _vp, _sz, _vp]),
     "sci_admm_tv": (_i, [_vp, _vp, _i, _i, _i, C.POINTER(SciParams), _vp, _vp, _vp, _vp, _i, _vp, _sz,
@@ -188,16 +189,18 @@ def sci_project(theta: torch.Tensor, y: torch.Tensor, bits: torch.Tensor, rho: f
 
 
 def sci_tv_prox(x: torch.Tensor, tv: str, lam: float, inner_iters: int,
-                work: Workspace | None = None) -> torch.Tensor:
-    """FGP TV proximal map with `inner_iters` dual updates (Algorithm 1, FGP box)."""
+                work: Workspace | None = None, dual: str = "fgp") -> torch.Tensor:
+    """TV proximal map with `inner_iters` dual updates: dual='fgp' (Algorithm 1,
+    FGP box; sci_tv_prox) or 'cham' (Chambolle box; sci_tv_prox_cham)."""
     _need_cuda(x)
     B, nx, ny = x.shape
     lib = load()
     need = lib.sci_tv_prox_workspace(nx, ny, B, TV[tv])
     wbuf = (work or Workspace(x.device)).get(need)
     theta = torch.empty_like(x)
-    _check("sci_tv_prox", lib.sci_tv_prox(_ptr(x), nx, ny, B, TV[tv], float(lam), int(inner_iters),
-                                          _ptr(theta), _ptr(wbuf), wbuf.numel(), _stream(x.device)))
+    name = {"fgp": "sci_tv_prox", "cham": "sci_tv_prox_cham"}[dual]
+    _check(name, getattr(lib, name)(_ptr(x), nx, ny, B, TV[tv], float(lam), int(inner_iters),
+                                    _ptr(theta), _ptr(wbuf), wbuf.numel(), _stream(x.device)))
     return theta
 
 
@@ -217,13 +220,16 @@ def sci_tv_prox_noalloc(x: torch.Tensor, tv: str, lam: float, inner_iters: int) 
     return theta
 
 
-def _params(tv, lam, rho, outer, inner, storage, fuse_k, init, use_graph):
+DUAL = {"fgp": 0, "cham": 1}
+
+
+def _params(tv, lam, rho, outer, inner, storage, fuse_k, init, use_graph, dual="fgp"):
     return SciParams(TV[tv], float(lam), float(rho), int(outer), int(inner), DTYPE[storage],
-                     int(fuse_k), int(init), int(use_graph))
+                     int(fuse_k), int(init), int(use_graph), DUAL[dual])
 
 
 def _solve(admm: bool, y, bits, B, tv, lam, outer, inner, rho=0.0, storage="f32", theta=None, u=None,
-           init=None, x_out=None, resid=None, resid_every=0, fuse_k=0, use_graph=True, work=None):
+           init=None, x_out=None, resid=None, resid_every=0, fuse_k=0, use_graph=True, work=None, dual="fgp"):
     _need_cuda(y, bits, theta, u, x_out, resid)
     nx, ny = y.shape
     dev = y.device
@@ -237,7 +243,7 @@ def _solve(admm: bool, y, bits, B, tv, lam, outer, inner, rho=0.0, storage="f32"
         u = torch.empty((B, nx, ny), dtype=torch.float32, device=dev)
     if x_out is None:
         x_out = torch.empty((B, nx, ny), dtype=torch.float32, device=dev)
-    prm = _params(tv, lam, rho, outer, inner, storage, fuse_k, init, use_graph)
+    prm = _params(tv, lam, rho, outer, inner, storage, fuse_k, init, use_graph, dual)
     lib = load()
     need = lib.sci_solver_workspace(nx, ny, B, C.byref(prm))
     wbuf = (work or Workspace(dev)).get(need)
@@ -261,7 +267,8 @@ def sci_gap_tv(y, bits, B, tv, lam, outer, inner, **kw):
     Keyword arguments: storage ('f32'|'bf16'|'f16'); theta (state buffer,
     updated in place: resumed from unless init=True; default a new buffer
     started at Phi^T y); init; x_out; resid; resid_every; fuse_k; use_graph;
-    work (a Workspace reused across calls).  Reusing the same buffers lets
+    work (a Workspace reused across calls); dual ('fgp' or 'cham', the
+    TVdenoise box of Algorithm 1).  Reusing the same buffers lets
     the library replay its cached CUDA graph.
     """
     return _solve(False, y, bits, B, tv, lam, outer, inner, **kw)
@@ -298,9 +305,9 @@ class Batch:
 
 
 def sci_gap_tv_batched(batch: Batch, tv, lam, outer, inner, storage="f32", init=True, fuse_k=0,
-                       use_graph=True):
+                       use_graph=True, dual="fgp"):
     """GAP-TV on every measurement of `batch` (results in batch.x_outs / batch.thetas)."""
-    prm = _params(tv, lam, 0.0, outer, inner, storage, fuse_k, init, use_graph)
+    prm = _params(tv, lam, 0.0, outer, inner, storage, fuse_k, init, use_graph, dual)
     lib = load()
     n = len(batch.ys)
     need = lib.sci_gap_tv_batched_workspace(batch.problems, n, C.byref(prm))

@@ -62,6 +62,9 @@ def test_argument_errors_return_before_any_launch(lib):
     assert lib.sci_gap_tv(fake, fake, 8, 8, 2, C.byref(s0), fake, fake, None, 0, fake, 1 << 30, None) == 1
     tv9 = SciParams(9, 0.05, 0.0, 10, 5, 0, 0, 1, 1)
     assert lib.sci_gap_tv(fake, fake, 8, 8, 2, C.byref(tv9), fake, fake, None, 0, fake, 1 << 30, None) == 1
+    dual7 = SciParams(0, 0.05, 0.0, 10, 5, 0, 0, 1, 1, 7)  # neither FGP (0) nor Chambolle (1)
+    assert lib.sci_gap_tv(fake, fake, 8, 8, 2, C.byref(dual7), fake, fake, None, 0, fake, 1 << 30, None) == 1
+    assert lib.sci_tv_prox_cham(fake, 8, 8, 2, 0, 0.05, 5, fake, fake, 1 << 30, None) == 1  # x aliases theta
     neg = SciParams(0, 0.05, -0.5, 10, 5, 0, 0, 1, 1)
     assert lib.sci_admm_tv(fake, fake, 8, 8, 2, C.byref(neg), fake, fake, fake, None, 0, fake, 1 << 30,
                            None) == 1
