@@ -34,6 +34,11 @@ Readings where the paper is silent or garbled (each is listed in the design doc):
     used.
   * Pixels with R = sum_k C_k^2 = 0 use the pseudo-inverse (R^+ = 0).
   * ADMM's TVdenoise uses the same lam as GAP (Eq. 25 has no rho).
+  * FISTA (Sec. 2.2): L(f) = ||Phi||^2 = max_ij R_ij (Phi Phi^T = diag(R));
+    its momentum reads theta^(t+1) = x^(t) + ((tau_t - 1)/tau_{t+1})
+    (x^(t) - x^(t-1)) with tau_1 = 1 (the printed update's indices are
+    garbled); TVdenoise takes the same lam as GAP (plug-in reading), so its
+    fixed points minimise 1/2||y - Phi x||^2 + lam L TV(x).
 """
 from __future__ import annotations
 
@@ -43,7 +48,7 @@ __all__ = [
     "TV_TYPES", "forward", "adjoint", "mask_energy", "gap_project", "admm_xupdate",
     "grad_h", "grad_v", "grad_h_adj", "grad_v_adj", "div_adj", "tv_value",
     "dual_project", "fgp_momentum_coeffs", "fgp_prox", "divergence", "cham_prox", "prox_objective",
-    "dual_objective", "gap_tv", "admm_tv", "psnr", "residual_sq",
+    "dual_objective", "gap_tv", "admm_tv", "lipschitz", "fista_tv", "psnr", "residual_sq",
 ]
 
 TV_TYPES = ("atv", "itv2d", "vtv")
@@ -339,6 +344,40 @@ def admm_tv(y: np.ndarray, C: np.ndarray, lam: float, rho: float, T: int, S: int
         theta = denoise(u + x, lam, S, tv)
         u = u + x - theta
     return x, theta, u
+
+
+def lipschitz(C: np.ndarray) -> float:
+    """L(f) for f(x) = 1/2||y - Phi x||^2: ||Phi||^2 = ||Phi Phi^T|| = max_ij R_ij."""
+    return float(np.max(mask_energy(C)))
+
+
+def fista_tv(y: np.ndarray, C: np.ndarray, lam: float, T: int, S: int, tv: str,
+             theta0: np.ndarray | None = None, dual: str = "fgp"):
+    """FISTA-TV (Sec. 2.2, FISTA steps): returns (x^(T), x^(T)).
+
+    theta^(1) = Phi^T y unless ``theta0`` is given; tau_1 = 1.  Iteration t:
+      z^(t)        = theta^(t) + (1/L) Phi^T (y - Phi theta^(t))
+      x^(t)        = TVdenoise(z^(t))
+      tau_{t+1}    = (1 + sqrt(1 + 4 tau_t^2)) / 2
+      theta^(t+1)  = x^(t) + ((tau_t - 1)/tau_{t+1}) (x^(t) - x^(t-1))
+    The estimate is x^(T); it is also returned as the second value, in the
+    place where gap_tv returns theta.
+    """
+    denoise = _tv_denoise(dual)
+    L = lipschitz(C)
+    step = 0.0 if L == 0.0 else 1.0 / L
+    theta = adjoint(y, C) if theta0 is None else np.array(theta0, dtype=np.float64)
+    x_prev = np.zeros_like(theta)
+    x = theta
+    tau = 1.0
+    for _ in range(T):
+        z = theta + step * adjoint(y - forward(theta, C), C)
+        x = denoise(z, lam, S, tv)
+        tau_next = (1.0 + np.sqrt(1.0 + 4.0 * tau * tau)) / 2.0
+        theta = x + ((tau - 1.0) / tau_next) * (x - x_prev)
+        x_prev = x
+        tau = tau_next
+    return x, x
 
 
 # --------------------------------------------------------------------------
