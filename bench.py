@@ -255,6 +255,7 @@ def run_gpu(args):
 
     # ---- the Chambolle TVdenoise box on the same measurement ----
     cham = _chambolle(pkg, torch, dev, stream, flush, c, y, bits, x_gt, psnr)
+    fista = _fista(pkg, torch, dev, stream, flush, c, y, bits, x_gt, psnr)
 
     # ---- precision: GAP-ITV2D on 2048x2048x32 with FP32 / FP16 / BF16 storage ----
     precision = None if args.no_precision else _precision(pkg, torch, dev, stream, flush)
@@ -277,6 +278,7 @@ def run_gpu(args):
                                      "not stated)"),
         "psnr": psnr,
         "chambolle": cham,
+        "fista": fista,
         "batched": batched,
         "precision": precision,
         "learned": learned,
@@ -457,6 +459,37 @@ def _chambolle(pkg, torch, dev, stream, flush, c, y, bits, x_gt, psnr_fgp):
         out[tv] = {"value": N * c["outer"] / (ms * 1e-3), "unit": UNIT, "ms": round(ms, 2),
                    "psnr_db": round(10.0 * np.log10(1.0 / mse), 4),
                    "psnr_fgp_db": psnr_fgp.get(f"gap_{tv}", {}).get("gpu_db")}
+    return out
+
+
+def _fista(pkg, torch, dev, stream, flush, c, y, bits, x_gt, psnr_gap):
+    """FISTA-TV (Sec. 2.2; L = max R, the same lambda as GAP, FGP box) on the
+    same 512x512x10 measurement, T = 200, S = 10: one timed solve per TV form
+    after a warm-up, L2 flushed before.  PSNR beside GAP-TV's (the framework
+    rows of the paper's Table 1)."""
+    B, nx, ny = c["B"], c["nx"], c["ny"]
+    N = B * nx * ny
+    theta = torch.empty((B, nx, ny), device=dev)
+    x = torch.empty_like(theta)
+    work = pkg.Workspace(dev)
+    out = {"workload": f"FISTA-TV, {nx}x{ny}x{B}, T={c['outer']}, S={c['inner']}, lambda={c['lam']}"}
+    for tv in ("atv", "itv2d", "vtv"):
+        def run():
+            pkg.sci_fista_tv(y, bits, B, tv, c["lam"], c["outer"], c["inner"], theta=theta, x_out=x, init=True,
+                             work=work)
+        run()
+        torch.cuda.synchronize(dev)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        mse = float(pkg.sci_sqdiff_f64(x, x_gt).item()) / N
+        out[tv] = {"value": N * c["outer"] / (ms * 1e-3), "unit": UNIT, "ms": round(ms, 2),
+                   "psnr_db": round(10.0 * np.log10(1.0 / mse), 4),
+                   "psnr_gap_db": psnr_gap.get(f"gap_{tv}", {}).get("gpu_db")}
     return out
 
 

@@ -158,6 +158,24 @@ sci_status sci_gap_tv(const float* y, const uint32_t* bits, int nx, int ny, int 
                       sci_stream_t stream);
 
 /*
+ * FISTA-TV (Sec. 2.2, FISTA steps), with L = ||Phi||^2 = max_ij R_ij and
+ * tau_1 = 1: T iterations of
+ *   z = theta + (1/L) Phi^T (y - Phi theta);  x = TVdenoise(z);
+ *   theta = x + ((tau_t - 1)/tau_{t+1}) (x - x_prev).
+ * TVdenoise takes params->lambda (the same plug-in strength as GAP), so a
+ * fixed point minimises 1/2||y - Phi x||^2 + lambda L TV(x).  The printed
+ * momentum indices are garbled; this is standard FISTA.  Same arguments,
+ * workspace (sci_solver_workspace) and errors as sci_gap_tv.  params->init = 1
+ * starts from theta = Phi^T y; 0 starts from the given theta with the momentum
+ * restarted.  On return theta and x_out (if not NULL) hold the estimate x^(T).
+ * resid (if resid_every > 0) records ||y - Phi x^(t)||^2.
+ */
+sci_status sci_fista_tv(const float* y, const uint32_t* bits, int nx, int ny, int B,
+                        const sci_params* params, float* theta, float* x_out,
+                        double* resid, int resid_every, void* work, size_t work_bytes,
+                        sci_stream_t stream);
+
+/*
  * ADMM-TV (Eqs. 24-26): T iterations of
  *   x = ADMM x-update (rho = params->rho);  theta = TVdenoise(u + x);  u = u + x - theta.
  * TVdenoise uses params->lambda (Eq. 25 carries no rho).  theta, u: in/out

@@ -47,7 +47,7 @@ std::vector<float> momentum_coeffs(int S, int dual = SCI_DUAL_FGP) {
 
 // ---- workspace layout ----
 struct Layout {
-    size_t rinv, r, partials, xt, p[4], theta_s, theta_s2, u_s, total;
+    size_t rinv, r, partials, xt, p[4], theta_s, theta_s2, u_s, xprev, lmax, total;
 };
 
 Layout solver_layout(int nx, int ny, int B, int storage, bool admm) {
@@ -65,6 +65,8 @@ Layout solver_layout(int nx, int ny, int B, int storage, bool admm) {
     L.theta_s2 = take(N * es);  // second theta buffer: the fused launch reads theta^(t) halos
                                 // while other CTAs write theta^(t+1)
     L.u_s = (storage != SCI_F32 && admm) ? take(N * es) : 0;
+    L.xprev = take(N * es);  // FISTA: x^(t-1)
+    L.lmax = take(256);      // FISTA: the largest mask count
     L.total = off;
     return L;
 }
@@ -149,6 +151,7 @@ int enqueue_fused_prox(int tv, OuterMode mode, int K, int S, float lam, const st
 // ---- the outer loop ----
 struct SolveArgs {
     bool admm;
+    bool fista;  // FISTA outer loop (admm is then false)
     const float* y;
     const uint32_t* bits;
     int nx, ny, B;
@@ -183,8 +186,26 @@ int enqueue_solve(const SolveArgs& A, cudaStream_t s) {
     if (A.admm) u = f32 ? reinterpret_cast<T*>(A.u) : reinterpret_cast<T*>(w + L.u_s);
     T* const theta_home = theta;
 
-    launch_rinv(A.bits, g, A.admm ? A.prm.rho : 0.f, rinv, s);
-    ++nk;
+    T* xprev = reinterpret_cast<T*>(w + L.xprev);
+    if (A.fista) {
+        // z = theta + (1/L) Phi^T (y - Phi theta): the GAP residual with 1/L for 1/R
+        launch_fista_step(A.bits, g, reinterpret_cast<unsigned*>(w + L.lmax), rinv, s);
+        launch_zero(xprev, (size_t)N * sizeof(T), s);
+        nk += 2;
+    } else {
+        launch_rinv(A.bits, g, A.admm ? A.prm.rho : 0.f, rinv, s);
+        ++nk;
+    }
+    // FISTA momentum coefficients (tau_t - 1)/tau_{t+1}, tau_1 = 1, in FP64
+    std::vector<float> beta((size_t)std::max(A.prm.outer_iters, 1), 0.f);
+    if (A.fista) {
+        double tau = 1.0;
+        for (int t = 0; t < A.prm.outer_iters; ++t) {
+            const double next = (1.0 + std::sqrt(1.0 + 4.0 * tau * tau)) / 2.0;
+            beta[(size_t)t] = (float)((tau - 1.0) / next);
+            tau = next;
+        }
+    }
     if (A.prm.init) {
         launch_adjoint<T>(A.y, A.bits, g, theta, s);
         ++nk;
@@ -214,10 +235,21 @@ int enqueue_solve(const SolveArgs& A, cudaStream_t s) {
             FusedBufs<T> fb{theta, u, theta_alt, u, xt,
                             {P[0], P[0] + N, P[1], P[1] + N}, {P[2], P[2] + N, P[3], P[3] + N}};
             const int nf = enqueue_fused_prox<T>(A.prm.tv, mode, K, S, lam, coef, base, fb,
-                                                 last ? A.x_out : nullptr, s);
+                                                 (last && !A.fista) ? A.x_out : nullptr, s);
             if (nf < 0) return -1;
             nk += nf;
             std::swap(theta, theta_alt);
+            if (A.fista) {
+                // theta holds x^(t); the residual metric is of x^(t)
+                if (metric) { launch_residual_norm<T>(theta, A.y, A.bits, g, partials, resid_slot, s); nk += 2; }
+                if (!last) {
+                    launch_fista_momentum<T>(theta, xprev, theta_alt, N, beta[(size_t)t], s);
+                    std::swap(theta, theta_alt);
+                    launch_residual_field<T>(theta, u, A.y, A.bits, rinv, g, r, s);
+                    nk += 2;
+                }
+                continue;
+            }
             if (!last) { launch_residual_field<T>(theta, u, A.y, A.bits, rinv, g, r, s); ++nk; }
             if (metric) { launch_residual_norm<T>(theta, A.y, A.bits, g, partials, resid_slot, s); nk += 2; }
             continue;
@@ -239,8 +271,8 @@ int enqueue_solve(const SolveArgs& A, cudaStream_t s) {
         oa.y = A.y;
         oa.bits = A.bits;
         oa.rinv = rinv;
-        oa.r_next = last ? nullptr : r;
-        oa.x_out = (last && f32) ? A.x_out : nullptr;
+        oa.r_next = (last || A.fista) ? nullptr : r;
+        oa.x_out = (last && f32 && !A.fista) ? A.x_out : nullptr;
         oa.resid_partials = metric ? partials : nullptr;
         if (last && !f32 && A.x_out != nullptr && A.admm) {
             // x = xt - u_old: stage u_old in FP32 through x_out before the output overwrites u
@@ -249,8 +281,17 @@ int enqueue_solve(const SolveArgs& A, cudaStream_t s) {
         }
         launch_fgp_out<T>(oa, xt, P[cur], g, lam, theta, u, s);
         ++nk;
-        if (last && !f32 && A.x_out != nullptr) { launch_xt_minus(xt, A.prm.storage, A.x_out, N, A.admm, s); ++nk; }
+        if (last && !f32 && A.x_out != nullptr && !A.fista) {
+            launch_xt_minus(xt, A.prm.storage, A.x_out, N, A.admm, s);
+            ++nk;
+        }
         if (metric) { launch_sum_partials(partials, nparts, resid_slot, s); ++nk; }
+        if (A.fista && !last) {
+            launch_fista_momentum<T>(theta, xprev, theta_alt, N, beta[(size_t)t], s);
+            std::swap(theta, theta_alt);
+            launch_residual_field<T>(theta, u, A.y, A.bits, rinv, g, r, s);
+            nk += 2;
+        }
     }
     if (!f32) {
         launch_cast<T, float>(theta, A.theta, N, s);
@@ -259,7 +300,7 @@ int enqueue_solve(const SolveArgs& A, cudaStream_t s) {
     } else if (theta != theta_home) {
         cudaMemcpyAsync(theta_home, theta, (size_t)N * sizeof(T), cudaMemcpyDeviceToDevice, s);
     }
-    if (T_outer == 0 && A.x_out != nullptr)
+    if ((T_outer == 0 || A.fista) && A.x_out != nullptr)  // FISTA's estimate is x^(T), held in theta
         cudaMemcpyAsync(A.x_out, A.theta, (size_t)N * 4, cudaMemcpyDeviceToDevice, s);
     return nk;
 }
@@ -287,7 +328,7 @@ constexpr size_t kMaxGraphs = 16;
 cudaStream_t g_capture_stream[64] = {};
 
 bool same_args(const SolveArgs& a, const SolveArgs& b) {
-    return a.admm == b.admm && a.y == b.y && a.bits == b.bits && a.nx == b.nx && a.ny == b.ny &&
+    return a.admm == b.admm && a.fista == b.fista && a.y == b.y && a.bits == b.bits && a.nx == b.nx && a.ny == b.ny &&
            a.B == b.B && std::memcmp(&a.prm, &b.prm, sizeof(sci_params)) == 0 && a.theta == b.theta &&
            a.u == b.u && a.x_out == b.x_out && a.resid == b.resid && a.resid_every == b.resid_every &&
            a.work == b.work;
@@ -343,7 +384,7 @@ sci_status run_solve(const SolveArgs& A, cudaStream_t stream) {
 sci_status solve_common(bool admm, const float* y, const uint32_t* bits, int nx, int ny, int B,
                         const sci_params* params, float* theta, float* u, float* x_out,
                         double* resid, int resid_every, void* work, size_t work_bytes,
-                        sci_stream_t stream) {
+                        sci_stream_t stream, bool fista = false) {
     if (y == nullptr || bits == nullptr || theta == nullptr || (admm && u == nullptr)) return SCI_ERR_ARG;
     if (!sizes_ok(nx, ny, B)) return SCI_ERR_ARG;
     if (B > 32) return SCI_ERR_SHAPE;
@@ -353,7 +394,7 @@ sci_status solve_common(bool admm, const float* y, const uint32_t* bits, int nx,
     const Layout L = solver_layout(nx, ny, B, params->storage, admm);
     st = validate_work(work, work_bytes, L.total);
     if (st != SCI_OK) return st;
-    SolveArgs A{admm, y, bits, nx, ny, B, *params, theta, u, x_out, resid, resid_every, work};
+    SolveArgs A{admm, fista, y, bits, nx, ny, B, *params, theta, u, x_out, resid, resid_every, work};
     return run_solve(A, (cudaStream_t)stream);
 }
 
@@ -492,6 +533,13 @@ sci_status sci_admm_tv(const float* y, const uint32_t* bits, int nx, int ny, int
                        size_t work_bytes, sci_stream_t stream) {
     return solve_common(true, y, bits, nx, ny, B, params, theta, u, x_out, resid, resid_every, work,
                         work_bytes, stream);
+}
+
+sci_status sci_fista_tv(const float* y, const uint32_t* bits, int nx, int ny, int B, const sci_params* params,
+                        float* theta, float* x_out, double* resid, int resid_every, void* work,
+                        size_t work_bytes, sci_stream_t stream) {
+    return solve_common(false, y, bits, nx, ny, B, params, theta, nullptr, x_out, resid, resid_every, work,
+                        work_bytes, stream, true);
 }
 
 void sci_graph_cache_clear(void) {

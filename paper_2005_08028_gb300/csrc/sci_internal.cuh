@@ -11,6 +11,11 @@ void launch_forward(const float* x, const uint32_t* bits, Geo g, float* y, cudaS
 template <typename T>
 void launch_adjoint(const float* y, const uint32_t* bits, Geo g, T* x, cudaStream_t s);
 void launch_rinv(const uint32_t* bits, Geo g, float rho, float* rinv, cudaStream_t s);
+// FISTA (Sec. 2.2): rinv = 1/L in every pixel, L = max mask count (lmax: one
+// device word of scratch); theta_next = x + beta (x - x_prev), x_prev = x.
+void launch_fista_step(const uint32_t* bits, Geo g, unsigned* lmax, float* rinv, cudaStream_t s);
+template <typename T>
+void launch_fista_momentum(const T* x, T* x_prev, T* theta_next, long long n, float beta, cudaStream_t s);
 template <typename T>
 void launch_residual_field(const T* theta, const T* u, const float* y, const uint32_t* bits,
                            const float* rinv, Geo g, float* r, cudaStream_t s);

@@ -8,6 +8,8 @@
 // Every kernel here gives one thread one pixel (i, j) and loops over the B
 // frames, so the frame sum of a pixel stays in registers.  A warp covers 32
 // consecutive columns: each frame load is one coalesced 128-byte line.
+#include <algorithm>
+
 #include "sci_internal.cuh"
 
 namespace sci {
@@ -60,6 +62,39 @@ __global__ void k_rinv(const uint32_t* __restrict__ bits, Geo g, float rho, floa
     const uint32_t mask = g.B >= 32 ? 0xffffffffu : ((1u << g.B) - 1u);
     const double R = (double)__popc(bits[pix] & mask) + (double)rho;
     rinv[pix] = R == 0.0 ? 0.f : (float)(1.0 / R);
+}
+
+// FISTA's step (Sec. 2.2): 1/L with L = ||Phi||^2 = max_ij R_ij.  k_mask_max
+// takes the largest mask count into *lmax (zeroed by the caller); k_fill_step
+// writes 1/L (0 when no pixel is measured) in every pixel of the field the
+// GAP residual kernels scale by, so they form z = theta + (1/L) Phi^T (y - Phi theta).
+__global__ void k_mask_max(const uint32_t* __restrict__ bits, Geo g, unsigned* __restrict__ lmax) {
+    const uint32_t mask = g.B >= 32 ? 0xffffffffu : ((1u << g.B) - 1u);
+    unsigned m = 0;
+    for (long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x; pix < g.n;
+         pix += (long long)gridDim.x * blockDim.x)
+        m = max(m, (unsigned)__popc(bits[pix] & mask));
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0) atomicMax(lmax, m);
+}
+
+__global__ void k_fill_step(const unsigned* __restrict__ lmax, Geo g, float* __restrict__ rinv) {
+    const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= g.n) return;
+    const unsigned L = *lmax;
+    rinv[pix] = L == 0 ? 0.f : (float)(1.0 / (double)L);
+}
+
+// FISTA momentum: theta_next = x + beta (x - x_prev), then x_prev = x.
+template <typename T>
+__global__ void k_fista_momentum(const T* __restrict__ x, T* __restrict__ x_prev, T* __restrict__ theta_next,
+                                 long long n, float beta) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float xv = ld<T>(x, i), xp = ld<T>(x_prev, i);
+        st<T>(theta_next, i, fmaf(beta, xv - xp, xv));
+        st<T>(x_prev, i, xv);
+    }
 }
 
 // r = rinv * (y - sum_k c_k (theta_k - u_k)); u may be null.
@@ -191,6 +226,26 @@ void launch_rinv(const uint32_t* bits, Geo g, float rho, float* rinv, cudaStream
     const long long blocks = (g.n + threads - 1) / threads;
     k_rinv<<<(unsigned)blocks, threads, 0, s>>>(bits, g, rho, rinv);
 }
+
+void launch_fista_step(const uint32_t* bits, Geo g, unsigned* lmax, float* rinv, cudaStream_t s) {
+    const int threads = 256;
+    const long long blocks = (g.n + threads - 1) / threads;
+    cudaMemsetAsync(lmax, 0, sizeof(unsigned), s);
+    k_mask_max<<<(unsigned)std::min<long long>(blocks, 152 * 8), threads, 0, s>>>(bits, g, lmax);
+    k_fill_step<<<(unsigned)blocks, threads, 0, s>>>(lmax, g, rinv);
+}
+
+template <typename T>
+void launch_fista_momentum(const T* x, T* x_prev, T* theta_next, long long n, float beta, cudaStream_t s) {
+    const int threads = 256;
+    long long blocks = (n + threads - 1) / threads;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_fista_momentum<T><<<(unsigned)std::max(blocks, 1LL), threads, 0, s>>>(x, x_prev, theta_next, n, beta);
+}
+template void launch_fista_momentum<float>(const float*, float*, float*, long long, float, cudaStream_t);
+template void launch_fista_momentum<__nv_bfloat16>(const __nv_bfloat16*, __nv_bfloat16*, __nv_bfloat16*, long long,
+                                                   float, cudaStream_t);
+template void launch_fista_momentum<__half>(const __half*, __half*, __half*, long long, float, cudaStream_t);
 
 template <typename T>
 void launch_residual_field(const T* theta, const T* u, const float* y, const uint32_t* bits,

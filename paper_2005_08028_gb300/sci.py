@@ -14,7 +14,7 @@ import torch
 
 __all__ = [
     "SciError", "TV", "DTYPE", "DUAL", "load", "sci_masks_pack", "sci_forward", "sci_adjoint",
-    "sci_project", "sci_tv_prox", "sci_gap_tv", "sci_admm_tv", "sci_sqdiff_f64",
+    "sci_project", "sci_tv_prox", "sci_gap_tv", "sci_admm_tv", "sci_fista_tv", "sci_sqdiff_f64",
     "sci_residual_f64", "sci_graph_cache_clear", "sci_tv_prox_noalloc", "sci_last_solve_launches", "sci_fused_updates", "Batch", "SciProblem",
     "sci_gap_tv_batched", "sci_last_batch_launches",
     "sci_conv3d_c32_bf16", "LearnedProx", "sci_gap_tv_lprox", "Workspace", "SciParams",
@@ -60,6 +60,7 @@ _SIGS = {
     "sci_tv_prox_cham": (_i, [_vp, _i, _i, _i, _i, _f, _i, _vp, _vp, _sz, _vp]),
     "sci_solver_workspace": (_sz, [_i, _i, _i, C.POINTER(SciParams)]),
     "sci_gap_tv": (_i, [_vp, _vp, _i, _i, _i, C.POINTER(SciParams), _vp, _vp, _vp, _i, _vp, _sz, _vp]),
+    "sci_fista_tv": (_i, [_vp, _vp, _i, _i, _i, C.POINTER(SciParams), _vp, _vp, _vp, _i, _vp, _sz, _vp]),
     "sci_admm_tv": (_i, [_vp, _vp, _i, _i, _i, C.POINTER(SciParams), _vp, _vp, _vp, _vp, _i, _vp, _sz,
                          _vp]),
     "sci_graph_cache_clear": (None, []),
@@ -228,7 +229,7 @@ def _params(tv, lam, rho, outer, inner, storage, fuse_k, init, use_graph, dual="
                      int(fuse_k), int(init), int(use_graph), DUAL[dual])
 
 
-def _solve(admm: bool, y, bits, B, tv, lam, outer, inner, rho=0.0, storage="f32", theta=None, u=None,
+def _solve(admm: bool, y, bits, B, tv, lam, outer, inner, rho=0.0, storage="f32", theta=None, u=None, fista=False,
            init=None, x_out=None, resid=None, resid_every=0, fuse_k=0, use_graph=True, work=None, dual="fgp"):
     _need_cuda(y, bits, theta, u, x_out, resid)
     nx, ny = y.shape
@@ -255,9 +256,10 @@ def _solve(admm: bool, y, bits, B, tv, lam, outer, inner, rho=0.0, storage="f32"
                              _stream(dev))
         _check("sci_admm_tv", st)
         return x_out, theta, u, resid
-    st = lib.sci_gap_tv(_ptr(y), _ptr(bits), nx, ny, B, C.byref(prm), _ptr(theta), _ptr(x_out),
-                        _ptr(resid), int(resid_every), _ptr(wbuf), wbuf.numel(), _stream(dev))
-    _check("sci_gap_tv", st)
+    name = "sci_fista_tv" if fista else "sci_gap_tv"
+    st = getattr(lib, name)(_ptr(y), _ptr(bits), nx, ny, B, C.byref(prm), _ptr(theta), _ptr(x_out),
+                            _ptr(resid), int(resid_every), _ptr(wbuf), wbuf.numel(), _stream(dev))
+    _check(name, st)
     return x_out, theta, resid
 
 
@@ -272,6 +274,12 @@ def sci_gap_tv(y, bits, B, tv, lam, outer, inner, **kw):
     the library replay its cached CUDA graph.
     """
     return _solve(False, y, bits, B, tv, lam, outer, inner, **kw)
+
+
+def sci_fista_tv(y, bits, B, tv, lam, outer, inner, **kw):
+    """FISTA-TV (Sec. 2.2; L = max R, same lambda as GAP).  Returns (x^(T), x^(T), resid-or-None);
+    keyword arguments as sci_gap_tv."""
+    return _solve(False, y, bits, B, tv, lam, outer, inner, fista=True, **kw)
 
 
 def sci_admm_tv(y, bits, B, tv, lam, rho, outer, inner, **kw):
