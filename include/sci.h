@@ -140,7 +140,7 @@ sci_status sci_tv_prox_cham(const float* x, int nx, int ny, int B, int tv, float
                             int inner_iters, float* theta, void* work, size_t work_bytes,
                             sci_stream_t stream);
 
-/* Bytes of scratch sci_gap_tv / sci_admm_tv need for these sizes and params. */
+/* Bytes of scratch sci_gap_tv / sci_admm_tv / sci_fista_tv need for these sizes and params. */
 size_t sci_solver_workspace(int nx, int ny, int B, const sci_params* params);
 
 /*
