@@ -76,3 +76,33 @@ def test_fista_residual_history(pkg):
         xt, _, _ = pkg.sci_fista_tv(to_dev(y), bits, 6, "itv2d", 0.05, t, 5)
         ref = O.residual_sq(xt.cpu().numpy().astype(np.float64), y.astype(np.float32), case.masks)
         assert abs(got[t - 1] - ref) <= 1e-6 * ref, (t, got[t - 1], ref)
+
+
+def test_graph_cache_keeps_solvers_apart(pkg):
+    """The library replays a cached CUDA graph when a solve's arguments repeat.
+    GAP-FGP, FISTA-FGP and GAP-Chambolle on the same buffers and workspace
+    must each give what a fresh call gives, also when interleaved."""
+    case, y = make_problem(60, 70, 8, 41, sigma=0.01)
+    bits = pkg.sci_masks_pack(to_dev(case.masks))
+    yd = to_dev(y)
+    th = torch.empty((8, 60, 70), device=yd.device)
+    xo = torch.empty_like(th)
+    work = pkg.Workspace(yd.device)
+    runs = [("gap", "fgp"), ("fista", "fgp"), ("gap", "cham"), ("gap", "fgp"), ("fista", "fgp")]
+    fresh = {}
+    for algo, dual in set(runs):
+        f = pkg.sci_fista_tv if algo == "fista" else pkg.sci_gap_tv
+        x, _, _ = f(yd, bits, 8, "vtv", 0.05, 5, 6, dual=dual, use_graph=False)
+        fresh[(algo, dual)] = x.cpu().numpy()
+    for algo, dual in runs:
+        f = pkg.sci_fista_tv if algo == "fista" else pkg.sci_gap_tv
+        f(yd, bits, 8, "vtv", 0.05, 5, 6, dual=dual, theta=th, x_out=xo, init=True, work=work)
+        np.testing.assert_array_equal(xo.cpu().numpy(), fresh[(algo, dual)], err_msg=f"{algo}/{dual}")
+
+
+def test_fista_zero_iterations_returns_the_start(pkg):
+    case, y = make_problem(20, 30, 4, 43)
+    bits = pkg.sci_masks_pack(to_dev(case.masks))
+    x, th, _ = pkg.sci_fista_tv(to_dev(y), bits, 4, "atv", 0.05, 0, 5)
+    ref = O.adjoint(y.astype(np.float32).astype(np.float64), case.masks)
+    assert maxabs(x, ref) <= 1e-6 and maxabs(th, ref) <= 1e-6
