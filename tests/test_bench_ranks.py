@@ -74,3 +74,22 @@ def test_reference_arm_runs_on_rank_0_only():
                           "--warmup", "0"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
     assert out.returncode == 0
     assert out.stdout.strip() == ""  # rank 1 prints nothing and does no work
+
+
+def test_reference_arm_prints_one_contract_line():
+    """Alone (rank 0), the reference arm times the FP64 oracle on a bounded
+    sample of the same workload and prints one JSON line carrying the
+    benchmark's keys, with no host-device traffic in its e2e record."""
+    import json
+
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "voxel-iters/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["steps"] == 1 and d["n_gpus"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
