@@ -328,7 +328,7 @@ ALU_OPS_PER_UPDATE = 20  # FP32 operations per voxel per FGP dual update (FMA = 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per k_fgp_fused
 # launch of the roofline case below (one prox launch on 10 x 512 x 512 FP32,
 # default updates per launch), from one ncu capture of the current kernel
-# (profiles/k_fgp_fused_sci512x512x10.md).  The launch must move at least the
+# (its summary is kept under profiles/).  The launch must move at least the
 # 10.49 MB input; its 10.49 MB output stays in L2.
 NCU_DRAM_BYTES_PER_LAUNCH = {"atv": 14286848, "itv2d": 11173888, "vtv": 10554368}
 

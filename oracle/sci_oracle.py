@@ -16,7 +16,7 @@ Arrays are ``[B][nx][ny]`` float64: frame k, row i (vertical, D_v), column j
 (horizontal, D_h).  Masks are dense arrays of the same shape (any real values;
 the synthetic workloads use binary ones).
 
-Readings where the paper is silent or garbled (each is listed in the design doc):
+Readings where the paper is silent or garbled:
   * D_h, D_v are forward differences without wrap-around (Eq. 7 gives
     n-1 rows); duals are padded to full size with zeros in the last column
     (h) / last row (v).
