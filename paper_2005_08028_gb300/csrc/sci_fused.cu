@@ -297,9 +297,10 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
 
     const float lam = a.lambda, step = a.step;
     // Two updates per loop trip let the compiler alternate registers instead
-    // of copying the loop-carried duals (measured: VTV -6%, ITV2D -3%; the
-    // one-frame ATV tile, whose register file is fuller, gains nothing).
-    constexpr int kUnroll = (TV == SCI_TV_ATV && F == 1) ? 1 : 2;
+    // of copying the loop-carried duals (measured: VTV tiles of up to 10
+    // frames -6%, ITV2D -3%).  The one-frame ATV tile gains nothing, and the
+    // 16- and 24-frame VTV tiles, already near the register limit, lose.
+    constexpr int kUnroll = ((TV == SCI_TV_ATV && F == 1) || F > 10) ? 1 : 2;
 #pragma unroll kUnroll
     for (int s = 0; s < a.K; ++s) {
         // rows whose p stays exact after this update: [1 + s, EH - 1 - s);
