@@ -94,3 +94,37 @@ def test_workspace_sizes_scale(lib):
     assert a >= 7 * N * 4  # xt + three 2-field dual buffers
     assert b >= 9 * N * 2  # plus theta and u copies in 16-bit
     assert lib.sci_tv_prox_workspace(64, 64, 4, 0) >= 6 * 64 * 64 * 4 * 4
+
+
+def _header_struct_fields(name):
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + r"\s*;", src).group(1)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        parts = [p.strip() for p in decl.split(",")]
+        ctype, first = parts[0].rsplit(None, 1)
+        ctype = ctype.replace(" ", "")
+        for name in [first] + parts[1:]:  # declarators sharing one base type
+            stars = len(name) - len(name.lstrip("*"))
+            fields.append((ctype + "*" * stars, name.lstrip("*")))
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("sci_params", "SciParams"), ("sci_problem", "SciProblem")])
+def test_binding_structs_mirror_the_header(cname, pyname):
+    """The ctypes mirrors of the ABI structs have the header's fields, in its
+    order, with matching widths (the binding renames lambda to lam only)."""
+    import paper_2005_08028_gb300.sci as s
+    width = {"int": C.c_int, "float": C.c_float}
+    header = _header_struct_fields(cname)
+    mirror = getattr(s, pyname)._fields_
+    assert len(header) == len(mirror)
+    for (ctype, cfield), (pfield, ptype) in zip(header, mirror):
+        assert pfield == {"lambda": "lam"}.get(cfield, cfield)
+        if ctype in width:
+            assert ptype is width[ctype], (cfield, ctype, ptype)
+        else:  # pointers
+            assert C.sizeof(ptype) == C.sizeof(C.c_void_p), (cfield, ctype)
