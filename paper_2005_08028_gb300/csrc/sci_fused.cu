@@ -560,16 +560,18 @@ constexpr int type_slot(int tv, int cfg) {
 
 template <typename T, int TV>
 bool launch_tv(const FusedArgs& a, const FusedBufs<T>& b, cudaStream_t s) {
-    if (TV != SCI_TV_VTV) {
+    // if constexpr: each TV form instantiates only the tiles it can launch
+    if constexpr (TV != SCI_TV_VTV) {
         if (a.halo <= 8 && (long long)a.g.nx * a.g.ny < 192LL * 192)
             return launch_cfg<T, TV, CfgF1s>(type_slot<T>(TV, 1), a, b, s);
         return launch_cfg<T, TV, CfgF1>(type_slot<T>(TV, 0), a, b, s);
+    } else {
+        if (a.g.B <= 8) return launch_cfg<T, TV, CfgV8>(type_slot<T>(TV, 2), a, b, s);
+        if (a.g.B <= 10) return launch_cfg<T, TV, CfgV10>(type_slot<T>(TV, 3), a, b, s);
+        if (a.g.B <= 16) return launch_cfg<T, TV, CfgV16>(type_slot<T>(TV, 4), a, b, s);
+        if (a.g.B <= 24) return launch_cfg<T, TV, CfgV24>(type_slot<T>(TV, 5), a, b, s);
+        return false;
     }
-    if (a.g.B <= 8) return launch_cfg<T, TV, CfgV8>(type_slot<T>(TV, 2), a, b, s);
-    if (a.g.B <= 10) return launch_cfg<T, TV, CfgV10>(type_slot<T>(TV, 3), a, b, s);
-    if (a.g.B <= 16) return launch_cfg<T, TV, CfgV16>(type_slot<T>(TV, 4), a, b, s);
-    if (a.g.B <= 24) return launch_cfg<T, TV, CfgV24>(type_slot<T>(TV, 5), a, b, s);
-    return false;
 }
 
 template <class Cfg>
@@ -643,18 +645,21 @@ bool launch_batched_cfg(int slot, const FusedArgs& a, const BatchItem<T>* items,
 template <typename T, int TV>
 bool launch_batched_tv(int cls, const FusedArgs& a, const BatchItem<T>* items, int nitems, int total, int tpar,
                        int spar, int want_x, cudaStream_t s) {
-    if (TV != SCI_TV_VTV) return launch_batched_cfg<T, TV, CfgF1>(type_slot<T>(TV, 0), a, items, nitems, total,
-                                                                  tpar, spar, want_x, s);
-    switch (cls) {
-        case 8: return launch_batched_cfg<T, TV, CfgV8>(type_slot<T>(TV, 2), a, items, nitems, total, tpar, spar,
-                                                        want_x, s);
-        case 10: return launch_batched_cfg<T, TV, CfgV10>(type_slot<T>(TV, 3), a, items, nitems, total, tpar,
-                                                          spar, want_x, s);
-        case 16: return launch_batched_cfg<T, TV, CfgV16>(type_slot<T>(TV, 4), a, items, nitems, total, tpar,
-                                                          spar, want_x, s);
-        case 24: return launch_batched_cfg<T, TV, CfgV24>(type_slot<T>(TV, 5), a, items, nitems, total, tpar,
-                                                          spar, want_x, s);
-        default: return false;
+    if constexpr (TV != SCI_TV_VTV) {
+        return launch_batched_cfg<T, TV, CfgF1>(type_slot<T>(TV, 0), a, items, nitems, total, tpar, spar, want_x,
+                                                s);
+    } else {
+        switch (cls) {
+            case 8: return launch_batched_cfg<T, TV, CfgV8>(type_slot<T>(TV, 2), a, items, nitems, total, tpar, spar,
+                                                            want_x, s);
+            case 10: return launch_batched_cfg<T, TV, CfgV10>(type_slot<T>(TV, 3), a, items, nitems, total, tpar,
+                                                              spar, want_x, s);
+            case 16: return launch_batched_cfg<T, TV, CfgV16>(type_slot<T>(TV, 4), a, items, nitems, total, tpar,
+                                                              spar, want_x, s);
+            case 24: return launch_batched_cfg<T, TV, CfgV24>(type_slot<T>(TV, 5), a, items, nitems, total, tpar,
+                                                              spar, want_x, s);
+            default: return false;
+        }
     }
 }
 }  // namespace
