@@ -24,6 +24,13 @@
 // No global memory is touched between the updates of one launch.  Where it
 // pays (see the configurations), rows whose results can no longer reach the
 // interior are skipped: the band that matters shrinks by one row per update.
+//
+// This header holds the implementation; sci_fused_f32.cu, sci_fused_f16.cu and
+// sci_fused_bf16.cu each instantiate it for one storage type (SCI_FUSED_STORAGE),
+// so the three compile in parallel.  The f32 unit also defines the tile-class
+// queries (SCI_FUSED_COMMON).
+#pragma once
+
 #include <algorithm>
 #include <atomic>
 #include <type_traits>
@@ -582,6 +589,7 @@ void dims_of(int& EH, int& EW) {
 
 }  // namespace
 
+#ifdef SCI_FUSED_COMMON
 int fused_max_halo(int tv, int B) {
     if (tv != SCI_TV_VTV) return 20;
     if (B <= 10) return 8;
@@ -610,6 +618,7 @@ void fused_class_dims(int cls, int* EH, int* EW) {
     *EH = h;
     *EW = w;
 }
+#endif  // SCI_FUSED_COMMON
 
 namespace {
 std::atomic<unsigned long long> g_battr_done[64];
@@ -684,17 +693,11 @@ bool launch_fgp_fused(int tv, const FusedArgs& a, const FusedBufs<T>& b, cudaStr
     }
 }
 
-#define SCI_INST_B(T)                                                                                 \
-    template bool launch_fgp_fused_batched<T>(int, int, const FusedArgs&, const BatchItem<T>*, int, int, int, \
-                                              int, int, cudaStream_t);
-SCI_INST_B(float)
-SCI_INST_B(__nv_bfloat16)
-SCI_INST_B(__half)
-#undef SCI_INST_B
-
-template bool launch_fgp_fused<float>(int, const FusedArgs&, const FusedBufs<float>&, cudaStream_t);
-template bool launch_fgp_fused<__nv_bfloat16>(int, const FusedArgs&, const FusedBufs<__nv_bfloat16>&,
-                                              cudaStream_t);
-template bool launch_fgp_fused<__half>(int, const FusedArgs&, const FusedBufs<__half>&, cudaStream_t);
+// The including translation unit names the storage type to instantiate.
+template bool launch_fgp_fused_batched<SCI_FUSED_STORAGE>(int, int, const FusedArgs&,
+                                                          const BatchItem<SCI_FUSED_STORAGE>*, int, int, int, int,
+                                                          int, cudaStream_t);
+template bool launch_fgp_fused<SCI_FUSED_STORAGE>(int, const FusedArgs&, const FusedBufs<SCI_FUSED_STORAGE>&,
+                                                  cudaStream_t);
 
 }  // namespace sci

@@ -80,7 +80,7 @@ void launch_fgp_out(const OutArgs& a, const T* xt, const T* p, Geo g, float lamb
 void launch_sum_partials(const double* partials, int count, double* out, cudaStream_t s);
 int out_partial_count(Geo g);
 
-// ---- temporally blocked FGP (sci_fused.cu) ----
+// ---- temporally blocked FGP (sci_fused.cuh, instantiated by sci_fused_{f32,f16,bf16}.cu) ----
 constexpr int kMaxFuse = 32;  // dual updates per fused launch
 struct FusedArgs {
     Geo g;
