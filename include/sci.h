@@ -311,6 +311,43 @@ long long sci_last_solve_launches(void);
  * one-launch-per-update kernels serve; -1: invalid arguments). */
 int sci_fused_updates(int tv, int B, int inner_iters, int fuse_k);
 
+/* Outer loop that sci_tune_fuse times. */
+typedef enum { SCI_ALGO_GAP = 0, SCI_ALGO_ADMM = 1, SCI_ALGO_FISTA = 2 } sci_algo;
+
+/*
+ * Fuse-depth autotuner (no counterpart in the paper; it picks the launch
+ * shape of its FGP box).  For each of the n_candidates values k in
+ * `candidates` (HOST array, each >= -1, as params->fuse_k), runs a solve of
+ * probe_iters outer iterations (sci_gap_tv, sci_admm_tv or sci_fista_tv by
+ * algo; params->init = 1 and use_graph = 0 are forced) once untimed, then
+ * `reps` times, each bracketed by CUDA events recorded on `stream`, and
+ * writes the median milliseconds per solve to ms[i] (HOST float array of
+ * n_candidates).  *best (HOST int) receives the first candidate with the
+ * smallest median.  With FP32 storage every fuse depth gives bit-identical
+ * results, so the choice only changes speed; with 16-bit storage the duals
+ * carried from one fused launch to the next are rounded to 16 bits, so the
+ * depth moves those roundings.  The other arguments are those of the timed
+ * solver (u: ADMM only, else ignored); theta (and u) are overwritten with
+ * the probe solve's output.  Blocks the calling thread (it synchronises on
+ * the events); SCI_ERR_ARG while `stream` is capturing, for
+ * 1 <= n_candidates <= 64, 1 <= reps <= 100, 1 <= probe_iters <= 1000 not
+ * met, or a NULL host pointer; the timed solver's errors otherwise.
+ */
+sci_status sci_tune_fuse(int algo, const float* y, const uint32_t* bits, int nx, int ny, int B,
+                         const sci_params* params, float* theta, float* u, void* work,
+                         size_t work_bytes, const int* candidates, int n_candidates,
+                         int probe_iters, int reps, float* ms, int* best, sci_stream_t stream);
+
+/*
+ * The same for sci_gap_tv_batched: one K for every tile class of the batch
+ * (k <= 0 selects the library's default there).  Each problem's theta and
+ * x_out are overwritten.  Same limits and errors as sci_tune_fuse.
+ */
+sci_status sci_tune_fuse_batched(const sci_problem* problems, int count, const sci_params* params,
+                                 void* work, size_t work_bytes, const int* candidates,
+                                 int n_candidates, int probe_iters, int reps, float* ms, int* best,
+                                 sci_stream_t stream);
+
 /* Scratch for the FP64 reductions below: at least this many bytes. */
 size_t sci_reduce_workspace(void);
 

@@ -16,7 +16,7 @@ __all__ = [
     "SciError", "TV", "DTYPE", "DUAL", "load", "sci_masks_pack", "sci_forward", "sci_adjoint",
     "sci_project", "sci_tv_prox", "sci_gap_tv", "sci_admm_tv", "sci_fista_tv", "sci_sqdiff_f64",
     "sci_residual_f64", "sci_graph_cache_clear", "sci_tv_prox_noalloc", "sci_last_solve_launches", "sci_fused_updates", "Batch", "SciProblem",
-    "sci_gap_tv_batched", "sci_last_batch_launches",
+    "sci_gap_tv_batched", "sci_last_batch_launches", "ALGO", "sci_tune_fuse", "sci_tune_fuse_batched",
     "sci_conv3d_c32_bf16", "LearnedProx", "sci_gap_tv_lprox", "Workspace", "SciParams",
 ]
 
@@ -71,6 +71,10 @@ _SIGS = {
     "sci_tv_prox_noalloc_max_voxels": (C.c_longlong, []),
     "sci_last_solve_launches": (C.c_longlong, []),
     "sci_fused_updates": (_i, [_i, _i, _i, _i]),
+    "sci_tune_fuse": (_i, [_i, _vp, _vp, _i, _i, _i, C.POINTER(SciParams), _vp, _vp, _vp, _sz,
+                           C.POINTER(_i), _i, _i, _i, C.POINTER(_f), C.POINTER(_i), _vp]),
+    "sci_tune_fuse_batched": (_i, [C.POINTER(SciProblem), _i, C.POINTER(SciParams), _vp, _sz,
+                                   C.POINTER(_i), _i, _i, _i, C.POINTER(_f), C.POINTER(_i), _vp]),
     "sci_gap_tv_batched_workspace": (_sz, [C.POINTER(SciProblem), _i, C.POINTER(SciParams)]),
     "sci_gap_tv_batched": (_i, [C.POINTER(SciProblem), _i, C.POINTER(SciParams), _vp, _sz, _vp]),
     "sci_last_batch_launches": (C.c_longlong, []),
@@ -244,6 +248,10 @@ def _solve(admm: bool, y, bits, B, tv, lam, outer, inner, rho=0.0, storage="f32"
         u = torch.empty((B, nx, ny), dtype=torch.float32, device=dev)
     if x_out is None:
         x_out = torch.empty((B, nx, ny), dtype=torch.float32, device=dev)
+    if fuse_k == "tuned":
+        from . import tune
+        fuse_k = tune.tuned_fuse("admm" if admm else ("fista" if fista else "gap"), y, bits, B, tv, lam, inner,
+                                 rho=rho, storage=storage, dual=dual)
     prm = _params(tv, lam, rho, outer, inner, storage, fuse_k, init, use_graph, dual)
     lib = load()
     need = lib.sci_solver_workspace(nx, ny, B, C.byref(prm))
@@ -268,7 +276,8 @@ def sci_gap_tv(y, bits, B, tv, lam, outer, inner, **kw):
 
     Keyword arguments: storage ('f32'|'bf16'|'f16'); theta (state buffer,
     updated in place: resumed from unless init=True; default a new buffer
-    started at Phi^T y); init; x_out; resid; resid_every; fuse_k; use_graph;
+    started at Phi^T y); init; x_out; resid; resid_every; fuse_k (an int, or
+    'tuned' for the autotuner's cached choice); use_graph;
     work (a Workspace reused across calls); dual ('fgp' or 'cham', the
     TVdenoise box of Algorithm 1).  Reusing the same buffers lets
     the library replay its cached CUDA graph.
@@ -314,7 +323,14 @@ class Batch:
 
 def sci_gap_tv_batched(batch: Batch, tv, lam, outer, inner, storage="f32", init=True, fuse_k=0,
                        use_graph=True, dual="fgp"):
-    """GAP-TV on every measurement of `batch` (results in batch.x_outs / batch.thetas)."""
+    """GAP-TV on every measurement of `batch` (results in batch.x_outs / batch.thetas).
+    fuse_k='tuned' takes the depth from the autotuner's cache, timing the batch
+    first on a miss (which overwrites its buffers, so it needs init=True)."""
+    if fuse_k == "tuned":
+        if not init:
+            raise ValueError("fuse_k='tuned' times probe solves in the batch's buffers: it needs init=True")
+        from . import tune
+        fuse_k = tune.tuned_batch_fuse(batch, tv, lam, inner, storage=storage, dual=dual)
     prm = _params(tv, lam, 0.0, outer, inner, storage, fuse_k, init, use_graph, dual)
     lib = load()
     n = len(batch.ys)
@@ -325,6 +341,55 @@ def sci_gap_tv_batched(batch: Batch, tv, lam, outer, inner, storage="f32", init=
     _check("sci_gap_tv_batched", lib.sci_gap_tv_batched(batch.problems, n, C.byref(prm), _ptr(wbuf),
                                                         wbuf.numel(), _stream(batch.device)))
     return batch.x_outs, batch.thetas
+
+
+ALGO = {"gap": 0, "admm": 1, "fista": 2}
+
+
+def _host_candidates(candidates):
+    cands = [int(k) for k in candidates]
+    if not cands:
+        raise ValueError("no fuse-depth candidates")
+    return cands, (C.c_int * len(cands))(*cands), (C.c_float * len(cands))(), C.c_int(0)
+
+
+def sci_tune_fuse(algo, y, bits, B, tv, lam, inner, candidates, rho=0.0, storage="f32", dual="fgp",
+                  probe_iters=2, reps=3, work=None):
+    """Times probe_iters outer iterations of the `algo` solve ('gap', 'admm',
+    'fista') at each fuse depth in `candidates` (sci_tune_fuse, CUDA events on
+    the current stream).  Returns (best candidate, [median ms per candidate]).
+    The probe solves run in buffers of their own."""
+    _need_cuda(y, bits)
+    nx, ny = y.shape
+    dev = y.device
+    theta = torch.empty((B, nx, ny), dtype=torch.float32, device=dev)
+    u = torch.empty_like(theta) if algo == "admm" else None
+    prm = _params(tv, lam, rho, probe_iters, inner, storage, 0, True, False, dual)
+    lib = load()
+    wbuf = (work or Workspace(dev)).get(lib.sci_solver_workspace(nx, ny, B, C.byref(prm)))
+    cands, c_arr, ms, best = _host_candidates(candidates)
+    _check("sci_tune_fuse", lib.sci_tune_fuse(ALGO[algo], _ptr(y), _ptr(bits), nx, ny, int(B), C.byref(prm),
+                                              _ptr(theta), _ptr(u), _ptr(wbuf), wbuf.numel(), c_arr, len(cands),
+                                              int(probe_iters), int(reps), ms, C.byref(best), _stream(dev)))
+    return int(best.value), [float(v) for v in ms]
+
+
+def sci_tune_fuse_batched(batch: Batch, tv, lam, inner, candidates, storage="f32", dual="fgp",
+                          probe_iters=1, reps=3):
+    """sci_tune_fuse for sci_gap_tv_batched on `batch` (one depth for the whole
+    batch; overwrites batch.thetas and batch.x_outs).  Returns (best, [ms])."""
+    prm = _params(tv, lam, 0.0, probe_iters, inner, storage, 0, True, False, dual)
+    lib = load()
+    n = len(batch.ys)
+    need = lib.sci_gap_tv_batched_workspace(batch.problems, n, C.byref(prm))
+    if need == 0:
+        raise SciError("sci_gap_tv_batched_workspace", 1)
+    wbuf = batch.work.get(need)
+    cands, c_arr, ms, best = _host_candidates(candidates)
+    _check("sci_tune_fuse_batched",
+           lib.sci_tune_fuse_batched(batch.problems, n, C.byref(prm), _ptr(wbuf), wbuf.numel(), c_arr, len(cands),
+                                     int(probe_iters), int(reps), ms, C.byref(best), _stream(batch.device)))
+    return int(best.value), [float(v) for v in ms]
 
 
 def sci_conv3d_c32_bf16(act: torch.Tensor, w: torch.Tensor, bias: torch.Tensor | None = None,

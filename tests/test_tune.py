@@ -1,0 +1,162 @@
+"""CPU checks of the fuse-depth autotuner: candidate choice, cache keys, the
+JSON cache file, the cache-hit path (no timing), and the C ABI's argument
+checks, which return before any CUDA call.  Timing itself is covered by
+tests/test_gpu_tune.py."""
+import ctypes as C
+import json
+import os
+import types
+
+import pytest
+import torch
+
+from paper_2005_08028_gb300 import sci as S
+from paper_2005_08028_gb300 import tune
+
+ARG = 1  # SCI_ERR_ARG
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2005_08028_gb300 import build as b
+    return S.load(b.build())
+
+
+class FakeTimer:
+    """Stands in for sci_tune_fuse(_batched): records calls, prefers one depth."""
+
+    def __init__(self, prefer):
+        self.prefer, self.calls = prefer, []
+
+    def __call__(self, *args, **kw):
+        cands = args[7] if len(args) > 7 else args[4]
+        self.calls.append((list(cands), kw))
+        ms = [1.0 if c == self.prefer else 2.0 + i for i, c in enumerate(cands)]
+        return (self.prefer if self.prefer in cands else cands[0]), ms
+
+
+@pytest.mark.parametrize("tv", ["atv", "itv2d", "vtv"])
+@pytest.mark.parametrize("B", [1, 8, 10, 16, 24])
+@pytest.mark.parametrize("inner", [1, 5, 10])
+def test_candidates_are_the_distinct_depths_the_library_runs(lib, tv, B, inner):
+    c = tune.fuse_candidates(tv, B, inner)
+    assert c[0] == S.sci_fused_updates(tv, B, inner, 0)  # the default first: a tie keeps it
+    assert c[-1] == -1 and len(set(c)) == len(c)
+    for k in c[:-1]:
+        assert 1 <= k <= inner and S.sci_fused_updates(tv, B, inner, k) == k
+    # every depth the library can run for fuse_k = 1..inner is offered
+    assert {S.sci_fused_updates(tv, B, inner, k) for k in range(1, inner + 1)} == set(c[:-1])
+
+
+def test_no_fused_kernel_leaves_the_per_update_path_only(lib):
+    assert tune.fuse_candidates("vtv", 32, 10) == [-1]
+    assert tune.fuse_candidates("vtv", 32, 10, per_update=False) == []
+
+
+def test_batch_candidates_give_distinct_per_class_depths(lib):
+    Bs = [8, 8, 10, 24]
+    c = tune.batch_fuse_candidates("vtv", Bs, 10)
+    assert c[0] == 0
+    depths = [tuple(S.sci_fused_updates("vtv", b, 10, k) for b in sorted(set(Bs))) for k in c]
+    assert len(set(depths)) == len(depths)
+    every = {tuple(S.sci_fused_updates("vtv", b, 10, k) for b in sorted(set(Bs))) for k in range(0, 11)}
+    assert set(depths) == every
+
+
+def test_batch_key_ignores_order_and_hashes_long_mixes():
+    a = tune.batch_key("g", "vtv", [(64, 64, 8), (128, 96, 10), (64, 64, 8)], 5, "f16", "fgp")
+    b = tune.batch_key("g", "vtv", [(128, 96, 10), (64, 64, 8), (64, 64, 8)], 5, "f16", "fgp")
+    assert a == b and "64x64x8*2" in a
+    assert a != tune.batch_key("g", "vtv", [(64, 64, 8), (128, 96, 10)], 5, "f16", "fgp")
+    long = tune.batch_key("g", "vtv", [(n, n, 8) for n in range(16, 80)], 5, "f16", "fgp")
+    assert "sha1:" in long and len(long) < 120
+
+
+def test_cache_round_trip_and_atomic_file(tmp_path):
+    p = str(tmp_path / "sub" / "fuse.json")
+    c = tune.FuseCache(p)
+    assert len(c) == 0 and c.get("k") is None
+    c.put("k", 5, [6, 5, -1], [0.2, 0.1, 0.9])
+    assert tune.FuseCache(p).get("k") == 5
+    assert json.load(open(p))["k"]["candidates"] == [6, 5, -1]
+    assert sorted(os.listdir(tmp_path / "sub")) == ["fuse.json"]  # no temporary file left
+
+
+def test_unreadable_or_foreign_cache_starts_empty(tmp_path):
+    p = tmp_path / "fuse.json"
+    p.write_text("{not json")
+    assert len(tune.FuseCache(str(p))) == 0
+    p.write_text("[1, 2]")
+    assert len(tune.FuseCache(str(p))) == 0
+    p.write_text(json.dumps({"k": {"fuse_k": "five"}}))
+    assert tune.FuseCache(str(p)).get("k") is None
+
+
+def test_env_var_names_the_cache(monkeypatch, tmp_path):
+    monkeypatch.setenv("SCI_TUNE_CACHE", str(tmp_path / "x.json"))
+    assert tune.default_cache_path() == str(tmp_path / "x.json")
+
+
+def test_tuned_fuse_times_once_then_hits_the_cache(lib, tmp_path):
+    cache = tune.FuseCache(str(tmp_path / "f.json"))
+    y, bits = torch.zeros(40, 56), torch.zeros(40, 56, dtype=torch.int32)
+    t = FakeTimer(prefer=5)
+    k = tune.tuned_fuse("gap", y, bits, 8, "vtv", 0.05, 10, cache=cache, timer=t)
+    assert k == 5 and len(t.calls) == 1
+    assert t.calls[0][0] == tune.fuse_candidates("vtv", 8, 10)
+    assert tune.tuned_fuse("gap", y, bits, 8, "vtv", 0.05, 10, cache=cache, timer=t) == 5
+    assert len(t.calls) == 1  # cache hit: nothing timed
+    # a fresh cache object reads the stored choice from the file
+    assert tune.tuned_fuse("gap", y, bits, 8, "vtv", 0.05, 10, cache=tune.FuseCache(cache.path), timer=t) == 5
+    assert len(t.calls) == 1
+    # what decides the depth is in the key: another storage type is timed again
+    tune.tuned_fuse("gap", y, bits, 8, "vtv", 0.05, 10, storage="f16", cache=cache, timer=t)
+    tune.tuned_fuse("admm", y, bits, 8, "vtv", 0.05, 10, rho=0.01, cache=cache, timer=t)
+    tune.tuned_fuse("gap", y, bits, 8, "vtv", 0.05, 5, cache=cache, timer=t)
+    assert len(t.calls) == 4 and t.calls[2][1]["rho"] == 0.01
+
+
+def test_a_single_candidate_is_not_timed(lib, tmp_path):
+    cache = tune.FuseCache(str(tmp_path / "f.json"))
+    t = FakeTimer(prefer=3)
+    y = torch.zeros(16, 16)
+    assert tune.tuned_fuse("gap", y, y, 32, "vtv", 0.05, 10, cache=cache, timer=t) == -1
+    assert t.calls == []
+
+
+def test_tuned_batch_fuse_keys_the_size_mix(lib, tmp_path):
+    cache = tune.FuseCache(str(tmp_path / "f.json"))
+    batch = types.SimpleNamespace(ys=[torch.zeros(64, 64), torch.zeros(96, 80)], Bs=[8, 24],
+                                  device=torch.device("cpu"))
+    t = FakeTimer(prefer=4)
+    assert tune.tuned_batch_fuse(batch, "vtv", 0.05, 10, cache=cache, timer=t) == 4
+    assert t.calls[0][0] == tune.batch_fuse_candidates("vtv", [8, 24], 10)
+    batch.ys.reverse(); batch.Bs.reverse()
+    assert tune.tuned_batch_fuse(batch, "vtv", 0.05, 10, cache=cache, timer=t) == 4
+    assert len(t.calls) == 1
+
+
+def test_c_abi_rejects_bad_tuner_arguments_before_any_launch(lib):
+    fake = C.c_void_p(0x10000)  # never dereferenced: validation fails first
+    prm = S.SciParams(0, 0.05, 0.0, 10, 5, 0, 0, 1, 1, 0)
+    cands = (C.c_int * 3)(5, 2, -1)
+    ms = (C.c_float * 3)()
+    best = C.c_int(0)
+
+    def tune_call(algo=0, params=C.byref(prm), c=cands, n=3, probe=2, reps=3, msp=ms, bestp=C.byref(best), u=None):
+        return lib.sci_tune_fuse(algo, fake, fake, 8, 8, 2, params, fake, u, fake, 1 << 30, c, n, probe, reps,
+                                 msp, bestp, None)
+
+    assert tune_call(params=None) == ARG
+    assert tune_call(n=0) == ARG and tune_call(n=65) == ARG
+    assert tune_call(c=(C.c_int * 3)(5, -2, 1)) == ARG
+    assert tune_call(c=None) == ARG and tune_call(msp=None) == ARG and tune_call(bestp=None) == ARG
+    assert tune_call(reps=0) == ARG and tune_call(reps=101) == ARG
+    assert tune_call(probe=0) == ARG and tune_call(probe=1001) == ARG
+    assert tune_call(algo=3) == ARG and tune_call(algo=-1) == ARG
+    assert tune_call(algo=1) == ARG  # ADMM without u
+    probs = (S.SciProblem * 1)()
+    assert lib.sci_tune_fuse_batched(probs, 1, None, fake, 1 << 30, cands, 3, 1, 3, ms, C.byref(best), None) == ARG
+    assert lib.sci_tune_fuse_batched(probs, 1, C.byref(prm), fake, 1 << 30, cands, 0, 1, 3, ms, C.byref(best),
+                                     None) == ARG
+    assert best.value == 0  # untouched on error
