@@ -26,7 +26,12 @@ Readings where the paper is silent or garbled:
   * TVdenoise(x) is the proximal map argmin_t 1/2||t - x||^2 + lam*TV(t): the
     FGP step 1/(8 lam) and t = x - lam*D^T w of Algorithm 1 fix this scale.
   * FGP starts from w = p = 0 and nu = 1 at every TVdenoise call and returns
-    t = x - lam*D^T p after S dual updates (Beck & Teboulle's output).
+    t = x - lam*D^T p after S dual updates (Beck & Teboulle's output).  The
+    dual warm start (``warm_start=True`` on gap_tv / admm_tv) instead keeps
+    the box's w from one call to the next, as Algorithm 1 initialises w once
+    before its outer loop, and still resets nu to 1 inside the box; the FGP
+    box carries its last momentum point w (which may lie outside the dual
+    set), the Chambolle box its w.
   * Loops run exactly T outer and S inner iterations.
   * The Chambolle box of Algorithm 1 is read with its D^T as the divergence
     (minus the adjoint), as in Chambolle's derivation; with the adjoint its
@@ -215,7 +220,7 @@ def fgp_momentum_coeffs(S: int) -> np.ndarray:
 
 
 def fgp_prox(x: np.ndarray, lam: float, S: int, tv: str, *, momentum: bool = True,
-             return_dual: bool = False):
+             return_dual: bool = False, w0=None, return_state: bool = False):
     """S iterations of FGP for argmin_t 1/2||t - x||^2 + lam*TV(t).
 
     Per iteration s (Algorithm 1, ATV-FGP box, with Eqs. 29-32 for ITV2D/VTV):
@@ -225,12 +230,25 @@ def fgp_prox(x: np.ndarray, lam: float, S: int, tv: str, *, momentum: bool = Tru
       w = p_new + ((nu_s - 1)/nu_{s+1}) (p_new - p)
     Output theta = x - lam D^T p after the S dual updates.  ``momentum=False``
     gives the plain gradient-projection method (all coefficients 0).
+
+    w starts at 0, or at ``w0 = (w_h, w_v)`` (the dual warm start: Algorithm 1
+    sets w once before its outer loop and resets only nu inside the box, so
+    nu_0 = 1 still and the first coefficient is 0).  ``return_state=True``
+    returns (theta, (w_h, w_v)) with the box's final w, the state a warm
+    start carries to the next call; ``return_dual=True`` returns
+    (theta, (p_h, p_v)).
     """
+    if return_dual and return_state:
+        raise ValueError("return_dual and return_state are exclusive")
     x = np.asarray(x, dtype=np.float64)
     step = 1.0 / (8.0 * lam)
     coef = fgp_momentum_coeffs(S) if momentum else np.zeros(S)
-    wh = np.zeros_like(x)
-    wv = np.zeros_like(x)
+    if w0 is None:
+        wh = np.zeros_like(x)
+        wv = np.zeros_like(x)
+    else:
+        wh = np.array(w0[0], dtype=np.float64)
+        wv = np.array(w0[1], dtype=np.float64)
     ph = np.zeros_like(x)
     pv = np.zeros_like(x)
     for s in range(S):
@@ -242,6 +260,8 @@ def fgp_prox(x: np.ndarray, lam: float, S: int, tv: str, *, momentum: bool = Tru
         wv = pv_new + coef[s] * (pv_new - pv)
         ph, pv = ph_new, pv_new
     theta = x - lam * div_adj(ph, pv)
+    if return_state:
+        return theta, (wh, wv)
     if return_dual:
         return theta, (ph, pv)
     return theta
@@ -253,7 +273,8 @@ def divergence(wh: np.ndarray, wv: np.ndarray) -> np.ndarray:
     return -div_adj(wh, wv)
 
 
-def cham_prox(x: np.ndarray, lam: float, S: int, tv: str, *, return_dual: bool = False):
+def cham_prox(x: np.ndarray, lam: float, S: int, tv: str, *, return_dual: bool = False, w0=None,
+              return_state: bool = False):
     """S iterations of Chambolle's dual algorithm for argmin_t 1/2||t - x||^2 + lam*TV(t).
 
     Algorithm 1, ATV-Cham box (ITV2D-Cham and the ITV3D dual take the norms
@@ -263,20 +284,28 @@ def cham_prox(x: np.ndarray, lam: float, S: int, tv: str, *, return_dual: bool =
       z_h = D_h z,  z_v = D_v z
       w   = (w + delta t z) / max(1, |w + delta t z|)
       p_d = div w
-    Output theta = x - lam p_d.
+    Output theta = x - lam p_d.  ``w0 = (w_h, w_v)`` starts from that w
+    instead (dual warm start), with p_d = div w0.  ``return_dual`` and
+    ``return_state`` both return (theta, (w_h, w_v)): w is this box's whole
+    state.
     """
     x = np.asarray(x, dtype=np.float64)
     dt = 1.0 / 8.0
-    wh = np.zeros_like(x)
-    wv = np.zeros_like(x)
-    pd = np.zeros_like(x)
+    if w0 is None:
+        wh = np.zeros_like(x)
+        wv = np.zeros_like(x)
+        pd = np.zeros_like(x)
+    else:
+        wh = np.array(w0[0], dtype=np.float64)
+        wv = np.array(w0[1], dtype=np.float64)
+        pd = divergence(wh, wv)
     for _ in range(S):
         z = pd - x / lam
         zh, zv = grad_h(z), grad_v(z)
         wh, wv = dual_project(wh + dt * zh, wv + dt * zv, tv)
         pd = divergence(wh, wv)
     theta = x - lam * pd
-    if return_dual:
+    if return_dual or return_state:
         return theta, (wh, wv)
     return theta
 
@@ -312,36 +341,49 @@ def dual_objective(ph: np.ndarray, pv: np.ndarray, x: np.ndarray, lam: float) ->
 # --------------------------------------------------------------------------
 
 def gap_tv(y: np.ndarray, C: np.ndarray, lam: float, T: int, S: int, tv: str,
-           theta0: np.ndarray | None = None, dual: str = "fgp"):
+           theta0: np.ndarray | None = None, dual: str = "fgp", warm_start: bool = False):
     """GAP-TV (Eqs. 21-22; Algorithm 1): returns (x^(T), theta^(T)).
 
     theta^(0) = Phi^T y unless ``theta0`` is given (resuming).  Each of the T
     iterations projects onto {Phi x = y} and applies the S-step TVdenoise
     (``dual`` = 'fgp' or 'cham': the FGP or the Chambolle box).
+    ``warm_start=True`` carries the box's w from each TVdenoise call to the
+    next (Algorithm 1 initialises w once, before the outer loop); w starts at
+    0 in the first call.
     """
     denoise = _tv_denoise(dual)
     theta = adjoint(y, C) if theta0 is None else np.array(theta0, dtype=np.float64)
     x = theta
+    w = None
     for _ in range(T):
         x = gap_project(theta, y, C)
-        theta = denoise(x, lam, S, tv)
+        if warm_start:
+            theta, w = denoise(x, lam, S, tv, w0=w, return_state=True)
+        else:
+            theta = denoise(x, lam, S, tv)
     return x, theta
 
 
 def admm_tv(y: np.ndarray, C: np.ndarray, lam: float, rho: float, T: int, S: int,
-            tv: str, theta0: np.ndarray | None = None, u0: np.ndarray | None = None, dual: str = "fgp"):
+            tv: str, theta0: np.ndarray | None = None, u0: np.ndarray | None = None, dual: str = "fgp",
+            warm_start: bool = False):
     """ADMM-TV (Eqs. 24-26): returns (x^(T), theta^(T), u^(T)).
 
     theta^(0) = Phi^T y and u^(0) = 0 unless given.  Per iteration:
     x = admm_xupdate(theta, u), theta = TVdenoise(u + x), u = u + x - theta.
+    ``warm_start`` as in gap_tv.
     """
     denoise = _tv_denoise(dual)
     theta = adjoint(y, C) if theta0 is None else np.array(theta0, dtype=np.float64)
     u = np.zeros_like(theta) if u0 is None else np.array(u0, dtype=np.float64)
     x = theta
+    w = None
     for _ in range(T):
         x = admm_xupdate(theta, u, y, C, rho)
-        theta = denoise(u + x, lam, S, tv)
+        if warm_start:
+            theta, w = denoise(u + x, lam, S, tv, w0=w, return_state=True)
+        else:
+            theta = denoise(u + x, lam, S, tv)
         u = u + x - theta
     return x, theta, u
 

@@ -33,10 +33,11 @@ def test_fgp_hand_iterates_golden():
 
 # ---------------------------------------------------------------- SciPy dual solve
 
-def _dual_solve_scipy(x, lam, tv):
+def _dual_solve_scipy(x, lam, tv, return_w=False):
     """min_w 1/2||x - lam D^T w||^2 over the TV's dual unit set, by SciPy.
 
-    Variables are the non-padded dual entries only.  theta* = x - lam D^T w*.
+    Variables are the non-padded dual entries only.  theta* = x - lam D^T w*;
+    return_w=True returns (theta*, (w_h*, w_v*)).
     """
     B, nx, ny = x.shape
     mh = np.zeros((B, nx, ny), bool)
@@ -75,7 +76,8 @@ def _dual_solve_scipy(x, lam, tv):
                                 constraints=[dict(type="ineq", fun=cons)],
                                 options=dict(ftol=1e-15, maxiter=2000))
     wh, wv = unpack(res.x)
-    return x - lam * O.div_adj(wh, wv)
+    theta = x - lam * O.div_adj(wh, wv)
+    return (theta, (wh, wv)) if return_w else theta
 
 
 @pytest.mark.parametrize("tv", O.TV_TYPES)
