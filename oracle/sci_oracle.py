@@ -44,6 +44,11 @@ Readings where the paper is silent or garbled:
     (x^(t) - x^(t-1)) with tau_1 = 1 (the printed update's indices are
     garbled); TVdenoise takes the same lam as GAP (plug-in reading), so its
     fixed points minimise 1/2||y - Phi x||^2 + lam L TV(x).
+  * TwIST (Sec. 2.2): its unit step runs on Phi / sqrt(L); alpha and beta
+    ("determined by the eigenvalues of Phi^T Phi") follow TwIST's own rule
+    with the extreme nonzero eigenvalues of the normalised operator
+    (xim = 1, xi1 = min_{R>0} R / max R); the first iteration is a plain
+    step; TVdenoise takes lam as for FISTA.
 """
 from __future__ import annotations
 
@@ -53,7 +58,9 @@ __all__ = [
     "TV_TYPES", "forward", "adjoint", "mask_energy", "gap_project", "admm_xupdate",
     "grad_h", "grad_v", "grad_h_adj", "grad_v_adj", "div_adj", "tv_value",
     "dual_project", "fgp_momentum_coeffs", "fgp_prox", "divergence", "cham_prox", "prox_objective",
-    "dual_objective", "gap_tv", "admm_tv", "lipschitz", "fista_tv", "psnr", "residual_sq",
+    "dual_objective", "gap_tv", "admm_tv", "lipschitz", "fista_tv", "twist_params", "twist_xi1", "twist_tv",
+    "psnr",
+    "residual_sq",
 ]
 
 TV_TYPES = ("atv", "itv2d", "vtv")
@@ -420,6 +427,70 @@ def fista_tv(y: np.ndarray, C: np.ndarray, lam: float, T: int, S: int, tv: str,
         x_prev = x
         tau = tau_next
     return x, x
+
+
+def twist_params(xi1: float = 1e-4, xim: float = 1.0) -> tuple[float, float]:
+    """TwIST's (alpha, beta) for the eigenvalue bounds xi1 <= eig(A^T A) <= xim
+    of its (normalised) operator A (Sec. 2.2, TwIST steps, citing
+    Bioucas-Dias & Figueiredo 2007, whose rule this is):
+      kappa = xi1 / xim,  rho = (1 - sqrt(kappa)) / (1 + sqrt(kappa)),
+      alpha = 1 + rho^2,  beta = 2 alpha / (xim + xi1).
+    These give the two-step iteration its best worst-case linear rate, rho,
+    over the interval.  kappa = 1 gives alpha = beta = 1 (plain IST)."""
+    if not (0.0 < xi1 <= xim):
+        raise ValueError("need 0 < xi1 <= xim")
+    r = np.sqrt(xi1 / xim)
+    rho = (1.0 - r) / (1.0 + r)
+    alpha = 1.0 + rho * rho
+    return alpha, 2.0 * alpha / (xim + xi1)
+
+
+def twist_xi1(C: np.ndarray) -> float:
+    """Smallest nonzero eigenvalue of A^T A for A = Phi / sqrt(L): the
+    eigenvalues of Phi^T Phi are 0 (its nullspace) and the R_ij, so this is
+    min_{R > 0} R / max R (1 when nothing is measured)."""
+    R = mask_energy(C)
+    pos = R[R > 0]
+    return 1.0 if pos.size == 0 else float(pos.min() / pos.max())
+
+
+def twist_tv(y: np.ndarray, C: np.ndarray, lam: float, T: int, S: int, tv: str,
+             theta0: np.ndarray | None = None, dual: str = "fgp", xi1: float | None = None):
+    """TwIST-TV (Sec. 2.2, TwIST steps): returns (x^(T), theta^(T-1)).
+
+    The printed steps take a unit gradient step, which needs ||Phi|| <= 1;
+    they run here on A = Phi / sqrt(L) and y / sqrt(L) (L = max R, as for
+    FISTA), so the step reads z = x + (1/L) Phi^T (y - Phi x).  alpha and
+    beta come from the eigenvalues of A^T A (twist_params with xim = 1 and
+    xi1 = twist_xi1(C), its smallest nonzero eigenvalue; the nullspace is
+    left to the TV term).  ``xi1`` overrides it (TwIST's authors use 1e-4
+    for ill-conditioned operators, with a monotone safeguard that the
+    printed steps do not have).  x^(0) = Phi^T y
+    unless ``theta0`` is given; the first iteration is one plain step
+    x^(1) = theta^(0) (TwIST starts its two-step recursion from an IST step),
+    then for t >= 1:
+      z^(t)       = x^(t) + (1/L) Phi^T (y - Phi x^(t))
+      theta^(t)   = TVdenoise(z^(t))
+      x^(t+1)     = (1 - alpha) x^(t-1) + (alpha - beta) x^(t) + beta theta^(t)
+    TVdenoise takes lam as for FISTA, so fixed points minimise
+    1/2||y - Phi x||^2 + lam L TV(x).  theta^(T-1) is x^(0) when T = 0.
+    """
+    denoise = _tv_denoise(dual)
+    L = lipschitz(C)
+    step = 0.0 if L == 0.0 else 1.0 / L
+    alpha, beta = twist_params(twist_xi1(C) if xi1 is None else xi1, 1.0)
+    x = adjoint(y, C) if theta0 is None else np.array(theta0, dtype=np.float64)
+    x_prev = x
+    theta = x
+    for t in range(T):
+        z = x + step * adjoint(y - forward(x, C), C)
+        theta = denoise(z, lam, S, tv)
+        if t == 0:
+            x_next = theta
+        else:
+            x_next = (1.0 - alpha) * x_prev + (alpha - beta) * x + beta * theta
+        x_prev, x = x, x_next
+    return x, theta
 
 
 # --------------------------------------------------------------------------
