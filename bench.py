@@ -258,6 +258,9 @@ def run_gpu(args):
     cham = _chambolle(pkg, torch, dev, stream, flush, c, y, bits, x_gt, psnr)
     fista = _fista(pkg, torch, dev, stream, flush, c, y, bits, x_gt, psnr)
 
+    # ---- fuse-depth autotuner on the same measurement (outside every timed region) ----
+    tuning = None if args.no_tune else _fuse_tuning(pkg, c, y, bits)
+
     # ---- precision: GAP-ITV2D on 2048x2048x32 with FP32 / FP16 / BF16 storage ----
     precision = None if args.no_precision else _precision(pkg, torch, dev, stream, flush)
 
@@ -280,6 +283,7 @@ def run_gpu(args):
         "psnr": psnr,
         "chambolle": cham,
         "fista": fista,
+        "fuse_tuning": tuning,
         "batched": batched,
         "precision": precision,
         "learned": learned,
@@ -491,6 +495,24 @@ def _fista(pkg, torch, dev, stream, flush, c, y, bits, x_gt, psnr_gap):
         out[tv] = {"value": N * c["outer"] / (ms * 1e-3), "unit": UNIT, "ms": round(ms, 2),
                    "psnr_db": round(10.0 * np.log10(1.0 / mse), 4),
                    "psnr_gap_db": psnr_gap.get(f"gap_{tv}", {}).get("gpu_db")}
+    return out
+
+
+def _fuse_tuning(pkg, c, y, bits):
+    """sci_tune_fuse on each of the six reconstructions (4 outer iterations per
+    probe, median of 5 CUDA-event timings): per-candidate ms, the chosen
+    depth and the library default.  A failure is reported in the section."""
+    from paper_2005_08028_gb300 import tune
+    out = {"probe": "4 outer iterations, median of 5, ms per probe"}
+    try:
+        for algo, tv in COMBOS:
+            cands = tune.fuse_candidates(tv, c["B"], c["inner"])
+            best, ms = pkg.sci_tune_fuse(algo, y, bits, c["B"], tv, c["lam"], c["inner"], cands,
+                                         rho=c["rho"] if algo == "admm" else 0.0, probe_iters=4, reps=5)
+            out[f"{algo}_{tv}"] = {"best": best, "default": cands[0],
+                                   "ms": {str(k): round(m, 4) for k, m in zip(cands, ms)}}
+    except Exception as e:  # noqa: BLE001 -- the section reports its own failure
+        out["error"] = f"{type(e).__name__}: {e}"
     return out
 
 
@@ -734,6 +756,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-measurement batched solve")
     ap.add_argument("--no-learned", action="store_true", help="skip training and running the learned prox")
+    ap.add_argument("--no-tune", action="store_true", help="skip the fuse-depth autotuner section")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the 2048x2048x32 FP32 / FP16 / BF16 storage solves")
     ap.add_argument("--kernel-case", choices=["fused", "conv", "lprox"], default=None,

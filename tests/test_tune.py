@@ -160,3 +160,28 @@ def test_c_abi_rejects_bad_tuner_arguments_before_any_launch(lib):
     assert lib.sci_tune_fuse_batched(probs, 1, C.byref(prm), fake, 1 << 30, cands, 0, 1, 3, ms, C.byref(best),
                                      None) == ARG
     assert best.value == 0  # untouched on error
+
+
+def test_bench_tuning_section_reports_choices_and_failures(lib):
+    import bench
+    c = {"B": 10, "inner": 10, "lam": 0.05, "rho": 0.01}
+    calls = []
+
+    class Fake:
+        @staticmethod
+        def sci_tune_fuse(algo, y, bits, B, tv, lam, inner, cands, rho=0.0, probe_iters=2, reps=3):
+            calls.append((algo, tv, rho, probe_iters, reps))
+            return cands[0], [1.0 + i for i in range(len(cands))]
+
+    out = bench._fuse_tuning(Fake, c, None, None)
+    assert set(out) == {"probe"} | {f"{a}_{t}" for a, t in bench.COMBOS}
+    assert out["gap_vtv"]["best"] == out["gap_vtv"]["default"] == S.sci_fused_updates("vtv", 10, 10, 0)
+    assert list(out["admm_atv"]["ms"]) == [str(k) for k in tune.fuse_candidates("atv", 10, 10)]
+    assert [r for _, _, r, _, _ in calls] == [0.0] * 3 + [0.01] * 3
+
+    class Broken:
+        @staticmethod
+        def sci_tune_fuse(*a, **k):
+            raise S.SciError("sci_tune_fuse", 3)
+
+    assert "SCI_ERR_CUDA" in bench._fuse_tuning(Broken, c, None, None)["error"]
