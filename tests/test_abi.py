@@ -145,3 +145,51 @@ def test_fuse_depth_planner(lib):
     assert q("vtv", 25, 10) == 0 and q("vtv", 32, 10) == 0
     assert q("atv", 10, 10, -1) == 0 and q("vtv", 10, 10, -1) == 0
     assert q("atv", 10, 10, 3) == 3 and q("vtv", 10, 10, 30) == 7  # clamped to the halo
+
+
+def _problems(sizes, ptr=0x10000):
+    import paper_2005_08028_gb300.sci as s
+    arr = (s.SciProblem * max(1, len(sizes)))()
+    for k, (nx, ny, B) in enumerate(sizes):
+        arr[k] = s.SciProblem(nx, ny, B, ptr, ptr, ptr, None)  # pointers are never dereferenced here
+    return arr
+
+
+def test_batched_workspace_planner(lib):
+    """Host logic, no GPU: the batched solver's workspace holds, per
+    measurement, two pixel fields (R^+, r) and eleven storage-type voxel
+    fields (x-tilde, two theta, eight carried duals), each 256-byte aligned,
+    behind a descriptor table; invalid batches report 0."""
+    import paper_2005_08028_gb300.sci as s
+
+    def ws(sizes, tv=2, storage=0, lam=0.05, fuse_k=0):
+        prm = s.SciParams(tv, lam, 0.0, 10, 5, storage, fuse_k, 1, 1, 0)
+        return lib.sci_gap_tv_batched_workspace(_problems(sizes), len(sizes), C.byref(prm))
+
+    def al(b):
+        return (b + 255) // 256 * 256
+
+    def fields(sizes, es):
+        return sum(2 * al(nx * ny * 4) + 11 * al(nx * ny * B * es) for nx, ny, B in sizes)
+
+    mix = [(128, 128, 8), (256, 256, 8), (37, 70, 10), (48, 40, 24)]
+    for storage, es in ((0, 4), (1, 2), (2, 2)):
+        w = ws(mix, storage=storage)
+        table = w - fields(mix, es)
+        assert 0 < table <= al(1024 * len(mix)) and table % 256 == 0, (storage, table)
+    assert ws(mix, storage=2) < ws(mix, storage=0)
+    # the table grows with the count, the fields with the sizes; depth does not matter
+    assert ws(mix + [(16, 16, 8)]) > ws(mix)
+    assert ws(mix, fuse_k=2) == ws(mix) == ws(mix, fuse_k=-1)
+    # one-frame TV forms take any B up to 32; VTV only up to 24
+    assert ws([(64, 64, 32)], tv=0) > 0 and ws([(64, 64, 32)], tv=1) > 0
+    assert ws([(64, 64, 25)], tv=2) == 0
+    assert ws([(64, 64, 33)], tv=0) == 0
+    # invalid arguments
+    assert ws([]) == 0
+    assert ws(mix, lam=0.0) == 0 and ws(mix, lam=float("nan")) == 0
+    assert ws([(0, 16, 8)]) == 0 and ws([(16, 16, 0)]) == 0
+    assert ws(mix, storage=3) == 0 and ws(mix, fuse_k=-2) == 0
+    prm = s.SciParams(2, 0.05, 0.0, 10, 5, 0, 0, 1, 1, 0)
+    assert lib.sci_gap_tv_batched_workspace(_problems([(16, 16, 8)], ptr=None), 1, C.byref(prm)) == 0
+    assert lib.sci_gap_tv_batched_workspace(_problems(mix), len(mix), None) == 0
