@@ -58,8 +58,13 @@ class FuseCache:
         return None
 
     def put(self, key: str, fuse_k: int, candidates: list[int], ms: list[float]) -> None:
-        self._d[key] = {"fuse_k": int(fuse_k), "candidates": [int(c) for c in candidates],
-                        "ms": [round(float(m), 6) for m in ms]}
+        """Store one entry.  The file is read again first, so entries that
+        another process stored since this cache was loaded are kept."""
+        merged = self._load()
+        merged.update(self._d)
+        merged[key] = {"fuse_k": int(fuse_k), "candidates": [int(c) for c in candidates],
+                       "ms": [round(float(m), 6) for m in ms]}
+        self._d = merged
         self.save()
 
     def save(self) -> None:

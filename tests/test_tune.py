@@ -82,6 +82,16 @@ def test_cache_round_trip_and_atomic_file(tmp_path):
     assert sorted(os.listdir(tmp_path / "sub")) == ["fuse.json"]  # no temporary file left
 
 
+def test_two_writers_keep_each_others_entries(tmp_path):
+    p = str(tmp_path / "fuse.json")
+    a, b = tune.FuseCache(p), tune.FuseCache(p)  # both loaded before either wrote
+    a.put("ka", 4, [4, -1], [0.1, 0.2])
+    b.put("kb", 6, [6, -1], [0.3, 0.4])
+    a.put("kc", 2, [2, -1], [0.5, 0.6])
+    c = tune.FuseCache(p)
+    assert (c.get("ka"), c.get("kb"), c.get("kc")) == (4, 6, 2)
+
+
 def test_unreadable_or_foreign_cache_starts_empty(tmp_path):
     p = tmp_path / "fuse.json"
     p.write_text("{not json")
