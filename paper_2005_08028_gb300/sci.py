@@ -251,7 +251,7 @@ def _solve(admm: bool, y, bits, B, tv, lam, outer, inner, rho=0.0, storage="f32"
     if fuse_k == "tuned":
         from . import tune
         fuse_k = tune.tuned_fuse("admm" if admm else ("fista" if fista else "gap"), y, bits, B, tv, lam, inner,
-                                 rho=rho, storage=storage, dual=dual)
+                                 rho=rho, storage=storage, dual=dual, work=work)
     prm = _params(tv, lam, rho, outer, inner, storage, fuse_k, init, use_graph, dual)
     lib = load()
     need = lib.sci_solver_workspace(nx, ny, B, C.byref(prm))

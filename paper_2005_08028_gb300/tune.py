@@ -125,9 +125,10 @@ def batch_fuse_candidates(tv: str, Bs: list[int], inner: int) -> list[int]:
 
 def tuned_fuse(algo: str, y: torch.Tensor, bits: torch.Tensor, B: int, tv: str, lam: float, inner: int, *,
                rho: float = 0.0, storage: str = "f32", dual: str = "fgp", cache: FuseCache | None = None,
-               probe_iters: int = 2, reps: int = 3, timer=None) -> int:
+               probe_iters: int = 2, reps: int = 3, timer=None, work=None) -> int:
     """fuse_k for this solve: the cached choice, else timed (timer defaults to
-    sci.sci_tune_fuse, with the same arguments) and stored."""
+    sci.sci_tune_fuse, with the same arguments; ``work``, a sci.Workspace,
+    is lent to the probe solves) and stored."""
     nx, ny = int(y.shape[0]), int(y.shape[1])
     with _lock:
         cache = cache if cache is not None else FuseCache()
@@ -139,8 +140,10 @@ def tuned_fuse(algo: str, y: torch.Tensor, bits: torch.Tensor, B: int, tv: str, 
         if len(cands) == 1:
             best, ms = cands[0], [0.0]
         else:
+            kw = {} if work is None else {"work": work}
             best, ms = (timer or S.sci_tune_fuse)(algo, y, bits, B, tv, lam, inner, cands, rho=rho,
-                                                  storage=storage, dual=dual, probe_iters=probe_iters, reps=reps)
+                                                  storage=storage, dual=dual, probe_iters=probe_iters, reps=reps,
+                                                  **kw)
         cache.put(key, best, cands, ms)
         return best
 

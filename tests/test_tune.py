@@ -126,6 +126,17 @@ def test_tuned_fuse_times_once_then_hits_the_cache(lib, tmp_path):
     assert len(t.calls) == 4 and t.calls[2][1]["rho"] == 0.01
 
 
+def test_the_callers_workspace_is_lent_to_the_probes(lib, tmp_path):
+    cache = tune.FuseCache(str(tmp_path / "f.json"))
+    t = FakeTimer(prefer=6)
+    y = torch.zeros(16, 16)
+    ws = object()
+    tune.tuned_fuse("gap", y, y, 8, "vtv", 0.05, 10, cache=cache, timer=t, work=ws)
+    assert t.calls[0][1]["work"] is ws
+    tune.tuned_fuse("gap", y, y, 8, "vtv", 0.05, 5, cache=cache, timer=t)
+    assert "work" not in t.calls[1][1]
+
+
 def test_a_single_candidate_is_not_timed(lib, tmp_path):
     cache = tune.FuseCache(str(tmp_path / "f.json"))
     t = FakeTimer(prefer=3)
