@@ -75,7 +75,9 @@ def train(net: "S.LearnedProx", X: torch.Tensor, Y: torch.Tensor, *, epochs=8, b
     A peak rate of 1e-3 trains reliably; 3e-3 and above left every ReLU dead
     (the network collapsed to f = 0) in our runs."""
     n = X.shape[0]
-    steps = epochs * max(1, n // batch)
+    if batch < 1 or n < batch:
+        raise ValueError(f"need at least one batch of pairs: {n} pairs, batch {batch}")
+    steps = epochs * (n // batch)
     g = torch.Generator(device="cpu").manual_seed(seed)
     hist, k = [], 0
     for _ in range(epochs):
