@@ -108,24 +108,30 @@ sci_status validate_work(void* work, size_t have, size_t need) {
 
 // Dual updates per fused launch: fuse_k = -1 turns temporal blocking off;
 // otherwise the largest count the tile halo allows (halo = K + 1), capped by
-// fuse_k when it is positive.  Returns 0 when the per-update kernels serve.
+// fuse_k when it is positive, then lowered to the longest launch of an even
+// split of S into ceil(S/K) launches.  Returns 0 when the per-update kernels
+// serve.
 int choose_fuse(int tv, int B, int S, int fuse_k) {
     if (fuse_k < 0) return 0;
     const int maxh = fused_max_halo(tv, B);
     if (maxh < 2) return 0;
     int K = std::min(maxh - 1, default_fuse(tv));
     if (fuse_k > 0) K = std::min(fuse_k, maxh - 1);
-    K = std::min(K, kMaxFuse);
-    return std::max(1, std::min(K, S));
+    K = std::max(1, std::min(std::min(K, kMaxFuse), S));
+    // the launches split S evenly, so the longest one runs ceil(S / launches)
+    return (S + (S + K - 1) / K - 1) / ((S + K - 1) / K);
 }
 
-// S dual updates of FGP in fused launches of at most K updates each.
+// S dual updates of FGP in ceil(S/K) fused launches whose update counts
+// differ by at most one (S = 10, K = 4: 4 + 3 + 3), so no launch pays a
+// tile's fixed load and store cost for a short tail.
 template <typename T>
 int enqueue_fused_prox(int tv, OuterMode mode, int K, int S, float lam, const std::vector<float>& coef,
                        FusedArgs base, FusedBufs<T> bufs, float* x_out_last, cudaStream_t s) {
     int launches = 0;
-    for (int s0 = 0; s0 < S; s0 += K) {
-        const int k = std::min(K, S - s0);
+    const int n = (S + K - 1) / K;
+    for (int i = 0, s0 = 0; i < n; ++i) {
+        const int k = S / n + (i < S % n ? 1 : 0);
         FusedArgs a = base;
         a.mode = mode;
         a.K = k;
@@ -134,16 +140,17 @@ int enqueue_fused_prox(int tv, OuterMode mode, int K, int S, float lam, const st
         a.last = s0 + k == S;
         a.lambda = lam;
         a.step = (float)(1.0 / (8.0 * (double)lam));
-        for (int i = 0; i < k; ++i) a.coef[i] = coef[(size_t)(s0 + i)];
+        for (int j = 0; j < k; ++j) a.coef[j] = coef[(size_t)(s0 + j)];
         a.x_out = a.last ? x_out_last : nullptr;
         if (!launch_fgp_fused<T>(tv, a, bufs, s)) return -1;
         ++launches;
         // the next launch reads what this one wrote, and writes the other set
-        for (int i = 0; i < 4; ++i) {
-            T* written = bufs.st_out[i];
-            bufs.st_out[i] = const_cast<T*>(bufs.st_in[i]);
-            bufs.st_in[i] = written;
+        for (int j = 0; j < 4; ++j) {
+            T* written = bufs.st_out[j];
+            bufs.st_out[j] = const_cast<T*>(bufs.st_in[j]);
+            bufs.st_in[j] = written;
         }
+        s0 += k;
     }
     return launches;
 }

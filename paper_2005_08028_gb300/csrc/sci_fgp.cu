@@ -161,7 +161,7 @@ __global__ void k_fgp_out(OutArgs a, const T* __restrict__ xt, const T* __restri
             const float pu = i >= 1 ? ld<T>(p + N, base - g.ny) : 0.f;
             const float pv = i < g.nx - 1 ? ld<T>(p + N, base) : 0.f;
             const float x0 = a.mode == OuterMode::Prox ? a.xin[base] : ld<T>(xt, base);
-            const float th = x0 - lambda * ((pl - ph) + (pu - pv));
+            const float th = __fmaf_rn(-lambda, (pl - ph) + (pu - pv), x0);
             if (a.mode == OuterMode::Prox) {
                 a.theta_f32[base] = th;
                 continue;

@@ -71,6 +71,31 @@ template <> __device__ __forceinline__ float ldg<__half>(const __half* p, long l
 }
 
 
+// Packed FP32 arithmetic (sm_100 and later): one instruction applies the
+// operation to both lanes of a float2 with the rounding of the scalar
+// operation, so a packed update gives the same bits as the scalar one while
+// issuing half the arithmetic instructions.  a - b is formed as
+// fma(b, -1, a), which rounds once like a subtraction.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void sts4(float* p, float2 a, float2 b) {
+    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
+// Words of a per-thread shared-memory block holding n floats: n rounded up to
+// a multiple of 4 whose quotient by 4 is odd.  Consecutive columns' blocks then
+// start 16-byte aligned, and the 8 lanes of each phase of a 128-bit access
+// fall on 8 different 16-byte bank groups.
+__host__ __device__ constexpr int block_words(int n) {
+    return ((n + 3) / 4) % 2 == 1 ? ((n + 3) / 4) * 4 : ((n + 3) / 4) * 4 + 4;
+}
+
 // Compile-time tile configuration.
 template <int NT_, int Q_, int F_, int EW_LOG2_, bool REG_, bool SKIP_>
 struct FusedCfg {
@@ -81,19 +106,40 @@ struct FusedCfg {
     static constexpr int EW = 1 << EW_LOG2;   // tile width (columns)
     static constexpr int NS = NT / EW;        // strips
     static constexpr int EH = NS * Q;         // tile height (rows)
-    static constexpr bool REG = REG_;         // x-tilde and theta of owned slots in registers
+    static constexpr bool REG = REG_;         // x-tilde of owned slots in registers (else shared memory)
     static constexpr bool SKIP = SKIP_;       // skip rows that can no longer reach the interior
-    // Slot arrays (theta, w_h, and x-tilde unless REG) store each frame as one
-    // leading pad word followed by EH rows of EW slots and a trailing pad word:
-    // slot (r, c) sits at 1 + r * LD + c, so its left neighbour at c = 0 and its
-    // right neighbour at c = EW - 1 are pad words, which hold zero.
-    static constexpr int LD = EW + 1;
-    static constexpr int FPP = EH * LD + 1;
-    // shared memory: slot arrays [F][FPP]; w_v [F][NS][EW]
-    static constexpr size_t SMEM = ((size_t)F * FPP * (REG ? 2 : 3) + (size_t)F * NS * EW) * sizeof(float);
+    static constexpr int E = F * Q;           // slots per thread
+    static constexpr int NP = E / 2;          // packed register pairs per thread: element (q, f) is q F + f
+    // Shared memory, in floats.  Every thread's slots form one block of BLK
+    // words, element (q, f) at q FP + f with each row's frames padded to a
+    // multiple of 4 (FP), so rows and groups of 4 frames move as 128-bit
+    // words.  The blocks of a strip sit column by column, with one zero pad
+    // block on each side (columns -1 and EW): a thread reads its left and
+    // right neighbours' blocks with 128-bit loads and edge columns need no
+    // tests.  w_v of a strip's last row has blocks of BLKV words (one word for
+    // one-frame tiles).
+    static constexpr int FP = F == 1 ? 1 : (F + 3) / 4 * 4;
+    static constexpr int ES = Q * FP;                           // shared words of a thread's slots
+    static constexpr int BLK = block_words(ES);
+    static constexpr int BLKV = F == 1 ? 1 : block_words(FP);
+    static constexpr int SROW = (EW + 2) * BLK;                 // one strip of a padded slot array
+    static constexpr int A_TH = 0;                              // theta          [NS][EW + 2][BLK]
+    static constexpr int A_WH = A_TH + NS * SROW;               // w_h (then p_h) [NS][EW + 2][BLK]
+    static constexpr int A_WV = A_WH + NS * SROW;               // w_v (then p_v) of each strip's last row [NS][EW][BLKV]
+    static constexpr int A_XT = A_WV + ((NS * EW * BLKV + 3) & ~3);  // x-tilde [NS][EW][BLK] (only when !REG)
+    static constexpr size_t SMEM = (size_t)(A_XT + (REG ? 0 : NS * EW * BLK)) * sizeof(float);
     static_assert(NT % EW == 0, "a CTA must cover whole rows");
     static_assert(EW % 32 == 0, "a warp must stay inside one strip row");
+    static_assert(F == 1 ? Q % 4 == 0 : F % 2 == 0, "rows (one frame) or frames pair up for packed arithmetic");
+    static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
 };
+
+// Element (q, f) of a packed register array: pair (q F + f) / 2, lane (q F + f) % 2.
+template <int F>
+__device__ __forceinline__ float& el(float2* a, int q, int f) {
+    float2& p = a[(q * F + f) >> 1];
+    return ((q * F + f) & 1) ? p.y : p.x;
+}
 
 // Problem views for fused_tile: a single problem read from the kernel's
 // parameter space, or one entry of a device-resident batch table.
@@ -137,22 +183,40 @@ struct BatchProb {
 // One tile (bx, by) of frame bz (one-frame tiles) of one problem.  `a`
 // carries the launch-wide settings (K, halo, first/last, lambda, momentum),
 // `p` the problem's geometry and buffers.
-template <typename T, int TV, class Cfg, class Prob>
-__device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, int bx, int by, int bz,
-                                           float* smem) {
-    constexpr int Q = Cfg::Q, F = Cfg::F, EW = Cfg::EW, EH = Cfg::EH, NS = Cfg::NS;
+//
+// Per dual update (Algorithm 1, ATV-FGP box), in the order of scalar FP32
+// operations that the one-update-per-launch kernel also follows, so the two
+// paths agree bit for bit:
+//   theta = fma(-lambda, (w_h,left - w_h) + (w_v,up - w_v), xt)
+//   a_h   = fma(theta_right - theta, step_h, w_h),  a_v likewise downwards
+//   p     = a / max(1, |a|): clamp (ATV); a * min(1, rsqrt(fma(a_h, a_h, a_v a_v)))
+//           (ITV2D); a * min(1, rsqrt(n2_even + n2_odd)) with n2_par = fma(a_h, a_h,
+//           fma(a_v, a_v, n2_par)) over the frames of that parity (VTV)
+//   w     = fma(c, p - p_prev, p)
+// (In the first launch w = 0, and fma(-lambda, 0, xt) = xt exactly.)  One-frame
+// tiles pack pairs of rows of a thread's strip into float2 lanes; VTV tiles
+// pack pairs of frames of one pixel.  VTV tiles always update all F frames:
+// frames B..F-1 hold zeros, their a is zero and they add exact zeros to the
+// norm.
+//
+// BORDER: the tile has rows outside the image or its last row, so the
+// gradient steps carry per-row factors (zero where a difference is not
+// defined).  Interior tiles fold the column conditions into one factor per
+// thread: where a factor is zero, w starts at zero and stays zero (a = w +
+// 0 * difference projects to zero), as the per-row form gives.
+template <typename T, int TV, class Cfg, bool BORDER, class Prob>
+__device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& p, int bx, int by, int bz,
+                                                float* smem) {
+    constexpr int Q = Cfg::Q, F = Cfg::F, EW = Cfg::EW, EH = Cfg::EH, NS = Cfg::NS, FP = Cfg::FP;
+    constexpr int NP = Cfg::NP, BLK = Cfg::BLK, BLKV = Cfg::BLKV, SROW = Cfg::SROW;
     constexpr bool REG = Cfg::REG, SKIP = Cfg::SKIP;
-    constexpr int LD = Cfg::LD, FP = Cfg::FPP;  // row stride, frame stride (padded)
-    float* s_th = smem;                      // [F][FPP]
-    float* s_wh = s_th + F * FP;             // [F][FPP]
-    float* s_wv = s_wh + F * FP;             // [F][NS][EW]: last row of each strip
-    float* s_xt = s_wv + F * NS * EW;        // [F][FPP] (only when !REG)
+    static_assert((F == 1) == (TV != SCI_TV_VTV), "one-frame tiles for ATV / ITV2D, frame tiles for VTV");
 
     const Geo g = p.g();
     const int H = a.halo;
     const int TI = fused_interior(EH, H), TJ = fused_interior(EW, H);  // interior size
     const int gi0 = by * TI - H, gj0 = bx * TJ - H;
-    const int nfr = (F == 1) ? 1 : g.B;          // frames this CTA updates
+    const int nfr = (F == 1) ? 1 : g.B;          // frames of the problem in this CTA
     const int f0 = (F == 1) ? bz : 0;            // global frame of slot f = 0
     const int tid = threadIdx.x;
     const int col = tid & (EW - 1);
@@ -162,6 +226,19 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
     const bool col_in = gj >= 0 && gj < g.ny;
     const bool col_int = col >= H && col < EW - H + 1;
     const int gi_top = gi0 + r0;
+
+    // This thread's blocks and its neighbours'.  th_down (strip NS - 1) and
+    // wv_up (strip 0) then point at other, valid shared words, whose values
+    // are replaced before use.
+    float* const th_own = smem + Cfg::A_TH + strip * SROW + (col + 1) * BLK;
+    float* const wh_own = smem + Cfg::A_WH + strip * SROW + (col + 1) * BLK;
+    const float* const th_right = th_own + BLK;
+    const float* const wh_left = wh_own - BLK;
+    const float* const th_down = th_own + SROW;
+    float* const wv_own = smem + Cfg::A_WV + (strip * EW + col) * BLKV;
+    const float* const wv_up = wv_own - EW * BLKV;
+    float* const xt_own = smem + Cfg::A_XT + (strip * EW + col) * BLK;  // only when !REG
+    const bool has_up = strip > 0, has_down = strip < NS - 1;
 
     // per-row flags as bit masks (bit q: row r0 + q)
     unsigned in_m = 0, ah_m = 0, av_m = 0;
@@ -173,17 +250,13 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
         ah_m |= (unsigned)(in && gj < g.ny - 1) << q;
         av_m |= (unsigned)(in && gi < g.nx - 1) << q;
     }
-    // Strips whose rows all lie inside the image and above its last row need
-    // no row masks (warp-uniform): the column conditions fold into per-thread
-    // steps, zero where the gradient component is defined as zero.  w stays
-    // zero there (it starts at zero and a = w + 0 * (difference) projects to
-    // zero), so the masked and unmasked forms agree.
-    const bool rows_inner = gi_top >= 0 && gi_top + Q - 1 < g.nx - 1;
-    const float step_h = (col_in && gj < g.ny - 1) ? a.step : 0.f;
-    const float step_v = col_in ? a.step : 0.f;
+    const float step = a.step;
+    const float step_h = (col_in && gj < g.ny - 1) ? step : 0.f;
+    const float step_v = col_in ? step : 0.f;
+    auto fac = [&](unsigned m, int q) -> float { return ((m >> q) & 1u) ? step : 0.f; };
 
-    float ph[F][Q], pv[F][Q], wh[F][Q], wv[F][Q];
-    float xr[REG ? F : 1][REG ? Q : 1], thr[REG ? F : 1][REG ? Q : 1];
+    float2 PH[NP], PV[NP], WH[NP], WV[NP];
+    float2 X[REG ? NP : 1];
 
     // ---- load x-tilde (and the carried duals) for the whole extended tile ----
     // Every load is issued unconditionally -- a pixel outside the image reads
@@ -192,6 +265,8 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
     // rather than one row at a time.
     const long long pix_top = (long long)gi_top * g.ny + gj;
     auto pix_of = [&](int q) -> long long { return ((in_m >> q) & 1u) ? pix_top + (long long)q * g.ny : 0; };
+    float2 XS[REG ? 1 : NP];  // x-tilde staging for tiles that keep it in shared memory
+    auto xe = [&](int q, int f) -> float& { return REG ? el<F>(X, q, f) : el<F>(XS, q, f); };
     if (!a.first) {
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
@@ -200,17 +275,13 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
             for (int f = 0; f < F; ++f) {
                 if (f >= nfr) break;
                 const long long gidx = (long long)(f0 + f) * g.n + pix;
-                ph[f][q] = ldraw<T>(p.st_in(0), gidx);
-                pv[f][q] = ldraw<T>(p.st_in(1), gidx);
-                wh[f][q] = ldraw<T>(p.st_in(2), gidx);
-                wv[f][q] = ldraw<T>(p.st_in(3), gidx);
+                el<F>(PH, q, f) = ldraw<T>(p.st_in(0), gidx);
+                el<F>(PV, q, f) = ldraw<T>(p.st_in(1), gidx);
+                el<F>(WH, q, f) = ldraw<T>(p.st_in(2), gidx);
+                el<F>(WV, q, f) = ldraw<T>(p.st_in(3), gidx);
             }
         }
     }
-    // x-tilde as loaded: straight into the x-tilde registers of REG tiles,
-    // into staging registers otherwise
-    float xs[REG ? 1 : F][REG ? 1 : Q];
-    auto xq = [&](int f, int q) -> float& { return REG ? xr[REG ? f : 0][REG ? q : 0] : xs[REG ? 0 : f][REG ? 0 : q]; };
     if (a.mode == OuterMode::Prox) {
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
@@ -218,7 +289,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 if (f >= nfr) break;
-                xq(f, q) = __ldg(p.xin() + (long long)(f0 + f) * g.n + pix);
+                xe(q, f) = __ldg(p.xin() + (long long)(f0 + f) * g.n + pix);
             }
         }
     } else if (a.first) {
@@ -232,7 +303,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 if (f >= nfr) break;
-                xq(f, q) = ldraw<T>(p.theta_in(), (long long)(f0 + f) * g.n + pix);
+                xe(q, f) = ldraw<T>(p.theta_in(), (long long)(f0 + f) * g.n + pix);
             }
         }
 #pragma unroll
@@ -240,7 +311,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 if (f >= nfr) break;
-                xq(f, q) = rt<T>(cvraw<T>(xq(f, q)) + mask_bit(word[q], f0 + f) * rv[q]);
+                xe(q, f) = rt<T>(cvraw<T>(xe(q, f)) + mask_bit(word[q], f0 + f) * rv[q]);
             }
         }
     } else {
@@ -250,7 +321,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 if (f >= nfr) break;
-                xq(f, q) = ldraw<T>(p.xt(), (long long)(f0 + f) * g.n + pix);
+                xe(q, f) = ldraw<T>(p.xt(), (long long)(f0 + f) * g.n + pix);
             }
         }
 #pragma unroll
@@ -258,7 +329,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 if (f >= nfr) break;
-                xq(f, q) = cvraw<T>(xq(f, q));
+                xe(q, f) = cvraw<T>(xe(q, f));
             }
         }
     }
@@ -268,10 +339,10 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 if (f >= nfr) break;
-                ph[f][q] = cvraw<T>(ph[f][q]);
-                pv[f][q] = cvraw<T>(pv[f][q]);
-                wh[f][q] = cvraw<T>(wh[f][q]);
-                wv[f][q] = cvraw<T>(wv[f][q]);
+                el<F>(PH, q, f) = cvraw<T>(el<F>(PH, q, f));
+                el<F>(PV, q, f) = cvraw<T>(el<F>(PV, q, f));
+                el<F>(WH, q, f) = cvraw<T>(el<F>(WH, q, f));
+                el<F>(WV, q, f) = cvraw<T>(el<F>(WV, q, f));
             }
         }
     }
@@ -280,127 +351,223 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
         const bool in = (in_m >> q) & 1u;
 #pragma unroll
         for (int f = 0; f < F; ++f) {
-            if (f >= nfr) break;
-            const float x = in ? xq(f, q) : 0.f;
-            if (a.first || !in) {
-                ph[f][q] = 0.f;
-                pv[f][q] = 0.f;
-                wh[f][q] = 0.f;
-                wv[f][q] = 0.f;
+            const bool live = in && f < nfr;
+            if (!live) xe(q, f) = 0.f;
+            if (a.first || !live) {
+                el<F>(PH, q, f) = 0.f;
+                el<F>(PV, q, f) = 0.f;
+                el<F>(WH, q, f) = 0.f;
+                el<F>(WV, q, f) = 0.f;
             }
-            const int o = f * FP + 1 + (r0 + q) * LD + col;
-            if (REG) xr[REG ? f : 0][REG ? q : 0] = x;
-            else s_xt[o] = x;
-            s_wh[o] = wh[f][q];
-            if (q == Q - 1) s_wv[(f * NS + strip) * EW + col] = wv[f][q];
         }
     }
-    for (int e = tid; e < F * (EH + 1); e += Cfg::NT) {  // pad words
-        const int f = e / (EH + 1), k = e - f * (EH + 1);
-        s_th[f * FP + k * LD] = 0.f;
-        s_wh[f * FP + k * LD] = 0.f;
+    // Pair (q, f..f+1) of a register array as the 128-bit half it occupies in
+    // a shared block: rows of one-frame tiles pair as (2m, 2m+1) = words 2m..2m+1;
+    // frame tiles pair frames f, f+1 of row q = words q FP + f.
+    auto put_block = [&](float* blk, const float2* R) {
+        if constexpr (F == 1) {
+#pragma unroll
+            for (int c = 0; c < Q / 4; ++c) sts4(blk + 4 * c, R[2 * c], R[2 * c + 1]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+#pragma unroll
+                for (int c = 0; c < FP / 4; ++c) {
+                    const int e2 = (q * F + 4 * c) / 2;
+                    sts4(blk + q * FP + 4 * c, R[e2], 4 * c + 2 < F ? R[4 * c + 2 < F ? e2 + 1 : 0] : make_float2(0.f, 0.f));
+                }
+        }
+    };
+    auto put_last_row = [&](float* blk, const float2* R) {
+        if constexpr (F == 1) {
+            blk[0] = R[NP - 1].y;
+        } else {
+#pragma unroll
+            for (int c = 0; c < FP / 4; ++c) {
+                const int e2 = ((Q - 1) * F + 4 * c) / 2;
+                sts4(blk + 4 * c, R[e2], 4 * c + 2 < F ? R[4 * c + 2 < F ? e2 + 1 : 0] : make_float2(0.f, 0.f));
+            }
+        }
+    };
+    put_block(wh_own, WH);
+    if (!REG) put_block(xt_own, XS);
+    put_last_row(wv_own, WV);
+    // zero pad blocks (columns -1 and EW of every strip) of theta and w_h
+    for (int e = tid; e < NS * 2 * (BLK / 4); e += Cfg::NT) {
+        const int s = e / (2 * (BLK / 4)), rem = e - s * 2 * (BLK / 4);
+        const int side = rem / (BLK / 4), w4 = rem - side * (BLK / 4);
+        const int off = s * SROW + (side ? (EW + 1) * BLK : 0) + 4 * w4;
+        *reinterpret_cast<float4*>(smem + Cfg::A_TH + off) = make_float4(0.f, 0.f, 0.f, 0.f);
+        *reinterpret_cast<float4*>(smem + Cfg::A_WH + off) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
 
-    const float lam = a.lambda, step = a.step;
+    const float2 nlam2 = dup2(-a.lambda);
+    const float2 steph2 = dup2(step_h), stepv2 = dup2(step_v);
     // Two updates per loop trip let the compiler alternate registers instead
-    // of copying the loop-carried duals (measured: VTV tiles of up to 10
-    // frames -6%, ITV2D -3%).  The one-frame ATV tile gains nothing, and the
-    // 16- and 24-frame VTV tiles, already near the register limit, lose.
-    constexpr int kUnroll = ((TV == SCI_TV_ATV && F == 1) || F > 10) ? 1 : 2;
+    // of copying the loop-carried duals; the 16- and 24-frame VTV tiles, near
+    // the register limit, run one.
+    constexpr int kUnroll = F > 10 ? 1 : 2;
 #pragma unroll kUnroll
     for (int s = 0; s < a.K; ++s) {
-        // rows whose p stays exact after this update: [1 + s, EH - 1 - s);
-        // theta is needed on those rows and the one below
-        const int rlo = 1 + s, rhi = EH - 1 - s;
-        const int qlo = SKIP ? max(rlo - r0, 0) : 0;
-        const int qhi_p = SKIP ? min(rhi - r0, Q) : Q, qhi_t = SKIP ? min(rhi + 1 - r0, Q) : Q;
-        const bool skip_theta = a.first && s == 0;  // w = 0 there: theta = xt
-        // ---- theta = xt - lambda (D^T w) ----
+        const float2 c2 = dup2(a.coef[s]);
+        if constexpr (F == 1) {
+            // ---- theta = xt - lambda (D^T w), rows paired ----
+            const float up_in = wv_up[0];
+            const float up = has_up ? up_in : 0.f;
 #pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            if (q < qlo || q >= qhi_t) continue;
+            for (int c = 0; c < Q / 4; ++c) {
+                const float4 wl = lds4(wh_left + 4 * c);
+                float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (!REG) xv = lds4(xt_own + 4 * c);
+                float2 th[2];
 #pragma unroll
-            for (int f = 0; f < F; ++f) {
-                if (f >= nfr) break;
-                const int o = f * FP + 1 + (r0 + q) * LD + col;
-                float th = REG ? xr[REG ? f : 0][REG ? q : 0] : s_xt[o];
-                if (!skip_theta) {
-                    const float wl = s_wh[o - 1];
-                    float wu;
-                    if (q > 0) wu = wv[f][q > 0 ? q - 1 : 0];
-                    else wu = strip > 0 ? s_wv[(f * NS + strip - 1) * EW + col] : 0.f;
-                    th = th - lam * ((wl - wh[f][q]) + (wu - wv[f][q]));
+                for (int h = 0; h < 2; ++h) {
+                    const int m = 2 * c + h;
+                    const float wu0 = m == 0 ? up : WV[m > 0 ? m - 1 : 0].y;
+                    const float2 dv = make_float2(wu0 - WV[m].x, WV[m].x - WV[m].y);
+                    const float2 x2 = REG ? X[REG ? m : 0] : (h ? hi2(xv) : lo2(xv));
+                    th[h] = fma2(nlam2, add2(sub2(h ? hi2(wl) : lo2(wl), WH[m]), dv), x2);
                 }
-                if (REG) thr[REG ? f : 0][REG ? q : 0] = th;
-                s_th[o] = th;
+                sts4(th_own + 4 * c, th[0], th[1]);
             }
-        }
-        __syncthreads();
-        // ---- a = w + step * D theta (kept in the w registers), projection, momentum ----
-        const float c = a.coef[s];
-        auto dual_step = [&](auto masked_c) {
-            constexpr bool MASKED = decltype(masked_c)::value;
+            __syncthreads();
+            // ---- a = w + step * D theta, projection, momentum ----
+            const float down_in = th_down[0];
+            float4 tcur = lds4(th_own);
+#pragma unroll
+            for (int c = 0; c < Q / 4; ++c) {
+                const float4 tr = lds4(th_right + 4 * c);
+                float4 tnext = tcur;
+                if (c + 1 < Q / 4) tnext = lds4(th_own + 4 * (c + 1));
+                const float below_last = (c + 1 < Q / 4) ? tnext.x : (has_down ? down_in : tcur.w);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int m = 2 * c + h;
+                    const float2 t0 = h ? hi2(tcur) : lo2(tcur);
+                    const float below = h ? below_last : tcur.z;
+                    const float2 gh = sub2(h ? hi2(tr) : lo2(tr), t0);
+                    const float2 gv = make_float2(t0.y - t0.x, below - t0.y);
+                    float2 sh = steph2, sv = stepv2;
+                    if (BORDER) {
+                        sh = make_float2(fac(ah_m, 2 * m), fac(ah_m, 2 * m + 1));
+                        sv = make_float2(fac(av_m, 2 * m), fac(av_m, 2 * m + 1));
+                    }
+                    float2 ah = fma2(gh, sh, WH[m]);
+                    float2 av = fma2(gv, sv, WV[m]);
+                    if (TV == SCI_TV_ATV) {
+                        ah.x = fminf(fmaxf(ah.x, -1.f), 1.f);
+                        ah.y = fminf(fmaxf(ah.y, -1.f), 1.f);
+                        av.x = fminf(fmaxf(av.x, -1.f), 1.f);
+                        av.y = fminf(fmaxf(av.y, -1.f), 1.f);
+                    } else {
+                        // a / max(1, |a|) = a * min(1, 1/|a|); 1/sqrt(0) = inf gives 1
+                        const float2 nn = fma2(ah, ah, mul2(av, av));
+                        const float2 sc = make_float2(fminf(1.f, rsqrt_ftz(nn.x)), fminf(1.f, rsqrt_ftz(nn.y)));
+                        ah = mul2(ah, sc);
+                        av = mul2(av, sc);
+                    }
+                    WH[m] = fma2(c2, sub2(ah, PH[m]), ah);
+                    WV[m] = fma2(c2, sub2(av, PV[m]), av);
+                    PH[m] = ah;
+                    PV[m] = av;
+                }
+                sts4(wh_own + 4 * c, WH[2 * c], WH[2 * c + 1]);
+                tcur = tnext;
+            }
+            wv_own[0] = WV[NP - 1].y;
+            __syncthreads();
+        } else {
+            // rows whose p stays exact after this update: [1 + s, EH - 1 - s);
+            // theta is needed on those rows and the one below
+            const int rlo = 1 + s, rhi = EH - 1 - s;
+            const int qlo = SKIP ? max(rlo - r0, 0) : 0;
+            const int qhi_p = SKIP ? min(rhi - r0, Q) : Q, qhi_t = SKIP ? min(rhi + 1 - r0, Q) : Q;
+            // ---- theta = xt - lambda (D^T w), frames paired ----
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                if (q < qlo || q >= qhi_t) continue;
+#pragma unroll
+                for (int c = 0; c < FP / 4; ++c) {
+                    const float4 wl = lds4(wh_left + q * FP + 4 * c);
+                    float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (!REG) xv = lds4(xt_own + q * FP + 4 * c);
+                    float4 wu = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (q == 0) {
+                        const float4 w = lds4(wv_up + 4 * c);
+                        if (has_up) wu = w;
+                    }
+                    float2 th[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (4 * c + 2 * h >= F) continue;
+                        const int e2 = (q * F + 4 * c) / 2 + h;
+                        const float2 x2 = REG ? X[REG ? e2 : 0] : (h ? hi2(xv) : lo2(xv));
+                        const float2 wu2 = q > 0 ? WV[q > 0 ? e2 - F / 2 : 0] : (h ? hi2(wu) : lo2(wu));
+                        th[h] = fma2(nlam2, add2(sub2(h ? hi2(wl) : lo2(wl), WH[e2]), sub2(wu2, WV[e2])), x2);
+                    }
+                    sts4(th_own + q * FP + 4 * c, th[0], th[1]);
+                }
+            }
+            __syncthreads();
+            // ---- a = w + step * D theta (kept in the w registers), norm over frames,
+            //      projection onto the per-pixel ball, momentum ----
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
                 if (q < qlo || q >= qhi_p) continue;
-                const bool mh = (ah_m >> q) & 1u, mv = (av_m >> q) & 1u;
-                float n2 = 0.f;
-#pragma unroll
-                for (int f = 0; f < F; ++f) {
-                    if (f >= nfr) break;
-                    const int o = f * FP + 1 + (r0 + q) * LD + col;
-                    const float t0 = REG ? thr[REG ? f : 0][REG ? q : 0] : s_th[o];
-                    const float tr = s_th[o + 1];
-                    float td;
-                    if (q < Q - 1) td = REG ? thr[REG ? f : 0][REG && q < Q - 1 ? q + 1 : 0] : s_th[o + LD];
-                    else td = (r0 + q < EH - 1) ? s_th[o + LD] : t0;
-                    float ah, av;
-                    if (MASKED) {
-                        ah = mh ? fmaf(tr - t0, step, wh[f][q]) : 0.f;
-                        av = mv ? fmaf(td - t0, step, wv[f][q]) : 0.f;
-                    } else {
-                        ah = fmaf(tr - t0, step_h, wh[f][q]);
-                        av = fmaf(td - t0, step_v, wv[f][q]);
-                    }
-                    wh[f][q] = ah;
-                    wv[f][q] = av;
-                    if (TV == SCI_TV_VTV) n2 = fmaf(ah, ah, fmaf(av, av, n2));
+                float2 sh = steph2, sv = stepv2;
+                if (BORDER) {
+                    sh = dup2(fac(ah_m, q));
+                    sv = dup2(fac(av_m, q));
                 }
-                const float vscale = (TV == SCI_TV_VTV) ? fminf(1.f, rsqrt_ftz(n2)) : 1.f;
+                float2 n2 = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int f = 0; f < F; ++f) {
-                    if (f >= nfr) break;
-                    float nh = wh[f][q], nv = wv[f][q];
-                    if (TV == SCI_TV_ATV) {
-                        nh = fminf(fmaxf(nh, -1.f), 1.f);
-                        nv = fminf(fmaxf(nv, -1.f), 1.f);
-                    } else if (TV == SCI_TV_ITV2D) {
-                        // a / max(1, |a|) = a * min(1, 1/|a|); 1/sqrt(0) = inf gives 1
-                        const float sc = fminf(1.f, rsqrt_ftz(fmaf(nh, nh, nv * nv)));
-                        nh *= sc;
-                        nv *= sc;
+                for (int c = 0; c < FP / 4; ++c) {
+                    const float4 tr = lds4(th_right + q * FP + 4 * c);
+                    const float4 t0 = lds4(th_own + q * FP + 4 * c);
+                    float4 td;
+                    if (q < Q - 1) {
+                        td = lds4(th_own + (q + 1) * FP + 4 * c);
                     } else {
-                        nh *= vscale;
-                        nv *= vscale;
+                        const float4 d = lds4(th_down + 4 * c);
+                        td = has_down ? d : t0;
                     }
-                    const float wnh = fmaf(c, nh - ph[f][q], nh);
-                    const float wnv = fmaf(c, nv - pv[f][q], nv);
-                    ph[f][q] = nh;
-                    pv[f][q] = nv;
-                    wh[f][q] = wnh;
-                    wv[f][q] = wnv;
-                    s_wh[f * FP + 1 + (r0 + q) * LD + col] = wnh;
-                    if (q == Q - 1) s_wv[(f * NS + strip) * EW + col] = wnv;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (4 * c + 2 * h >= F) continue;
+                        const int e2 = (q * F + 4 * c) / 2 + h;
+                        const float2 tt = h ? hi2(t0) : lo2(t0);
+                        const float2 ah = fma2(sub2(h ? hi2(tr) : lo2(tr), tt), sh, WH[e2]);
+                        const float2 av = fma2(sub2(h ? hi2(td) : lo2(td), tt), sv, WV[e2]);
+                        WH[e2] = ah;
+                        WV[e2] = av;
+                        n2 = fma2(ah, ah, fma2(av, av, n2));
+                    }
+                }
+                const float2 vs = dup2(fminf(1.f, rsqrt_ftz(n2.x + n2.y)));
+#pragma unroll
+                for (int f = 0; f < F; f += 2) {
+                    const int e2 = (q * F + f) / 2;
+                    const float2 nh = mul2(WH[e2], vs), nv = mul2(WV[e2], vs);
+                    WH[e2] = fma2(c2, sub2(nh, PH[e2]), nh);
+                    WV[e2] = fma2(c2, sub2(nv, PV[e2]), nv);
+                    PH[e2] = nh;
+                    PV[e2] = nv;
+                }
+#pragma unroll
+                for (int c = 0; c < FP / 4; ++c) {
+                    const int e2 = (q * F + 4 * c) / 2;
+                    sts4(wh_own + q * FP + 4 * c, WH[e2],
+                         4 * c + 2 < F ? WH[4 * c + 2 < F ? e2 + 1 : 0] : make_float2(0.f, 0.f));
                 }
             }
-        };
-        if (rows_inner) dual_step(std::false_type{});
-        else dual_step(std::true_type{});
-        __syncthreads();
+            put_last_row(wv_own, WV);
+            __syncthreads();
+        }
     }
 
     // ---- epilogue ----
+    auto sidx = [&](int q, int f) { return q * FP + f; };  // element (q, f) of a shared block
     if (!a.last) {
         // carry x-tilde (first launch of a solve), p and w of the interior
 #pragma unroll
@@ -413,29 +580,22 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
                 if (f >= nfr) break;
                 const long long gidx = (long long)(f0 + f) * g.n + pix;
                 if (a.first && a.mode != OuterMode::Prox)
-                    st<T>(p.xt(), gidx, REG ? xr[REG ? f : 0][REG ? q : 0] : s_xt[f * FP + 1 + r * LD + col]);
-                st<T>(p.st_out(0), gidx, ph[f][q]);
-                st<T>(p.st_out(1), gidx, pv[f][q]);
-                st<T>(p.st_out(2), gidx, wh[f][q]);
-                st<T>(p.st_out(3), gidx, wv[f][q]);
+                    st<T>(p.xt(), gidx, REG ? el<F>(X, q, f) : xt_own[sidx(q, f)]);
+                st<T>(p.st_out(0), gidx, el<F>(PH, q, f));
+                st<T>(p.st_out(1), gidx, el<F>(PV, q, f));
+                st<T>(p.st_out(2), gidx, el<F>(WH, q, f));
+                st<T>(p.st_out(3), gidx, el<F>(WV, q, f));
             }
         }
         return;
     }
     // theta = xt - lambda D^T p needs p_h of the left neighbour and p_v of the
     // row above: stage them where w_h / w_v were (the loop ended with a barrier).
-#pragma unroll
-    for (int q = 0; q < Q; ++q) {
-#pragma unroll
-        for (int f = 0; f < F; ++f) {
-            if (f >= nfr) break;
-            s_wh[f * FP + 1 + (r0 + q) * LD + col] = ph[f][q];
-            if (q == Q - 1) s_wv[(f * NS + strip) * EW + col] = pv[f][q];
-        }
-    }
+    put_block(wh_own, PH);
+    put_last_row(wv_own, PV);
     // x^(t+1) = xt - u^(t) for ADMM (only when x is requested): u^(t) is read
     // before u^(t+1) overwrites it.  Issue every load first (into the thread's
-    // own theta slots, free now) so none waits behind a store it might alias.
+    // own theta block, free now) so none waits behind a store it might alias.
     if (a.mode == OuterMode::Admm && p.x_out() != nullptr) {
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
@@ -445,7 +605,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
 #pragma unroll
             for (int f = 0; f < F; ++f) {
                 if (f >= nfr) break;
-                s_th[f * FP + 1 + r * LD + col] = mine ? ldg<T>(p.u_in(), (long long)(f0 + f) * g.n + pix) : 0.f;
+                th_own[sidx(q, f)] = mine ? ldg<T>(p.u_in(), (long long)(f0 + f) * g.n + pix) : 0.f;
             }
         }
     }
@@ -458,13 +618,12 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
 #pragma unroll
         for (int f = 0; f < F; ++f) {
             if (f >= nfr) break;
-            const int o = f * FP + 1 + r * LD + col;
-            const float pl = s_wh[o - 1];
+            const float pl = wh_left[sidx(q, f)];
             float pu;
-            if (q > 0) pu = pv[f][q > 0 ? q - 1 : 0];
-            else pu = strip > 0 ? s_wv[(f * NS + strip - 1) * EW + col] : 0.f;
-            const float x0 = REG ? xr[REG ? f : 0][REG ? q : 0] : s_xt[o];
-            const float th = x0 - lam * ((pl - ph[f][q]) + (pu - pv[f][q]));
+            if (q > 0) pu = el<F>(PV, q > 0 ? q - 1 : 0, f);
+            else pu = has_up ? wv_up[f] : 0.f;
+            const float x0 = REG ? el<F>(X, q, f) : xt_own[sidx(q, f)];
+            const float th = __fmaf_rn(-a.lambda, (pl - el<F>(PH, q, f)) + (pu - el<F>(PV, q, f)), x0);
             const long long gidx = (long long)(f0 + f) * g.n + pix;
             if (a.mode == OuterMode::Prox) {
                 p.theta_f32()[gidx] = th;
@@ -475,10 +634,23 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
                 if (p.x_out() != nullptr) p.x_out()[gidx] = x0;
             } else {
                 st<T>(p.u_out(), gidx, x0 - rt<T>(th));
-                if (p.x_out() != nullptr) p.x_out()[gidx] = x0 - s_th[o];
+                if (p.x_out() != nullptr) p.x_out()[gidx] = x0 - th_own[sidx(q, f)];
             }
         }
     }
+}
+
+// A tile all of whose rows lie inside the image and above its last row runs
+// the interior form; the others the border form.
+template <typename T, int TV, class Cfg, class Prob>
+__device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, int bx, int by, int bz,
+                                           float* smem) {
+    const Geo g = p.g();
+    const int gi0 = by * fused_interior(Cfg::EH, a.halo) - a.halo;
+    if (gi0 >= 0 && gi0 + Cfg::EH - 1 < g.nx - 1)
+        fused_tile_impl<T, TV, Cfg, false>(a, p, bx, by, bz, smem);
+    else
+        fused_tile_impl<T, TV, Cfg, true>(a, p, bx, by, bz, smem);
 }
 
 // ---------------------------------------------------------------- configurations
@@ -488,7 +660,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
 // 1- or 2-row strips, where skipping balances well and saves work.
 using CfgF1 = FusedCfg<512, 16, 1, 7, true, false>;    // 128 x 64 tile, one frame
 using CfgF1s = FusedCfg<256, 8, 1, 6, true, false>;    // 64 x 32 tile, one frame (small images)
-using CfgV8 = FusedCfg<512, 2, 8, 5, false, true>;     // 32 x 32 tile, up to 8 frames
+using CfgV8 = FusedCfg<512, 2, 8, 5, true, true>;      // 32 x 32 tile, up to 8 frames
 using CfgV10 = FusedCfg<512, 2, 10, 5, false, true>;   // 32 x 32 tile, up to 10 frames
 using CfgV16 = FusedCfg<256, 2, 16, 5, false, true>;   // 32 x 16 tile, up to 16 frames
 using CfgV24 = FusedCfg<256, 2, 24, 5, false, true>;   // 32 x 16 tile, up to 24 frames

@@ -65,7 +65,10 @@ __global__ void __launch_bounds__(256) k_fgp_stream(StreamArgs a, const T* __res
     const bool has_q = q != nullptr;
 
     float ah_r[FMAX], av_r[FMAX];
-    float n2 = 0.f;
+    // VTV norm: the frames of each parity accumulate separately and the two
+    // sums are added at the end (the order the temporally blocked kernel's
+    // packed frame pairs follow)
+    float n2e = 0.f, n2o = 0.f;
 #pragma unroll
     for (int ff = 0; ff < FMAX; ++ff) {
         if (ff >= nfr) break;
@@ -100,7 +103,8 @@ __global__ void __launch_bounds__(256) k_fgp_stream(StreamArgs a, const T* __res
             const int rr = e / (TW + 1), cc = e % (TW + 1);
             float th = s_x[rr][cc];
             if (!a.first)
-                th -= a.lambda * ((s_wh[rr + 1][cc] - s_wh[rr + 1][cc + 1]) + (s_wv[rr][cc + 1] - s_wv[rr + 1][cc + 1]));
+                th = __fmaf_rn(-a.lambda,
+                               (s_wh[rr + 1][cc] - s_wh[rr + 1][cc + 1]) + (s_wv[rr][cc + 1] - s_wv[rr + 1][cc + 1]), th);
             s_th[rr][cc] = th;
         }
         __syncthreads();
@@ -112,7 +116,8 @@ __global__ void __launch_bounds__(256) k_fgp_stream(StreamArgs a, const T* __res
         if (TV == SCI_TV_VTV) {
             ah_r[ff] = ah;
             av_r[ff] = av;
-            n2 = fmaf(ah, ah, fmaf(av, av, n2));
+            if (ff & 1) n2o = fmaf(ah, ah, fmaf(av, av, n2o));
+            else n2e = fmaf(ah, ah, fmaf(av, av, n2e));
         } else if (in) {
             float nh = ah, nv = av;
             if (TV == SCI_TV_ATV) {
@@ -130,7 +135,7 @@ __global__ void __launch_bounds__(256) k_fgp_stream(StreamArgs a, const T* __res
         __syncthreads();  // the next frame reuses the shared tiles
     }
     if (TV == SCI_TV_VTV && in) {
-        const float sc = fminf(1.f, rsqrtf(n2));
+        const float sc = fminf(1.f, rsqrtf(n2e + n2o));
 #pragma unroll
         for (int ff = 0; ff < FMAX; ++ff) {
             if (ff >= nfr) break;

@@ -132,19 +132,27 @@ def test_binding_structs_mirror_the_header(cname, pyname):
 
 def test_fuse_depth_planner(lib):
     """Host logic, no GPU: dual updates per temporally blocked launch.  One-frame
-    tiles (ATV, ITV2D) take up to 10; the 32 x 32 VTV tiles of up to 10 frames
-    take up to 6 (halo <= 8); 16 / 24 frames take up to 3 (halo <= 4); more than
-    24 frames fall back to one launch per update (0).  fuse_k = -1 switches
-    blocking off; fuse_k > 0 caps the depth; S caps it too."""
+    tiles (ATV, ITV2D) take up to 10 by default; the 32 x 32 VTV tiles of up to
+    10 frames up to 4 (and at most 7: halo <= 8); 16 / 24 frames up to 3 (halo
+    <= 4); more than 24 frames fall back to one launch per update (0).  fuse_k
+    = -1 switches blocking off; fuse_k > 0 caps the depth; S caps it too.  The
+    S updates are split evenly over ceil(S/K) launches, so the depth reported
+    is the longest launch of that split (S = 25, K = 10: 9 + 8 + 8)."""
     import paper_2005_08028_gb300.sci as s
     q = s.sci_fused_updates
     assert q("atv", 10, 10) == 10 and q("itv2d", 32, 10) == 10
-    assert q("atv", 10, 25) == 10 and q("atv", 10, 4) == 4
-    assert q("vtv", 10, 10) == 6 and q("vtv", 8, 10) == 6 and q("vtv", 10, 5) == 5
+    assert q("atv", 10, 25) == 9 and q("atv", 10, 4) == 4
+    assert q("vtv", 10, 10) == 4 and q("vtv", 8, 10) == 4 and q("vtv", 10, 5) == 3
     assert q("vtv", 16, 10) == 3 and q("vtv", 24, 5) == 3
     assert q("vtv", 25, 10) == 0 and q("vtv", 32, 10) == 0
     assert q("atv", 10, 10, -1) == 0 and q("vtv", 10, 10, -1) == 0
-    assert q("atv", 10, 10, 3) == 3 and q("vtv", 10, 10, 30) == 7  # clamped to the halo
+    assert q("atv", 10, 10, 3) == 3 and q("vtv", 10, 10, 30) == 5  # clamped to the halo (7), then 5 + 5
+    for tv, B in (("atv", 1), ("vtv", 10), ("vtv", 24)):
+        for S in range(1, 26):
+            for k in range(0, S + 1):
+                K = q(tv, B, S, k)
+                n = -(-S // K)
+                assert K == -(-S // n), (tv, B, S, k)  # the longest launch of the even split
 
 
 def _problems(sizes, ptr=0x10000):
