@@ -33,6 +33,9 @@ Readings where the paper is silent or garbled:
     box carries its last momentum point w (which may lie outside the dual
     set), the Chambolle box its w.
   * Loops run exactly T outer and S inner iterations.
+  * The Clip box of Algorithm 1 (ATV only) clips at T = lam with step
+    1/alpha, alpha = 4, and outputs x - D_h^T w_h - D_v^T w_v from its final
+    duals (clip_prox states why).
   * The Chambolle box of Algorithm 1 is read with its D^T as the divergence
     (minus the adjoint), as in Chambolle's derivation; with the adjoint its
     update ascends.  It keeps the max(1, |.|) denominator the paper states it
@@ -57,7 +60,8 @@ import numpy as np
 __all__ = [
     "TV_TYPES", "forward", "adjoint", "mask_energy", "gap_project", "admm_xupdate",
     "grad_h", "grad_v", "grad_h_adj", "grad_v_adj", "div_adj", "tv_value",
-    "dual_project", "fgp_momentum_coeffs", "fgp_prox", "divergence", "cham_prox", "prox_objective",
+    "dual_project", "fgp_momentum_coeffs", "fgp_prox", "divergence", "cham_prox", "CLIP_ALPHA", "clip_prox",
+    "prox_objective",
     "dual_objective", "gap_tv", "admm_tv", "lipschitz", "fista_tv", "twist_params", "twist_xi1", "twist_tv",
     "psnr",
     "residual_sq",
@@ -317,12 +321,60 @@ def cham_prox(x: np.ndarray, lam: float, S: int, tv: str, *, return_dual: bool =
     return theta
 
 
+CLIP_ALPHA = 4.0  # 1/alpha is the clipping step; ||D_h||^2, ||D_v||^2 <= 4 for 1-D differences
+
+
+def clip_prox(x: np.ndarray, lam: float, S: int, tv: str = "atv", *, alpha: float = CLIP_ALPHA,
+              thresh: float | None = None, return_dual: bool = False, w0=None, return_state: bool = False):
+    """S iterations of the ATV-Clip box of Algorithm 1 (Selesnick's iterative
+    clipping, Sec. 2.3), with unscaled duals w_h, w_v.  Per iteration s:
+      theta_h = x - D_h^T w_h,    theta_v = x - D_v^T w_v
+      w_h = clip(w_h + (1/alpha) D_h theta_h, T),  w_v likewise with D_v, theta_v
+    where clip(a, T) = min(max(a, -T), T).  Output theta_h + theta_v - x,
+    formed from the final w: x - D_h^T w_h - D_v^T w_v.
+
+    Readings (the box leaves alpha undefined and prints the threshold 2 lam):
+    T = lam, so that a converged box gives, per direction, the exact 1-D
+    proximal map of lam * TV -- the same scale as the FGP and Chambolle boxes
+    (prox of lam TV under 1/2||theta - x||^2; the printed 2 lam matches a
+    fidelity without the 1/2); alpha = 4, the bound on the largest eigenvalue
+    of D_h D_h^T (and D_v D_v^T), which makes the clipped step converge; the
+    output uses the duals after the S-th update, as for FGP (Beck and
+    Teboulle's output).  The two directions never interact inside the box:
+    on a frame constant along one axis it is that axis's exact 1-D TV prox;
+    in general the output is x minus the sum of the two 1-D corrections.
+
+    ``w0 = (w_h, w_v)`` starts from those duals (the dual warm start);
+    ``return_dual`` / ``return_state`` return (theta, (w_h, w_v))."""
+    if tv != "atv":
+        raise ValueError("the Clip box is an ATV solver")
+    x = np.asarray(x, dtype=np.float64)
+    T = lam if thresh is None else float(thresh)
+    if w0 is None:
+        wh = np.zeros_like(x)
+        wv = np.zeros_like(x)
+    else:
+        wh = np.array(w0[0], dtype=np.float64)
+        wv = np.array(w0[1], dtype=np.float64)
+    for _ in range(S):
+        th_h = x - grad_h_adj(wh)
+        th_v = x - grad_v_adj(wv)
+        wh = np.clip(wh + grad_h(th_h) / alpha, -T, T)
+        wv = np.clip(wv + grad_v(th_v) / alpha, -T, T)
+    theta = x - grad_h_adj(wh) - grad_v_adj(wv)
+    if return_dual or return_state:
+        return theta, (wh, wv)
+    return theta
+
+
 def _tv_denoise(dual: str):
-    """TVdenoise of Algorithm 1: the FGP box or the Chambolle box."""
+    """TVdenoise of Algorithm 1: the FGP, Chambolle or Clip box."""
     if dual == "fgp":
         return fgp_prox
     if dual == "cham":
         return cham_prox
+    if dual == "clip":
+        return clip_prox
     raise ValueError(f"unknown dual solver {dual!r}")
 
 
@@ -353,7 +405,7 @@ def gap_tv(y: np.ndarray, C: np.ndarray, lam: float, T: int, S: int, tv: str,
 
     theta^(0) = Phi^T y unless ``theta0`` is given (resuming).  Each of the T
     iterations projects onto {Phi x = y} and applies the S-step TVdenoise
-    (``dual`` = 'fgp' or 'cham': the FGP or the Chambolle box).
+    (``dual`` = 'fgp', 'cham' or 'clip': the FGP, Chambolle or Clip box).
     ``warm_start=True`` carries the box's w from each TVdenoise call to the
     next (Algorithm 1 initialises w once, before the outer loop); w starts at
     0 in the first call.
