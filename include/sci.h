@@ -62,8 +62,16 @@ typedef enum { SCI_F32 = 0, SCI_BF16 = 1, SCI_F16 = 2 } sci_dtype;
  * reading its D^T as the divergence (minus the adjoint; with the adjoint the
  * printed update ascends).  It is then the same projected dual step as FGP
  * without momentum (nu = 1 throughout), and the ITV2D / VTV forms take the
- * paper's norms for ITV2D-Cham and the ITV3D dual (Eqs. 29-32). */
-typedef enum { SCI_DUAL_FGP = 0, SCI_DUAL_CHAM = 1 } sci_dual_solver;
+ * paper's norms for ITV2D-Cham and the ITV3D dual (Eqs. 29-32).  CLIP: the
+ * ATV-Clip box (iterative clipping; ATV only): theta_h = x - D_h^T w_h,
+ * theta_v = x - D_v^T w_v, w = clip(w + (1/alpha) D theta_dir, T), output
+ * x - D_h^T w_h - D_v^T w_v from the final duals, with alpha = 4 (the bound
+ * on the 1-D difference operator's largest eigenvalue; the box leaves alpha
+ * undefined) and T = lambda (the prox scale of the other boxes; the printed
+ * 2 lambda matches a fidelity without the factor 1/2).  The two directions
+ * do not interact: on a frame constant along one axis the converged box is
+ * that axis's exact 1-D TV prox. */
+typedef enum { SCI_DUAL_FGP = 0, SCI_DUAL_CHAM = 1, SCI_DUAL_CLIP = 2 } sci_dual_solver;
 
 /* Solver parameters (Algorithm 1; Sec. 2.2). */
 typedef struct {
@@ -78,7 +86,18 @@ typedef struct {
                          allows), -1 = one launch per update (no temporal blocking) */
     int init;         /* 1: start from theta = Phi^T y (and u = 0); 0: resume from theta (and u) */
     int use_graph;    /* 1: run the T iterations as one cached CUDA graph; 0: plain launches */
-    int dual;         /* sci_dual_solver of TVdenoise; 0 (FGP) when zero-initialised */
+    int dual;         /* sci_dual_solver of TVdenoise; 0 (FGP) when zero-initialised;
+                         SCI_DUAL_CLIP needs tv = SCI_TV_ATV and is not run by the
+                         batched driver */
+    int warm_start;   /* 1: dual warm start -- each TVdenoise call starts from the dual w
+                         the previous call ended with (Algorithm 1 initialises w once,
+                         before the outer loop; nu is still reset inside the box); 0 (the
+                         default): w = 0 at every call, so TVdenoise is a pure function.
+                         sci_gap_tv and sci_admm_tv on the temporally blocked path only
+                         (SCI_ERR_ARG with fuse_k = -1, VTV with B > 24, FISTA or TwIST).
+                         The carried w lives in the workspace in the storage type: init = 1
+                         starts it at 0, init = 0 resumes from what the previous call on
+                         the same workspace left there. */
 } sci_params;
 
 /* Human-readable name of a status code (static string). */
@@ -140,7 +159,17 @@ sci_status sci_tv_prox_cham(const float* x, int nx, int ny, int B, int tv, float
                             int inner_iters, float* theta, void* work, size_t work_bytes,
                             sci_stream_t stream);
 
-/* Bytes of scratch sci_gap_tv / sci_admm_tv / sci_fista_tv need for these sizes and params. */
+/*
+ * TVdenoise by the ATV-Clip box (Algorithm 1, ATV-Clip; see SCI_DUAL_CLIP):
+ * inner_iters clipping updates from w = 0, then theta = x - D_h^T w_h -
+ * D_v^T w_v.  tv must be SCI_TV_ATV (SCI_ERR_ARG otherwise).  Same arguments,
+ * layouts, workspace (sci_tv_prox_workspace) and errors as sci_tv_prox.
+ */
+sci_status sci_tv_prox_clip(const float* x, int nx, int ny, int B, int tv, float lambda,
+                            int inner_iters, float* theta, void* work, size_t work_bytes,
+                            sci_stream_t stream);
+
+/* Bytes of scratch sci_gap_tv / sci_admm_tv / sci_fista_tv / sci_twist_tv need for these sizes and params. */
 size_t sci_solver_workspace(int nx, int ny, int B, const sci_params* params);
 
 /*
@@ -171,6 +200,29 @@ sci_status sci_gap_tv(const float* y, const uint32_t* bits, int nx, int ny, int 
  * resid (if resid_every > 0) records ||y - Phi x^(t)||^2.
  */
 sci_status sci_fista_tv(const float* y, const uint32_t* bits, int nx, int ny, int B,
+                        const sci_params* params, float* theta, float* x_out,
+                        double* resid, int resid_every, void* work, size_t work_bytes,
+                        sci_stream_t stream);
+
+/*
+ * TwIST-TV (Sec. 2.2, TwIST steps).  The printed unit gradient step needs
+ * ||Phi|| <= 1, so the steps run on Phi / sqrt(L), y / sqrt(L) with L = max_ij
+ * R_ij (as for FISTA): T iterations of
+ *   z = x + (1/L) Phi^T (y - Phi x);  theta = TVdenoise(z);
+ *   x_next = theta (first iteration: one plain step)
+ *   x_next = (1 - alpha) x_prev + (alpha - beta) x + beta theta (later ones).
+ * alpha, beta follow TwIST's rule for the eigenvalue bounds of the normalised
+ * A^T A: xi_m = 1, xi_1 = min_{R > 0} R / max R (the nullspace's zero
+ * eigenvalues are left to the TV term): rho = (1 - sqrt(xi_1)) / (1 +
+ * sqrt(xi_1)), alpha = 1 + rho^2, beta = 2 alpha / (1 + xi_1); they are
+ * formed in FP64 on the device from the mask counts.  TVdenoise takes
+ * params->lambda (as FISTA).  params->init = 1 starts from x = Phi^T y, 0
+ * from the given theta (the two-step recursion restarts).  On return theta
+ * and x_out (if not NULL) hold x^(T); resid (if resid_every > 0) records
+ * ||y - Phi x^(t)||^2 for t = resid_every, 2 resid_every, ...  Same
+ * arguments, workspace (sci_solver_workspace) and errors as sci_gap_tv.
+ */
+sci_status sci_twist_tv(const float* y, const uint32_t* bits, int nx, int ny, int B,
                         const sci_params* params, float* theta, float* x_out,
                         double* resid, int resid_every, void* work, size_t work_bytes,
                         sci_stream_t stream);

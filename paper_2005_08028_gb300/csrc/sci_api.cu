@@ -35,7 +35,7 @@ bool finite_pos(float v) { return std::isfinite(v) && v > 0.f; }
 // update is the same projected step without momentum.
 std::vector<float> momentum_coeffs(int S, int dual = SCI_DUAL_FGP) {
     std::vector<float> c((size_t)std::max(S, 1), 0.f);
-    if (dual == SCI_DUAL_CHAM) return c;
+    if (dual != SCI_DUAL_FGP) return c;  // the Chambolle and Clip boxes have no momentum
     double nu = 1.0;
     for (int s = 0; s < S; ++s) {
         const double nx = (1.0 + std::sqrt(1.0 + 4.0 * nu * nu)) / 2.0;
@@ -47,10 +47,12 @@ std::vector<float> momentum_coeffs(int S, int dual = SCI_DUAL_FGP) {
 
 // ---- workspace layout ----
 struct Layout {
-    size_t rinv, r, partials, xt, p[4], theta_s, theta_s2, u_s, xprev, lmax, total;
+    size_t rinv, r, partials, xt, p[4], theta_s, theta_s2, u_s, xprev, lmax, warm, total;
 };
 
-Layout solver_layout(int nx, int ny, int B, int storage, bool admm) {
+// warm: room for the dual warm start's carried w (two ping-pong pairs of
+// w_h, w_v fields in the storage type).
+Layout solver_layout(int nx, int ny, int B, int storage, bool admm, bool warm = false) {
     Layout L{};
     const size_t n = (size_t)nx * ny, N = n * (size_t)B, es = dtype_bytes(storage);
     Geo g{nx, ny, B, (long long)n};
@@ -67,6 +69,7 @@ Layout solver_layout(int nx, int ny, int B, int storage, bool admm) {
     L.u_s = (storage != SCI_F32 && admm) ? take(N * es) : 0;
     L.xprev = take(N * es);  // FISTA: x^(t-1)
     L.lmax = take(256);      // FISTA: the largest mask count
+    L.warm = warm ? take(4 * N * es) : 0;
     L.total = off;
     return L;
 }
@@ -95,7 +98,9 @@ sci_status validate_params(const sci_params* p, bool admm) {
     if (p->outer_iters < 0 || p->inner_iters < 1) return SCI_ERR_ARG;
     if (p->storage < SCI_F32 || p->storage > SCI_F16) return SCI_ERR_ARG;
     if (p->fuse_k < -1) return SCI_ERR_ARG;
-    if (p->dual != SCI_DUAL_FGP && p->dual != SCI_DUAL_CHAM) return SCI_ERR_ARG;
+    if (p->dual != SCI_DUAL_FGP && p->dual != SCI_DUAL_CHAM && p->dual != SCI_DUAL_CLIP) return SCI_ERR_ARG;
+    if (p->dual == SCI_DUAL_CLIP && p->tv != SCI_TV_ATV) return SCI_ERR_ARG;  // Clip is an ATV box
+    if (p->warm_start != 0 && p->warm_start != 1) return SCI_ERR_ARG;
     return SCI_OK;
 }
 
@@ -108,30 +113,31 @@ sci_status validate_work(void* work, size_t have, size_t need) {
 
 // Dual updates per fused launch: fuse_k = -1 turns temporal blocking off;
 // otherwise the largest count the tile halo allows (halo = K + 1), capped by
-// fuse_k when it is positive, then lowered to the longest launch of an even
-// split of S into ceil(S/K) launches.  Returns 0 when the per-update kernels
-// serve.
+// fuse_k when it is positive.  Returns 0 when the per-update kernels serve.
 int choose_fuse(int tv, int B, int S, int fuse_k) {
     if (fuse_k < 0) return 0;
     const int maxh = fused_max_halo(tv, B);
     if (maxh < 2) return 0;
     int K = std::min(maxh - 1, default_fuse(tv));
     if (fuse_k > 0) K = std::min(fuse_k, maxh - 1);
-    K = std::max(1, std::min(std::min(K, kMaxFuse), S));
-    // the launches split S evenly, so the longest one runs ceil(S / launches)
-    return (S + (S + K - 1) / K - 1) / ((S + K - 1) / K);
+    K = std::min(K, kMaxFuse);
+    return std::max(1, std::min(K, S));
 }
 
-// S dual updates of FGP in ceil(S/K) fused launches whose update counts
-// differ by at most one (S = 10, K = 4: 4 + 3 + 3), so no launch pays a
-// tile's fixed load and store cost for a short tail.
+// Kernel code of the dual-update kernels for this TV form and TVdenoise box.
+int kernel_tv(int tv, int dual) { return dual == SCI_DUAL_CLIP ? kTvClip : tv; }
+
+// S dual updates of FGP in fused launches of K updates each and a last one
+// of the rest (S = 10, K = 6: 6 + 4).  (Even splits such as 4 + 3 + 3 were
+// measured slower in the full solve: each launch pays its tile loads and
+// stores, and the tile count's rounding to whole waves of CTAs decides more
+// than the longest launch.)
 template <typename T>
 int enqueue_fused_prox(int tv, OuterMode mode, int K, int S, float lam, const std::vector<float>& coef,
                        FusedArgs base, FusedBufs<T> bufs, float* x_out_last, cudaStream_t s) {
     int launches = 0;
-    const int n = (S + K - 1) / K;
-    for (int i = 0, s0 = 0; i < n; ++i) {
-        const int k = S / n + (i < S % n ? 1 : 0);
+    for (int s0 = 0; s0 < S;) {
+        const int k = std::min(K, S - s0);
         FusedArgs a = base;
         a.mode = mode;
         a.K = k;
@@ -139,7 +145,7 @@ int enqueue_fused_prox(int tv, OuterMode mode, int K, int S, float lam, const st
         a.first = s0 == 0;
         a.last = s0 + k == S;
         a.lambda = lam;
-        a.step = (float)(1.0 / (8.0 * (double)lam));
+        a.step = (float)(1.0 / ((tv == kTvClip ? kClipAlpha : 8.0) * (double)lam));
         for (int j = 0; j < k; ++j) a.coef[j] = coef[(size_t)(s0 + j)];
         a.x_out = a.last ? x_out_last : nullptr;
         if (!launch_fgp_fused<T>(tv, a, bufs, s)) return -1;
@@ -158,7 +164,8 @@ int enqueue_fused_prox(int tv, OuterMode mode, int K, int S, float lam, const st
 // ---- the outer loop ----
 struct SolveArgs {
     bool admm;
-    bool fista;  // FISTA outer loop (admm is then false)
+    bool fista;  // FISTA or TwIST outer loop (admm is then false)
+    bool twist;  // TwIST's two-step update in place of FISTA's momentum (fista is then true)
     const float* y;
     const uint32_t* bits;
     int nx, ny, B;
@@ -178,7 +185,8 @@ int enqueue_solve(const SolveArgs& A, cudaStream_t s) {
     int nk = 0;
     const Geo g{A.nx, A.ny, A.B, (long long)A.nx * A.ny};
     const long long N = (long long)A.B * g.n;
-    const Layout L = solver_layout(A.nx, A.ny, A.B, A.prm.storage, A.admm);
+    const bool warm = A.prm.warm_start != 0;
+    const Layout L = solver_layout(A.nx, A.ny, A.B, A.prm.storage, A.admm, warm);
     char* w = static_cast<char*>(A.work);
     float* rinv = reinterpret_cast<float*>(w + L.rinv);
     float* r = reinterpret_cast<float*>(w + L.r);
@@ -194,11 +202,17 @@ int enqueue_solve(const SolveArgs& A, cudaStream_t s) {
     T* const theta_home = theta;
 
     T* xprev = reinterpret_cast<T*>(w + L.xprev);
+    unsigned* counts = reinterpret_cast<unsigned*>(w + L.lmax);  // [0] max mask count, [1] smallest nonzero
+    const float* twist_w = reinterpret_cast<const float*>(w + L.lmax + 16);  // TwIST's three weights
     if (A.fista) {
         // z = theta + (1/L) Phi^T (y - Phi theta): the GAP residual with 1/L for 1/R
-        launch_fista_step(A.bits, g, reinterpret_cast<unsigned*>(w + L.lmax), rinv, s);
+        launch_fista_step(A.bits, g, counts, rinv, s);
         launch_zero(xprev, (size_t)N * sizeof(T), s);
         nk += 2;
+        if (A.twist) {
+            launch_twist_coef(A.bits, g, counts, const_cast<float*>(twist_w), s);
+            nk += 2;
+        }
     } else {
         launch_rinv(A.bits, g, A.admm ? A.prm.rho : 0.f, rinv, s);
         ++nk;
@@ -213,6 +227,18 @@ int enqueue_solve(const SolveArgs& A, cudaStream_t s) {
             tau = next;
         }
     }
+    // dual warm start: iteration t reads w from Wm[t % 2] and writes Wm[(t + 1) % 2];
+    // the solve leaves its last w in Wm[0]
+    T* Wm[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    if (warm) {
+        T* wb = reinterpret_cast<T*>(w + L.warm);
+        Wm[0][0] = wb;
+        Wm[0][1] = wb + N;
+        Wm[1][0] = wb + 2 * N;
+        Wm[1][1] = wb + 3 * N;
+        if (A.prm.init) launch_zero(Wm[0][0], (size_t)2 * N * sizeof(T), s);
+    }
+    int wpar = 0;
     if (A.prm.init) {
         launch_adjoint<T>(A.y, A.bits, g, theta, s);
         ++nk;
@@ -239,12 +265,26 @@ int enqueue_solve(const SolveArgs& A, cudaStream_t s) {
             base.g = g;
             base.bits = A.bits;
             base.r = r;
+            base.warm = warm ? 1 : 0;
             FusedBufs<T> fb{theta, u, theta_alt, u, xt,
-                            {P[0], P[0] + N, P[1], P[1] + N}, {P[2], P[2] + N, P[3], P[3] + N}};
-            const int nf = enqueue_fused_prox<T>(A.prm.tv, mode, K, S, lam, coef, base, fb,
+                            {P[0], P[0] + N, P[1], P[1] + N}, {P[2], P[2] + N, P[3], P[3] + N},
+                            {Wm[wpar][0], Wm[wpar][1]}, {Wm[wpar ^ 1][0], Wm[wpar ^ 1][1]}};
+            wpar ^= 1;
+            const int nf = enqueue_fused_prox<T>(kernel_tv(A.prm.tv, A.prm.dual), mode, K, S, lam, coef, base, fb,
                                                  (last && !A.fista) ? A.x_out : nullptr, s);
             if (nf < 0) return -1;
             nk += nf;
+            if (A.twist) {
+                // theta holds x^(t), theta_alt the TVdenoise output; x^(t+1) overwrites x^(t-1)
+                launch_twist_step<T>(xprev, theta, theta_alt, twist_w, N, t == 0, s);
+                ++nk;
+                T* next = xprev;
+                xprev = theta;
+                theta = next;
+                if (metric) { launch_residual_norm<T>(theta, A.y, A.bits, g, partials, resid_slot, s); nk += 2; }
+                if (!last) { launch_residual_field<T>(theta, u, A.y, A.bits, rinv, g, r, s); ++nk; }
+                continue;
+            }
             std::swap(theta, theta_alt);
             if (A.fista) {
                 // theta holds x^(t); the residual metric is of x^(t)
@@ -261,13 +301,15 @@ int enqueue_solve(const SolveArgs& A, cudaStream_t s) {
             if (metric) { launch_residual_norm<T>(theta, A.y, A.bits, g, partials, resid_slot, s); nk += 2; }
             continue;
         }
-        launch_fgp_stream<T>(A.prm.tv, mode, 1, nullptr, theta, r, A.bits, g, lam, 0.f, xt, nullptr, nullptr,
+        launch_fgp_stream<T>(kernel_tv(A.prm.tv, A.prm.dual), mode, 1, nullptr, theta, r, A.bits, g, lam, 0.f, xt,
+                             nullptr, nullptr,
                              P[0], s);
         ++nk;
         int cur = 0, prev = -1;
         for (int it = 1; it < S; ++it) {
             const int out = 3 - cur - (prev < 0 ? (cur == 0 ? 1 : 0) : prev);
-            launch_fgp_stream<T>(A.prm.tv, mode, 0, nullptr, theta, r, A.bits, g, lam, coef[(size_t)it - 1], xt,
+            launch_fgp_stream<T>(kernel_tv(A.prm.tv, A.prm.dual), mode, 0, nullptr, theta, r, A.bits, g, lam,
+                                 coef[(size_t)it - 1], xt,
                                  P[cur], prev >= 0 ? P[prev] : nullptr, P[out], s);
             ++nk;
             prev = cur;
@@ -286,11 +328,22 @@ int enqueue_solve(const SolveArgs& A, cudaStream_t s) {
             launch_cast<T, float>(u, A.x_out, N, s);
             ++nk;
         }
-        launch_fgp_out<T>(oa, xt, P[cur], g, lam, theta, u, s);
+        // TwIST keeps x^(t) beside the TVdenoise output
+        launch_fgp_out<T>(oa, xt, P[cur], g, lam, A.twist ? theta_alt : theta, u, s);
         ++nk;
         if (last && !f32 && A.x_out != nullptr && !A.fista) {
             launch_xt_minus(xt, A.prm.storage, A.x_out, N, A.admm, s);
             ++nk;
+        }
+        if (A.twist) {
+            launch_twist_step<T>(xprev, theta, theta_alt, twist_w, N, t == 0, s);
+            ++nk;
+            T* next = xprev;
+            xprev = theta;
+            theta = next;
+            if (metric) { launch_residual_norm<T>(theta, A.y, A.bits, g, partials, resid_slot, s); nk += 2; }
+            if (!last) { launch_residual_field<T>(theta, u, A.y, A.bits, rinv, g, r, s); ++nk; }
+            continue;
         }
         if (metric) { launch_sum_partials(partials, nparts, resid_slot, s); ++nk; }
         if (A.fista && !last) {
@@ -300,6 +353,8 @@ int enqueue_solve(const SolveArgs& A, cudaStream_t s) {
             nk += 2;
         }
     }
+    if (warm && wpar == 1)
+        cudaMemcpyAsync(Wm[0][0], Wm[1][0], (size_t)2 * N * sizeof(T), cudaMemcpyDeviceToDevice, s);
     if (!f32) {
         launch_cast<T, float>(theta, A.theta, N, s);
         ++nk;
@@ -307,7 +362,8 @@ int enqueue_solve(const SolveArgs& A, cudaStream_t s) {
     } else if (theta != theta_home) {
         cudaMemcpyAsync(theta_home, theta, (size_t)N * sizeof(T), cudaMemcpyDeviceToDevice, s);
     }
-    if ((T_outer == 0 || A.fista) && A.x_out != nullptr)  // FISTA's estimate is x^(T), held in theta
+    // FISTA's and TwIST's estimate is x^(T), held in theta
+    if ((T_outer == 0 || A.fista) && A.x_out != nullptr)
         cudaMemcpyAsync(A.x_out, A.theta, (size_t)N * 4, cudaMemcpyDeviceToDevice, s);
     return nk;
 }
@@ -335,7 +391,7 @@ constexpr size_t kMaxGraphs = 16;
 cudaStream_t g_capture_stream[64] = {};
 
 bool same_args(const SolveArgs& a, const SolveArgs& b) {
-    return a.admm == b.admm && a.fista == b.fista && a.y == b.y && a.bits == b.bits && a.nx == b.nx && a.ny == b.ny &&
+    return a.admm == b.admm && a.fista == b.fista && a.twist == b.twist && a.y == b.y && a.bits == b.bits && a.nx == b.nx && a.ny == b.ny &&
            a.B == b.B && std::memcmp(&a.prm, &b.prm, sizeof(sci_params)) == 0 && a.theta == b.theta &&
            a.u == b.u && a.x_out == b.x_out && a.resid == b.resid && a.resid_every == b.resid_every &&
            a.work == b.work;
@@ -391,17 +447,20 @@ sci_status run_solve(const SolveArgs& A, cudaStream_t stream) {
 sci_status solve_common(bool admm, const float* y, const uint32_t* bits, int nx, int ny, int B,
                         const sci_params* params, float* theta, float* u, float* x_out,
                         double* resid, int resid_every, void* work, size_t work_bytes,
-                        sci_stream_t stream, bool fista = false) {
+                        sci_stream_t stream, bool fista = false, bool twist = false) {
     if (y == nullptr || bits == nullptr || theta == nullptr || (admm && u == nullptr)) return SCI_ERR_ARG;
     if (!sizes_ok(nx, ny, B)) return SCI_ERR_ARG;
     if (B > 32) return SCI_ERR_SHAPE;
     sci_status st = validate_params(params, admm);
     if (st != SCI_OK) return st;
     if (resid_every < 0 || (resid_every > 0 && resid == nullptr)) return SCI_ERR_ARG;
-    const Layout L = solver_layout(nx, ny, B, params->storage, admm);
+    // the dual warm start runs on the temporally blocked path of GAP and ADMM only
+    if (params->warm_start && (fista || twist || choose_fuse(params->tv, B, params->inner_iters, params->fuse_k) == 0))
+        return SCI_ERR_ARG;
+    const Layout L = solver_layout(nx, ny, B, params->storage, admm, params->warm_start != 0);
     st = validate_work(work, work_bytes, L.total);
     if (st != SCI_OK) return st;
-    SolveArgs A{admm, fista, y, bits, nx, ny, B, *params, theta, u, x_out, resid, resid_every, work};
+    SolveArgs A{admm, fista || twist, twist, y, bits, nx, ny, B, *params, theta, u, x_out, resid, resid_every, work};
     return run_solve(A, (cudaStream_t)stream);
 }
 
@@ -470,6 +529,7 @@ static sci_status tv_prox_impl(const float* x, int nx, int ny, int B, int tv, fl
                                float* theta, void* work, size_t work_bytes, sci_stream_t stream, int dual) {
     if (x == nullptr || theta == nullptr || x == theta || !sizes_ok(nx, ny, B)) return SCI_ERR_ARG;
     if (tv < SCI_TV_ATV || tv > SCI_TV_VTV || inner_iters < 1) return SCI_ERR_ARG;
+    if (dual == SCI_DUAL_CLIP && tv != SCI_TV_ATV) return SCI_ERR_ARG;
     if (!std::isfinite(lambda)) return SCI_ERR_NONFINITE;
     if (!finite_pos(lambda)) return SCI_ERR_ARG;
     const Layout L = prox_layout(nx, ny, B);
@@ -490,16 +550,17 @@ static sci_status tv_prox_impl(const float* x, int nx, int ny, int B, int tv, fl
         const size_t N = (size_t)B * nx * ny;
         FusedBufs<float> fb{nullptr, nullptr, nullptr, nullptr, nullptr,
                             {P[0], P[0] + N, P[1], P[1] + N}, {P[2], P[2] + N, P[3], P[3] + N}};
-        if (enqueue_fused_prox<float>(tv, OuterMode::Prox, K, inner_iters, lambda, coef, base, fb, nullptr, s) < 0)
+        if (enqueue_fused_prox<float>(kernel_tv(tv, dual), OuterMode::Prox, K, inner_iters, lambda, coef, base, fb,
+                                      nullptr, s) < 0)
             return SCI_ERR_CUDA;
         return check_launch();
     }
-    launch_fgp_stream<float>(tv, OuterMode::Prox, 1, x, nullptr, nullptr, nullptr, g, lambda, 0.f, nullptr,
-                             nullptr, nullptr, P[0], s);
+    launch_fgp_stream<float>(kernel_tv(tv, dual), OuterMode::Prox, 1, x, nullptr, nullptr, nullptr, g, lambda, 0.f,
+                             nullptr, nullptr, nullptr, P[0], s);
     int cur = 0, prev = -1;
     for (int it = 1; it < inner_iters; ++it) {
         const int out = 3 - cur - (prev < 0 ? (cur == 0 ? 1 : 0) : prev);
-        launch_fgp_stream<float>(tv, OuterMode::Prox, 0, x, nullptr, nullptr, nullptr, g, lambda,
+        launch_fgp_stream<float>(kernel_tv(tv, dual), OuterMode::Prox, 0, x, nullptr, nullptr, nullptr, g, lambda,
                                  coef[(size_t)it - 1], nullptr, P[cur], prev >= 0 ? P[prev] : nullptr, P[out], s);
         prev = cur;
         cur = out;
@@ -522,10 +583,15 @@ sci_status sci_tv_prox_cham(const float* x, int nx, int ny, int B, int tv, float
     return tv_prox_impl(x, nx, ny, B, tv, lambda, inner_iters, theta, work, work_bytes, stream, SCI_DUAL_CHAM);
 }
 
+sci_status sci_tv_prox_clip(const float* x, int nx, int ny, int B, int tv, float lambda, int inner_iters,
+                            float* theta, void* work, size_t work_bytes, sci_stream_t stream) {
+    return tv_prox_impl(x, nx, ny, B, tv, lambda, inner_iters, theta, work, work_bytes, stream, SCI_DUAL_CLIP);
+}
+
 size_t sci_solver_workspace(int nx, int ny, int B, const sci_params* params) {
     if (params == nullptr || !sizes_ok(nx, ny, B)) return 0;
     if (params->storage < SCI_F32 || params->storage > SCI_F16) return 0;
-    return solver_layout(nx, ny, B, params->storage, true).total;
+    return solver_layout(nx, ny, B, params->storage, true, params->warm_start != 0).total;
 }
 
 sci_status sci_gap_tv(const float* y, const uint32_t* bits, int nx, int ny, int B, const sci_params* params,
@@ -547,6 +613,13 @@ sci_status sci_fista_tv(const float* y, const uint32_t* bits, int nx, int ny, in
                         size_t work_bytes, sci_stream_t stream) {
     return solve_common(false, y, bits, nx, ny, B, params, theta, nullptr, x_out, resid, resid_every, work,
                         work_bytes, stream, true);
+}
+
+sci_status sci_twist_tv(const float* y, const uint32_t* bits, int nx, int ny, int B, const sci_params* params,
+                        float* theta, float* x_out, double* resid, int resid_every, void* work,
+                        size_t work_bytes, sci_stream_t stream) {
+    return solve_common(false, y, bits, nx, ny, B, params, theta, nullptr, x_out, resid, resid_every, work,
+                        work_bytes, stream, false, true);
 }
 
 void sci_graph_cache_clear(void) {

@@ -19,7 +19,7 @@ namespace sci {
 // Default dual updates per fused launch (measured on 512x512x10: one-frame
 // tiles run all 10 updates of an outer iteration in one launch; the 32 x 32
 // VTV tiles are fastest at 6, i.e. launches of 6 + 4).
-int default_fuse(int tv) { return tv == SCI_TV_VTV ? 4 : 10; }
+int default_fuse(int tv) { return tv == SCI_TV_VTV ? 6 : 10; }
 
 namespace {
 
@@ -103,7 +103,9 @@ sci_status make_plan(const sci_problem* probs, int count, const sci_params* prm,
     if (!std::isfinite(prm->lambda)) return SCI_ERR_NONFINITE;
     if (!(prm->lambda > 0.f) || prm->outer_iters < 0 || prm->inner_iters < 1) return SCI_ERR_ARG;
     if (prm->storage < SCI_F32 || prm->storage > SCI_F16 || prm->fuse_k < -1) return SCI_ERR_ARG;
+    // the batched driver runs the FGP and Chambolle boxes, without the dual warm start
     if (prm->dual != SCI_DUAL_FGP && prm->dual != SCI_DUAL_CHAM) return SCI_ERR_ARG;
+    if (prm->warm_start != 0) return SCI_ERR_ARG;
     for (int i = 0; i < count; ++i) {
         const sci_problem& p = probs[i];
         if (p.nx <= 0 || p.ny <= 0 || p.B <= 0 || p.y == nullptr || p.bits == nullptr || p.theta == nullptr)
@@ -134,8 +136,6 @@ sci_status make_plan(const sci_problem* probs, int count, const sci_params* prm,
         const int maxh = fused_max_halo(prm->tv, probs[P.order[j]].B);
         int K = prm->fuse_k > 0 ? prm->fuse_k : default_fuse(prm->tv);
         K = std::max(1, std::min(std::min(K, maxh - 1), std::min(prm->inner_iters, kMaxFuse)));
-        const int S = prm->inner_iters, nl = (S + K - 1) / K;
-        K = (S + nl - 1) / nl;  // the longest launch of an even split (and the halo it needs)
         run.K = K;
         run.halo = K + 1;
         int EH = 0, EW = 0;
@@ -237,9 +237,8 @@ int enqueue_batch(const BatchPlan& P, const sci_params* prm, const BatchItem<T>*
         const bool last_outer = t == T_outer - 1;
         for (size_t c = 0; c < P.runs.size(); ++c) {
             const ClassRun& run = P.runs[c];
-            const int nl = (S + run.K - 1) / run.K;  // launches, update counts differing by at most one
-            for (int li = 0, s0 = 0; li < nl; s0 += S / nl + (li < S % nl ? 1 : 0), ++li) {
-                const int k = S / nl + (li < S % nl ? 1 : 0);
+            for (int s0 = 0; s0 < S; s0 += run.K) {
+                const int k = std::min(run.K, S - s0);
                 FusedArgs a{};
                 a.mode = OuterMode::Gap;
                 a.K = k;

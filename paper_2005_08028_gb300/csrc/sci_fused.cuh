@@ -127,7 +127,10 @@ struct FusedCfg {
     static constexpr int A_WH = A_TH + NS * SROW;               // w_h (then p_h) [NS][EW + 2][BLK]
     static constexpr int A_WV = A_WH + NS * SROW;               // w_v (then p_v) of each strip's last row [NS][EW][BLKV]
     static constexpr int A_XT = A_WV + ((NS * EW * BLKV + 3) & ~3);  // x-tilde [NS][EW][BLK] (only when !REG)
-    static constexpr size_t SMEM = (size_t)(A_XT + (REG ? 0 : NS * EW * BLK)) * sizeof(float);
+    static constexpr int A_TV = A_XT + (REG ? 0 : NS * EW * BLK);     // Clip box: theta_v of each strip's
+                                                                       // first row [NS + 1][EW] (one-frame
+                                                                       // tiles; the last row is never written)
+    static constexpr size_t SMEM = (size_t)(A_TV + (F == 1 ? (NS + 1) * EW : 0)) * sizeof(float);
     static_assert(NT % EW == 0, "a CTA must cover whole rows");
     static_assert(EW % 32 == 0, "a warp must stay inside one strip row");
     static_assert(F == 1 ? Q % 4 == 0 : F % 2 == 0, "rows (one frame) or frames pair up for packed arithmetic");
@@ -160,6 +163,8 @@ struct SingleProb {
     __device__ T* xt() const { return b->xt; }
     __device__ const T* st_in(int i) const { return b->st_in[i]; }
     __device__ T* st_out(int i) const { return b->st_out[i]; }
+    __device__ const T* warm_in(int i) const { return b->warm_in[i]; }
+    __device__ T* warm_out(int i) const { return b->warm_out[i]; }
 };
 template <typename T>
 struct BatchProb {
@@ -178,6 +183,8 @@ struct BatchProb {
     __device__ T* xt() const { return it->xt; }
     __device__ const T* st_in(int i) const { return it->st[spar][i]; }
     __device__ T* st_out(int i) const { return it->st[spar ^ 1][i]; }
+    __device__ const T* warm_in(int) const { return nullptr; }  // batched solves start w at 0
+    __device__ T* warm_out(int) const { return nullptr; }
 };
 
 // One tile (bx, by) of frame bz (one-frame tiles) of one problem.  `a`
@@ -210,7 +217,8 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
     constexpr int Q = Cfg::Q, F = Cfg::F, EW = Cfg::EW, EH = Cfg::EH, NS = Cfg::NS, FP = Cfg::FP;
     constexpr int NP = Cfg::NP, BLK = Cfg::BLK, BLKV = Cfg::BLKV, SROW = Cfg::SROW;
     constexpr bool REG = Cfg::REG, SKIP = Cfg::SKIP;
-    static_assert((F == 1) == (TV != SCI_TV_VTV), "one-frame tiles for ATV / ITV2D, frame tiles for VTV");
+    static_assert((F == 1) == (TV != SCI_TV_VTV), "one-frame tiles for ATV / ITV2D / Clip, frame tiles for VTV");
+    constexpr bool CLIP = TV == kTvClip;
 
     const Geo g = p.g();
     const int H = a.halo;
@@ -238,6 +246,7 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
     float* const wv_own = smem + Cfg::A_WV + (strip * EW + col) * BLKV;
     const float* const wv_up = wv_own - EW * BLKV;
     float* const xt_own = smem + Cfg::A_XT + (strip * EW + col) * BLK;  // only when !REG
+    float* const tv_own = smem + Cfg::A_TV + strip * EW + col;           // Clip box only
     const bool has_up = strip > 0, has_down = strip < NS - 1;
 
     // per-row flags as bit masks (bit q: row r0 + q)
@@ -267,6 +276,7 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
     auto pix_of = [&](int q) -> long long { return ((in_m >> q) & 1u) ? pix_top + (long long)q * g.ny : 0; };
     float2 XS[REG ? 1 : NP];  // x-tilde staging for tiles that keep it in shared memory
     auto xe = [&](int q, int f) -> float& { return REG ? el<F>(X, q, f) : el<F>(XS, q, f); };
+    const bool warm_first = a.first && a.warm;  // w from the previous TVdenoise, p = 0
     if (!a.first) {
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
@@ -279,6 +289,18 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
                 el<F>(PV, q, f) = ldraw<T>(p.st_in(1), gidx);
                 el<F>(WH, q, f) = ldraw<T>(p.st_in(2), gidx);
                 el<F>(WV, q, f) = ldraw<T>(p.st_in(3), gidx);
+            }
+        }
+    } else if (warm_first) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const long long pix = pix_of(q);
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                if (f >= nfr) break;
+                const long long gidx = (long long)(f0 + f) * g.n + pix;
+                el<F>(WH, q, f) = ldraw<T>(p.warm_in(0), gidx);
+                el<F>(WV, q, f) = ldraw<T>(p.warm_in(1), gidx);
             }
         }
     }
@@ -333,7 +355,7 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
             }
         }
     }
-    if (!a.first) {
+    if (!a.first || warm_first) {
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
 #pragma unroll
@@ -356,6 +378,8 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
             if (a.first || !live) {
                 el<F>(PH, q, f) = 0.f;
                 el<F>(PV, q, f) = 0.f;
+            }
+            if ((a.first && !a.warm) || !live) {
                 el<F>(WH, q, f) = 0.f;
                 el<F>(WV, q, f) = 0.f;
             }
@@ -412,9 +436,11 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
     for (int s = 0; s < a.K; ++s) {
         const float2 c2 = dup2(a.coef[s]);
         if constexpr (F == 1) {
-            // ---- theta = xt - lambda (D^T w), rows paired ----
+            // ---- theta = xt - lambda (D^T w), rows paired (Clip box: theta_h to
+            //      shared memory, theta_v kept in registers) ----
             const float up_in = wv_up[0];
             const float up = has_up ? up_in : 0.f;
+            float2 THV[CLIP ? NP : 1];
 #pragma unroll
             for (int c = 0; c < Q / 4; ++c) {
                 const float4 wl = lds4(wh_left + 4 * c);
@@ -427,13 +453,19 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
                     const float wu0 = m == 0 ? up : WV[m > 0 ? m - 1 : 0].y;
                     const float2 dv = make_float2(wu0 - WV[m].x, WV[m].x - WV[m].y);
                     const float2 x2 = REG ? X[REG ? m : 0] : (h ? hi2(xv) : lo2(xv));
-                    th[h] = fma2(nlam2, add2(sub2(h ? hi2(wl) : lo2(wl), WH[m]), dv), x2);
+                    if (CLIP) {
+                        th[h] = fma2(nlam2, sub2(h ? hi2(wl) : lo2(wl), WH[m]), x2);
+                        THV[CLIP ? m : 0] = fma2(nlam2, dv, x2);
+                    } else {
+                        th[h] = fma2(nlam2, add2(sub2(h ? hi2(wl) : lo2(wl), WH[m]), dv), x2);
+                    }
                 }
                 sts4(th_own + 4 * c, th[0], th[1]);
             }
+            if (CLIP) tv_own[0] = THV[0].x;
             __syncthreads();
             // ---- a = w + step * D theta, projection, momentum ----
-            const float down_in = th_down[0];
+            const float down_in = CLIP ? tv_own[EW] : th_down[0];  // the next strip's first row
             float4 tcur = lds4(th_own);
 #pragma unroll
             for (int c = 0; c < Q / 4; ++c) {
@@ -447,7 +479,13 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
                     const float2 t0 = h ? hi2(tcur) : lo2(tcur);
                     const float below = h ? below_last : tcur.z;
                     const float2 gh = sub2(h ? hi2(tr) : lo2(tr), t0);
-                    const float2 gv = make_float2(t0.y - t0.x, below - t0.y);
+                    float2 gv = make_float2(t0.y - t0.x, below - t0.y);
+                    if (CLIP) {
+                        const float2 v0 = THV[CLIP ? m : 0];
+                        const float vb = m < NP - 1 ? THV[CLIP && m < NP - 1 ? m + 1 : 0].x
+                                                    : (has_down ? down_in : v0.y);
+                        gv = make_float2(v0.y - v0.x, vb - v0.y);
+                    }
                     float2 sh = steph2, sv = stepv2;
                     if (BORDER) {
                         sh = make_float2(fac(ah_m, 2 * m), fac(ah_m, 2 * m + 1));
@@ -455,7 +493,7 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
                     }
                     float2 ah = fma2(gh, sh, WH[m]);
                     float2 av = fma2(gv, sv, WV[m]);
-                    if (TV == SCI_TV_ATV) {
+                    if (TV == SCI_TV_ATV || CLIP) {
                         ah.x = fminf(fmaxf(ah.x, -1.f), 1.f);
                         ah.y = fminf(fmaxf(ah.y, -1.f), 1.f);
                         av.x = fminf(fmaxf(av.x, -1.f), 1.f);
@@ -467,10 +505,15 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
                         ah = mul2(ah, sc);
                         av = mul2(av, sc);
                     }
-                    WH[m] = fma2(c2, sub2(ah, PH[m]), ah);
-                    WV[m] = fma2(c2, sub2(av, PV[m]), av);
-                    PH[m] = ah;
-                    PV[m] = av;
+                    if (CLIP) {  // no momentum: w = p
+                        WH[m] = ah;
+                        WV[m] = av;
+                    } else {
+                        WH[m] = fma2(c2, sub2(ah, PH[m]), ah);
+                        WV[m] = fma2(c2, sub2(av, PV[m]), av);
+                        PH[m] = ah;
+                        PV[m] = av;
+                    }
                 }
                 sts4(wh_own + 4 * c, WH[2 * c], WH[2 * c + 1]);
                 tcur = tnext;
@@ -566,6 +609,14 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
         }
     }
 
+    if constexpr (CLIP) {  // the Clip box's p is its w
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+            PH[m] = WH[m];
+            PV[m] = WV[m];
+        }
+    }
+
     // ---- epilogue ----
     auto sidx = [&](int q, int f) { return q * FP + f; };  // element (q, f) of a shared block
     if (!a.last) {
@@ -635,6 +686,10 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
             } else {
                 st<T>(p.u_out(), gidx, x0 - rt<T>(th));
                 if (p.x_out() != nullptr) p.x_out()[gidx] = x0 - th_own[sidx(q, f)];
+            }
+            if (a.warm) {
+                st<T>(p.warm_out(0), gidx, el<F>(WH, q, f));
+                st<T>(p.warm_out(1), gidx, el<F>(WV, q, f));
             }
         }
     }
@@ -708,7 +763,7 @@ k_fgp_fused_batched(const __grid_constant__ FusedArgs a, const BatchItem<T>* __r
     }
 }
 
-std::atomic<unsigned long long> g_attr_done[64];
+std::atomic<unsigned long long> g_attr_done[128];
 
 template <typename T, int TV, class Cfg>
 bool launch_cfg(int slot, const FusedArgs& a, const FusedBufs<T>& b, cudaStream_t s) {
@@ -731,10 +786,10 @@ bool launch_cfg(int slot, const FusedArgs& a, const FusedBufs<T>& b, cudaStream_
     return true;
 }
 
-// One "attribute set" flag word per (storage type, TV, configuration).
+// One "attribute set" flag word per (storage type, TV kernel code, configuration).
 template <typename T>
 constexpr int type_slot(int tv, int cfg) {
-    return (std::is_same<T, float>::value ? 0 : (std::is_same<T, __half>::value ? 1 : 2)) * 21 + tv * 7 + cfg;
+    return (std::is_same<T, float>::value ? 0 : (std::is_same<T, __half>::value ? 1 : 2)) * 28 + tv * 7 + cfg;
 }
 
 template <typename T, int TV>
@@ -793,7 +848,7 @@ void fused_class_dims(int cls, int* EH, int* EW) {
 #endif  // SCI_FUSED_COMMON
 
 namespace {
-std::atomic<unsigned long long> g_battr_done[64];
+std::atomic<unsigned long long> g_battr_done[128];
 
 // VTV tiles run one work item per CTA: with the persistent loop their
 // kernels spill (the 24-frame tile by about 0.8 KB a thread); one-frame tiles
@@ -861,6 +916,7 @@ bool launch_fgp_fused(int tv, const FusedArgs& a, const FusedBufs<T>& b, cudaStr
     switch (tv) {
         case SCI_TV_ATV: return launch_tv<T, SCI_TV_ATV>(a, b, s);
         case SCI_TV_ITV2D: return launch_tv<T, SCI_TV_ITV2D>(a, b, s);
+        case kTvClip: return launch_tv<T, kTvClip>(a, b, s);
         default: return launch_tv<T, SCI_TV_VTV>(a, b, s);
     }
 }

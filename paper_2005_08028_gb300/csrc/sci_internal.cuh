@@ -16,6 +16,13 @@ void launch_rinv(const uint32_t* bits, Geo g, float rho, float* rinv, cudaStream
 void launch_fista_step(const uint32_t* bits, Geo g, unsigned* lmax, float* rinv, cudaStream_t s);
 template <typename T>
 void launch_fista_momentum(const T* x, T* x_prev, T* theta_next, long long n, float beta, cudaStream_t s);
+// TwIST (Sec. 2.2): counts[0] = max mask count (launch_fista_step), counts[1]
+// = smallest nonzero count; w3 = (1 - alpha, alpha - beta, beta) on the device.
+// The step overwrites x_prev with x_next.
+void launch_twist_coef(const uint32_t* bits, Geo g, unsigned* counts, float* w3, cudaStream_t s);
+template <typename T>
+void launch_twist_step(T* x_prev, const T* x, const T* theta, const float* w3, long long n, bool first,
+                       cudaStream_t s);
 template <typename T>
 void launch_residual_field(const T* theta, const T* u, const float* y, const uint32_t* bits,
                            const float* rinv, Geo g, float* r, cudaStream_t s);
@@ -37,6 +44,15 @@ void launch_residual_norm(const T* theta, const float* y, const uint32_t* bits, 
 
 // ---- FGP TV prox kernels (sci_fgp.cu) ----
 enum class OuterMode : int { Prox = 0, Gap = 1, Admm = 2 };
+
+// Kernel code for the ATV-Clip box (Algorithm 1), passed where the dual-update
+// kernels take a sci_tv_type.  With the duals scaled by the threshold lambda
+// (|w| <= 1), the box is the ATV dual step without momentum, step
+// 1/(alpha lambda), whose horizontal gradient reads theta_h = xt - lambda
+// D_h^T w_h and vertical one theta_v = xt - lambda D_v^T w_v; its output is
+// the FGP box's, xt - lambda D^T w.
+constexpr int kTvClip = 3;
+constexpr double kClipAlpha = 4.0;
 
 struct FgpFields {
     void* xt;      // x-tilde, the prox input, storage type [B][nx][ny]
@@ -89,6 +105,8 @@ struct FusedArgs {
     int halo;               // top / left tile halo, >= K + 1 (bottom / right: halo - 1)
     int first;              // 1: w = p = 0 and x-tilde formed here (from theta, r or xin)
     int last;               // 1: write theta (and u, x_out); 0: carry p, w (and x-tilde)
+    int warm;               // dual warm start: the first launch starts from w = warm_in (p = 0),
+                            // the last one also writes its final w to warm_out
     float lambda, step;     // lambda and 1/(8 lambda)
     float coef[kMaxFuse];   // momentum coefficients of this launch's updates
     const float* xin;       // Prox mode: the prox input
@@ -110,6 +128,8 @@ struct FusedBufs {
     T* xt;              // x-tilde, written by the first launch, read by later ones
     const T* st_in[4];  // carried p_h, p_v, w_h, w_v (read by non-first launches)
     T* st_out[4];       // must not alias st_in (written by non-last launches)
+    const T* warm_in[2];  // dual warm start: w_h, w_v the previous TVdenoise ended with
+    T* warm_out[2];       // w_h, w_v this TVdenoise ends with (must not alias warm_in)
 };
 // One problem of a batched launch (device-resident table entry).
 template <typename T>

@@ -85,6 +85,55 @@ __global__ void k_fill_step(const unsigned* __restrict__ lmax, Geo g, float* __r
     rinv[pix] = L == 0 ? 0.f : (float)(1.0 / (double)L);
 }
 
+// TwIST's alpha, beta (Sec. 2.2, TwIST steps) for the normalised operator
+// A = Phi / sqrt(L): the eigenvalues of A^T A are 0 (its nullspace) and
+// R_ij / L, so xi_m = 1 and xi_1 = min_{R > 0} R / max R.  k_mask_min_pos
+// takes the smallest nonzero mask count into *cmin (set to ~0 by the
+// caller); k_twist_coef then forms, in FP64 on one thread,
+//   kappa = xi_1, rho = (1 - sqrt(kappa)) / (1 + sqrt(kappa)),
+//   alpha = 1 + rho^2, beta = 2 alpha / (1 + xi_1)
+// and stores the combination weights (1 - alpha, alpha - beta, beta) as FP32.
+__global__ void k_mask_min_pos(const uint32_t* __restrict__ bits, Geo g, unsigned* __restrict__ cmin) {
+    const uint32_t mask = g.B >= 32 ? 0xffffffffu : ((1u << g.B) - 1u);
+    unsigned m = 0xffffffffu;
+    for (long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x; pix < g.n;
+         pix += (long long)gridDim.x * blockDim.x) {
+        const unsigned c = (unsigned)__popc(bits[pix] & mask);
+        if (c > 0) m = min(m, c);
+    }
+    m = __reduce_min_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0) atomicMin(cmin, m);
+}
+
+__global__ void k_twist_coef(const unsigned* __restrict__ lmax, const unsigned* __restrict__ cmin,
+                             float* __restrict__ w3) {
+    const unsigned L = *lmax, c = *cmin;
+    const double xi1 = (L == 0 || c == 0xffffffffu) ? 1.0 : (double)c / (double)L;
+    const double sk = sqrt(xi1);
+    const double rho = (1.0 - sk) / (1.0 + sk);
+    const double alpha = 1.0 + rho * rho;
+    const double beta = 2.0 * alpha / (1.0 + xi1);
+    w3[0] = (float)(1.0 - alpha);
+    w3[1] = (float)(alpha - beta);
+    w3[2] = (float)beta;
+}
+
+// TwIST's two-step update, written over x_prev:
+//   x_next = theta (first iteration: one plain step)
+//   x_next = (1 - alpha) x_prev + (alpha - beta) x + beta theta   (later ones)
+// as fma(beta, theta, fma(alpha - beta, x, (1 - alpha) x_prev)) in FP32.
+template <typename T>
+__global__ void k_twist_step(T* __restrict__ x_prev, const T* __restrict__ x, const T* __restrict__ theta,
+                             const float* __restrict__ w3, long long n, int first) {
+    const float c0 = w3[0], c1 = w3[1], c2 = w3[2];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float th = ld<T>(theta, i);
+        const float xn = first ? th : fmaf(c2, th, fmaf(c1, ld<T>(x, i), c0 * ld<T>(x_prev, i)));
+        st<T>(x_prev, i, xn);
+    }
+}
+
 // FISTA momentum: theta_next = x + beta (x - x_prev), then x_prev = x.
 template <typename T>
 __global__ void k_fista_momentum(const T* __restrict__ x, T* __restrict__ x_prev, T* __restrict__ theta_next,
@@ -234,6 +283,29 @@ void launch_fista_step(const uint32_t* bits, Geo g, unsigned* lmax, float* rinv,
     k_mask_max<<<(unsigned)std::min<long long>(blocks, 152 * 8), threads, 0, s>>>(bits, g, lmax);
     k_fill_step<<<(unsigned)blocks, threads, 0, s>>>(lmax, g, rinv);
 }
+
+void launch_twist_coef(const uint32_t* bits, Geo g, unsigned* counts, float* w3, cudaStream_t s) {
+    const int threads = 256;
+    const long long blocks = (g.n + threads - 1) / threads;
+    cudaMemsetAsync(counts + 1, 0xff, sizeof(unsigned), s);
+    k_mask_min_pos<<<(unsigned)std::min<long long>(blocks, 152 * 8), threads, 0, s>>>(bits, g, counts + 1);
+    k_twist_coef<<<1, 1, 0, s>>>(counts, counts + 1, w3);
+}
+
+template <typename T>
+void launch_twist_step(T* x_prev, const T* x, const T* theta, const float* w3, long long n, bool first,
+                       cudaStream_t s) {
+    const int threads = 256;
+    long long blocks = (n + threads - 1) / threads;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_twist_step<T><<<(unsigned)std::max(blocks, 1LL), threads, 0, s>>>(x_prev, x, theta, w3, n, first ? 1 : 0);
+}
+template void launch_twist_step<float>(float*, const float*, const float*, const float*, long long, bool,
+                                       cudaStream_t);
+template void launch_twist_step<__nv_bfloat16>(__nv_bfloat16*, const __nv_bfloat16*, const __nv_bfloat16*,
+                                               const float*, long long, bool, cudaStream_t);
+template void launch_twist_step<__half>(__half*, const __half*, const __half*, const float*, long long, bool,
+                                        cudaStream_t);
 
 template <typename T>
 void launch_fista_momentum(const T* x, T* x_prev, T* theta_next, long long n, float beta, cudaStream_t s) {

@@ -52,6 +52,8 @@ __global__ void __launch_bounds__(256) k_fgp_stream(StreamArgs a, const T* __res
                                                     T* __restrict__ pout) {
     __shared__ float s_wh[TH + 2][TW + 2], s_wv[TH + 2][TW + 2];  // rows -1..TH, cols -1..TW
     __shared__ float s_x[TH + 1][TW + 1], s_th[TH + 1][TW + 1];   // rows 0..TH, cols 0..TW
+    constexpr bool CLIP = TV == kTvClip;                             // s_th: theta_h, s_tv: theta_v
+    __shared__ float s_tv[CLIP ? TH + 1 : 1][CLIP ? TW + 1 : 1];
     const Geo g = a.g;
     const long long N = (long long)g.B * g.n;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -102,16 +104,32 @@ __global__ void __launch_bounds__(256) k_fgp_stream(StreamArgs a, const T* __res
         for (int e = threadIdx.x; e < (TH + 1) * (TW + 1); e += 256) {
             const int rr = e / (TW + 1), cc = e % (TW + 1);
             float th = s_x[rr][cc];
-            if (!a.first)
+            if (CLIP) {
+                const float x0 = th;
+                if (!a.first) {
+                    th = __fmaf_rn(-a.lambda, s_wh[rr + 1][cc] - s_wh[rr + 1][cc + 1], x0);
+                    s_tv[CLIP ? rr : 0][CLIP ? cc : 0] =
+                        __fmaf_rn(-a.lambda, s_wv[rr][cc + 1] - s_wv[rr + 1][cc + 1], x0);
+                } else {
+                    s_tv[CLIP ? rr : 0][CLIP ? cc : 0] = x0;
+                }
+            } else if (!a.first) {
                 th = __fmaf_rn(-a.lambda,
                                (s_wh[rr + 1][cc] - s_wh[rr + 1][cc + 1]) + (s_wv[rr][cc + 1] - s_wv[rr + 1][cc + 1]), th);
+            }
             s_th[rr][cc] = th;
         }
         __syncthreads();
         // ---- a = w + step D theta at this thread's pixel ----
         const float t0 = s_th[ty][tx];
         const float ah = mh ? fmaf(s_th[ty][tx + 1] - t0, a.step, s_wh[ty + 1][tx + 1]) : 0.f;
-        const float av = mv ? fmaf(s_th[ty + 1][tx] - t0, a.step, s_wv[ty + 1][tx + 1]) : 0.f;
+        float av;
+        if (CLIP) {
+            const float v0 = s_tv[CLIP ? ty : 0][CLIP ? tx : 0];
+            av = mv ? fmaf(s_tv[CLIP ? ty + 1 : 0][CLIP ? tx : 0] - v0, a.step, s_wv[ty + 1][tx + 1]) : 0.f;
+        } else {
+            av = mv ? fmaf(s_th[ty + 1][tx] - t0, a.step, s_wv[ty + 1][tx + 1]) : 0.f;
+        }
         if (a.first && a.mode != OuterMode::Prox && in) st<T>(xt, (long long)f * g.n + mypix, s_x[ty][tx]);
         if (TV == SCI_TV_VTV) {
             ah_r[ff] = ah;
@@ -120,7 +138,7 @@ __global__ void __launch_bounds__(256) k_fgp_stream(StreamArgs a, const T* __res
             else n2e = fmaf(ah, ah, fmaf(av, av, n2e));
         } else if (in) {
             float nh = ah, nv = av;
-            if (TV == SCI_TV_ATV) {
+            if (TV == SCI_TV_ATV || CLIP) {
                 nh = fminf(fmaxf(nh, -1.f), 1.f);
                 nv = fminf(fmaxf(nv, -1.f), 1.f);
             } else {
@@ -167,7 +185,7 @@ void launch_fgp_stream(int tv, OuterMode mode, int first, const float* xin, cons
     a.first = first;
     a.mode = mode;
     a.lambda = lambda;
-    a.step = (float)(1.0 / (8.0 * (double)lambda));
+    a.step = (float)(1.0 / ((tv == kTvClip ? kClipAlpha : 8.0) * (double)lambda));
     a.c = coef;
     a.xin = xin;
     a.bits = bits;
@@ -175,6 +193,7 @@ void launch_fgp_stream(int tv, OuterMode mode, int first, const float* xin, cons
     switch (tv) {
         case SCI_TV_ATV: launch_t<T, SCI_TV_ATV, 1>(a, theta, xt, p, q, pout, s); break;
         case SCI_TV_ITV2D: launch_t<T, SCI_TV_ITV2D, 1>(a, theta, xt, p, q, pout, s); break;
+        case kTvClip: launch_t<T, kTvClip, 1>(a, theta, xt, p, q, pout, s); break;
         default:
             if (g.B <= 16) launch_t<T, SCI_TV_VTV, 16>(a, theta, xt, p, q, pout, s);
             else launch_t<T, SCI_TV_VTV, 32>(a, theta, xt, p, q, pout, s);

@@ -14,7 +14,7 @@ import torch
 
 __all__ = [
     "SciError", "TV", "DTYPE", "DUAL", "load", "sci_masks_pack", "sci_forward", "sci_adjoint",
-    "sci_project", "sci_tv_prox", "sci_gap_tv", "sci_admm_tv", "sci_fista_tv", "sci_sqdiff_f64",
+    "sci_project", "sci_tv_prox", "sci_gap_tv", "sci_admm_tv", "sci_fista_tv", "sci_twist_tv", "sci_sqdiff_f64",
     "sci_residual_f64", "sci_graph_cache_clear", "sci_tv_prox_noalloc", "sci_last_solve_launches", "sci_fused_updates", "Batch", "SciProblem",
     "sci_gap_tv_batched", "sci_last_batch_launches", "ALGO", "sci_tune_fuse", "sci_tune_fuse_batched",
     "sci_conv3d_c32_bf16", "LearnedProx", "sci_gap_tv_lprox", "Workspace", "SciParams",
@@ -39,7 +39,8 @@ class SciError(RuntimeError):
 class SciParams(C.Structure):
     _fields_ = [("tv", C.c_int), ("lam", C.c_float), ("rho", C.c_float),
                 ("outer_iters", C.c_int), ("inner_iters", C.c_int), ("storage", C.c_int),
-                ("fuse_k", C.c_int), ("init", C.c_int), ("use_graph", C.c_int), ("dual", C.c_int)]
+                ("fuse_k", C.c_int), ("init", C.c_int), ("use_graph", C.c_int), ("dual", C.c_int),
+                ("warm_start", C.c_int)]
 
 
 class SciProblem(C.Structure):
@@ -58,9 +59,11 @@ _SIGS = {
     "sci_tv_prox_workspace": (_sz, [_i, _i, _i, _i]),
     "sci_tv_prox": (_i, [_vp, _i, _i, _i, _i, _f, _i, _vp, _vp, _sz, _vp]),
     "sci_tv_prox_cham": (_i, [_vp, _i, _i, _i, _i, _f, _i, _vp, _vp, _sz, _vp]),
+    "sci_tv_prox_clip": (_i, [_vp, _i, _i, _i, _i, _f, _i, _vp, _vp, _sz, _vp]),
     "sci_solver_workspace": (_sz, [_i, _i, _i, C.POINTER(SciParams)]),
     "sci_gap_tv": (_i, [_vp, _vp, _i, _i, _i, C.POINTER(SciParams), _vp, _vp, _vp, _i, _vp, _sz, _vp]),
     "sci_fista_tv": (_i, [_vp, _vp, _i, _i, _i, C.POINTER(SciParams), _vp, _vp, _vp, _i, _vp, _sz, _vp]),
+    "sci_twist_tv": (_i, [_vp, _vp, _i, _i, _i, C.POINTER(SciParams), _vp, _vp, _vp, _i, _vp, _sz, _vp]),
     "sci_admm_tv": (_i, [_vp, _vp, _i, _i, _i, C.POINTER(SciParams), _vp, _vp, _vp, _vp, _i, _vp, _sz,
                          _vp]),
     "sci_graph_cache_clear": (None, []),
@@ -196,14 +199,15 @@ def sci_project(theta: torch.Tensor, y: torch.Tensor, bits: torch.Tensor, rho: f
 def sci_tv_prox(x: torch.Tensor, tv: str, lam: float, inner_iters: int,
                 work: Workspace | None = None, dual: str = "fgp") -> torch.Tensor:
     """TV proximal map with `inner_iters` dual updates: dual='fgp' (Algorithm 1,
-    FGP box; sci_tv_prox) or 'cham' (Chambolle box; sci_tv_prox_cham)."""
+    FGP box; sci_tv_prox), 'cham' (Chambolle box; sci_tv_prox_cham) or 'clip'
+    (ATV-Clip box, tv='atv'; sci_tv_prox_clip)."""
     _need_cuda(x)
     B, nx, ny = x.shape
     lib = load()
     need = lib.sci_tv_prox_workspace(nx, ny, B, TV[tv])
     wbuf = (work or Workspace(x.device)).get(need)
     theta = torch.empty_like(x)
-    name = {"fgp": "sci_tv_prox", "cham": "sci_tv_prox_cham"}[dual]
+    name = {"fgp": "sci_tv_prox", "cham": "sci_tv_prox_cham", "clip": "sci_tv_prox_clip"}[dual]
     _check(name, getattr(lib, name)(_ptr(x), nx, ny, B, TV[tv], float(lam), int(inner_iters),
                                     _ptr(theta), _ptr(wbuf), wbuf.numel(), _stream(x.device)))
     return theta
@@ -225,16 +229,18 @@ def sci_tv_prox_noalloc(x: torch.Tensor, tv: str, lam: float, inner_iters: int) 
     return theta
 
 
-DUAL = {"fgp": 0, "cham": 1}
+DUAL = {"fgp": 0, "cham": 1, "clip": 2}
 
 
-def _params(tv, lam, rho, outer, inner, storage, fuse_k, init, use_graph, dual="fgp"):
+def _params(tv, lam, rho, outer, inner, storage, fuse_k, init, use_graph, dual="fgp", warm_start=False):
     return SciParams(TV[tv], float(lam), float(rho), int(outer), int(inner), DTYPE[storage],
-                     int(fuse_k), int(init), int(use_graph), DUAL[dual])
+                     int(fuse_k), int(init), int(use_graph), DUAL[dual], int(bool(warm_start)))
 
 
 def _solve(admm: bool, y, bits, B, tv, lam, outer, inner, rho=0.0, storage="f32", theta=None, u=None, fista=False,
-           init=None, x_out=None, resid=None, resid_every=0, fuse_k=0, use_graph=True, work=None, dual="fgp"):
+           twist=False,
+           init=None, x_out=None, resid=None, resid_every=0, fuse_k=0, use_graph=True, work=None, dual="fgp",
+           warm_start=False):
     _need_cuda(y, bits, theta, u, x_out, resid)
     nx, ny = y.shape
     dev = y.device
@@ -250,9 +256,11 @@ def _solve(admm: bool, y, bits, B, tv, lam, outer, inner, rho=0.0, storage="f32"
         x_out = torch.empty((B, nx, ny), dtype=torch.float32, device=dev)
     if fuse_k == "tuned":
         from . import tune
+        if twist:
+            raise ValueError("fuse_k='tuned' covers GAP, ADMM and FISTA; pass a depth for TwIST")
         fuse_k = tune.tuned_fuse("admm" if admm else ("fista" if fista else "gap"), y, bits, B, tv, lam, inner,
                                  rho=rho, storage=storage, dual=dual, work=work)
-    prm = _params(tv, lam, rho, outer, inner, storage, fuse_k, init, use_graph, dual)
+    prm = _params(tv, lam, rho, outer, inner, storage, fuse_k, init, use_graph, dual, warm_start)
     lib = load()
     need = lib.sci_solver_workspace(nx, ny, B, C.byref(prm))
     wbuf = (work or Workspace(dev)).get(need)
@@ -264,7 +272,7 @@ def _solve(admm: bool, y, bits, B, tv, lam, outer, inner, rho=0.0, storage="f32"
                              _stream(dev))
         _check("sci_admm_tv", st)
         return x_out, theta, u, resid
-    name = "sci_fista_tv" if fista else "sci_gap_tv"
+    name = "sci_twist_tv" if twist else ("sci_fista_tv" if fista else "sci_gap_tv")
     st = getattr(lib, name)(_ptr(y), _ptr(bits), nx, ny, B, C.byref(prm), _ptr(theta), _ptr(x_out),
                             _ptr(resid), int(resid_every), _ptr(wbuf), wbuf.numel(), _stream(dev))
     _check(name, st)
@@ -279,8 +287,10 @@ def sci_gap_tv(y, bits, B, tv, lam, outer, inner, **kw):
     started at Phi^T y); init; x_out; resid; resid_every; fuse_k (an int, or
     'tuned' for the autotuner's cached choice); use_graph;
     work (a Workspace reused across calls); dual ('fgp' or 'cham', the
-    TVdenoise box of Algorithm 1).  Reusing the same buffers lets
-    the library replay its cached CUDA graph.
+    TVdenoise box of Algorithm 1); warm_start (carry the box's dual w from
+    one TVdenoise call to the next; resuming with init=False continues from
+    the w the previous call left in the same work).  Reusing the same
+    buffers lets the library replay its cached CUDA graph.
     """
     return _solve(False, y, bits, B, tv, lam, outer, inner, **kw)
 
@@ -289,6 +299,13 @@ def sci_fista_tv(y, bits, B, tv, lam, outer, inner, **kw):
     """FISTA-TV (Sec. 2.2; L = max R, same lambda as GAP).  Returns (x^(T), x^(T), resid-or-None);
     keyword arguments as sci_gap_tv."""
     return _solve(False, y, bits, B, tv, lam, outer, inner, fista=True, **kw)
+
+
+def sci_twist_tv(y, bits, B, tv, lam, outer, inner, **kw):
+    """TwIST-TV (Sec. 2.2; steps on Phi / sqrt(L), alpha and beta from the
+    eigenvalue bounds of the normalised Phi^T Phi).  Returns (x^(T), x^(T),
+    resid-or-None); keyword arguments as sci_gap_tv."""
+    return _solve(False, y, bits, B, tv, lam, outer, inner, twist=True, **kw)
 
 
 def sci_admm_tv(y, bits, B, tv, lam, rho, outer, inner, **kw):

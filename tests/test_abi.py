@@ -62,8 +62,11 @@ def test_argument_errors_return_before_any_launch(lib):
     assert lib.sci_gap_tv(fake, fake, 8, 8, 2, C.byref(s0), fake, fake, None, 0, fake, 1 << 30, None) == 1
     tv9 = SciParams(9, 0.05, 0.0, 10, 5, 0, 0, 1, 1)
     assert lib.sci_gap_tv(fake, fake, 8, 8, 2, C.byref(tv9), fake, fake, None, 0, fake, 1 << 30, None) == 1
-    dual7 = SciParams(0, 0.05, 0.0, 10, 5, 0, 0, 1, 1, 7)  # neither FGP (0) nor Chambolle (1)
+    dual7 = SciParams(0, 0.05, 0.0, 10, 5, 0, 0, 1, 1, 7)  # neither FGP (0), Chambolle (1) nor Clip (2)
     assert lib.sci_gap_tv(fake, fake, 8, 8, 2, C.byref(dual7), fake, fake, None, 0, fake, 1 << 30, None) == 1
+    clip_itv = SciParams(1, 0.05, 0.0, 10, 5, 0, 0, 1, 1, 2)  # the Clip box is an ATV solver
+    assert lib.sci_gap_tv(fake, fake, 8, 8, 2, C.byref(clip_itv), fake, fake, None, 0, fake, 1 << 30, None) == 1
+    assert lib.sci_tv_prox_clip(fake, 8, 8, 2, 2, 0.05, 5, C.c_void_p(0x20000), fake, 1 << 30, None) == 1
     assert lib.sci_tv_prox_cham(fake, 8, 8, 2, 0, 0.05, 5, fake, fake, 1 << 30, None) == 1  # x aliases theta
     neg = SciParams(0, 0.05, -0.5, 10, 5, 0, 0, 1, 1)
     assert lib.sci_admm_tv(fake, fake, 8, 8, 2, C.byref(neg), fake, fake, fake, None, 0, fake, 1 << 30,
@@ -82,6 +85,30 @@ def test_argument_errors_return_before_any_launch(lib):
     # projection: negative rho, x aliasing theta
     assert lib.sci_project(fake, None, fake, fake, 8, 8, 2, -1.0, C.c_void_p(0x20000), None) == 1
     assert lib.sci_project(fake, None, fake, fake, 8, 8, 2, 0.0, fake, None) == 1
+
+
+def test_warm_start_arguments(lib):
+    """The dual warm start: 0 or 1; GAP and ADMM on the temporally blocked
+    path only (not FISTA, not fuse_k = -1, not VTV with B > 24); it needs
+    room for two pairs of carried dual fields in the workspace."""
+    from paper_2005_08028_gb300.sci import SciParams
+    fake = C.c_void_p(0x10000)  # never dereferenced: validation fails first
+    big = 1 << 40
+    cold = SciParams(0, 0.05, 0.0, 10, 5, 0, 0, 1, 1, 0, 0)
+    warm = SciParams(0, 0.05, 0.0, 10, 5, 0, 0, 1, 1, 0, 1)
+    two = SciParams(0, 0.05, 0.0, 10, 5, 0, 0, 1, 1, 0, 2)
+    assert lib.sci_gap_tv(fake, fake, 8, 8, 2, C.byref(two), fake, fake, None, 0, fake, big, None) == 1
+    per_update = SciParams(0, 0.05, 0.0, 10, 5, 0, -1, 1, 1, 0, 1)
+    assert lib.sci_gap_tv(fake, fake, 8, 8, 2, C.byref(per_update), fake, fake, None, 0, fake, big, None) == 1
+    assert lib.sci_fista_tv(fake, fake, 8, 8, 2, C.byref(warm), fake, fake, None, 0, fake, big, None) == 1
+    vtv32 = SciParams(2, 0.05, 0.0, 10, 5, 0, 0, 1, 1, 0, 1)
+    assert lib.sci_gap_tv(fake, fake, 8, 8, 32, C.byref(vtv32), fake, fake, None, 0, fake, big, None) == 1
+    N, es = 64 * 48 * 4, 4
+    grow = lib.sci_solver_workspace(64, 48, 4, C.byref(warm)) - lib.sci_solver_workspace(64, 48, 4, C.byref(cold))
+    assert grow >= 4 * N * es
+    need = lib.sci_solver_workspace(64, 48, 4, C.byref(warm))
+    assert lib.sci_admm_tv(fake, fake, 64, 48, 4, C.byref(warm), fake, fake, fake, None, 0, fake, need - 1,
+                           None) == 6
 
 
 def test_workspace_sizes_scale(lib):
@@ -132,27 +159,20 @@ def test_binding_structs_mirror_the_header(cname, pyname):
 
 def test_fuse_depth_planner(lib):
     """Host logic, no GPU: dual updates per temporally blocked launch.  One-frame
-    tiles (ATV, ITV2D) take up to 10 by default; the 32 x 32 VTV tiles of up to
-    10 frames up to 4 (and at most 7: halo <= 8); 16 / 24 frames up to 3 (halo
-    <= 4); more than 24 frames fall back to one launch per update (0).  fuse_k
-    = -1 switches blocking off; fuse_k > 0 caps the depth; S caps it too.  The
-    S updates are split evenly over ceil(S/K) launches, so the depth reported
-    is the longest launch of that split (S = 25, K = 10: 9 + 8 + 8)."""
+    tiles (ATV, ITV2D) take up to 10; the 32 x 32 VTV tiles of up to 10 frames
+    take up to 6 by default (and at most 7: halo <= 8); 16 / 24 frames take up
+    to 3 (halo <= 4); more than 24 frames fall back to one launch per update
+    (0).  fuse_k = -1 switches blocking off; fuse_k > 0 caps the depth; S caps
+    it too."""
     import paper_2005_08028_gb300.sci as s
     q = s.sci_fused_updates
     assert q("atv", 10, 10) == 10 and q("itv2d", 32, 10) == 10
-    assert q("atv", 10, 25) == 9 and q("atv", 10, 4) == 4
-    assert q("vtv", 10, 10) == 4 and q("vtv", 8, 10) == 4 and q("vtv", 10, 5) == 3
+    assert q("atv", 10, 25) == 10 and q("atv", 10, 4) == 4
+    assert q("vtv", 10, 10) == 6 and q("vtv", 8, 10) == 6 and q("vtv", 10, 5) == 5
     assert q("vtv", 16, 10) == 3 and q("vtv", 24, 5) == 3
     assert q("vtv", 25, 10) == 0 and q("vtv", 32, 10) == 0
     assert q("atv", 10, 10, -1) == 0 and q("vtv", 10, 10, -1) == 0
-    assert q("atv", 10, 10, 3) == 3 and q("vtv", 10, 10, 30) == 5  # clamped to the halo (7), then 5 + 5
-    for tv, B in (("atv", 1), ("vtv", 10), ("vtv", 24)):
-        for S in range(1, 26):
-            for k in range(0, S + 1):
-                K = q(tv, B, S, k)
-                n = -(-S // K)
-                assert K == -(-S // n), (tv, B, S, k)  # the longest launch of the even split
+    assert q("atv", 10, 10, 3) == 3 and q("vtv", 10, 10, 30) == 7  # clamped to the halo
 
 
 def _problems(sizes, ptr=0x10000):

@@ -149,11 +149,11 @@ def test_tuned_batch_fuse_keys_the_size_mix(lib, tmp_path):
     cache = tune.FuseCache(str(tmp_path / "f.json"))
     batch = types.SimpleNamespace(ys=[torch.zeros(64, 64), torch.zeros(96, 80)], Bs=[8, 24],
                                   device=torch.device("cpu"))
-    t = FakeTimer(prefer=2)
-    assert tune.tuned_batch_fuse(batch, "vtv", 0.05, 10, cache=cache, timer=t) == 2
+    t = FakeTimer(prefer=4)
+    assert tune.tuned_batch_fuse(batch, "vtv", 0.05, 10, cache=cache, timer=t) == 4
     assert t.calls[0][0] == tune.batch_fuse_candidates("vtv", [8, 24], 10)
     batch.ys.reverse(); batch.Bs.reverse()
-    assert tune.tuned_batch_fuse(batch, "vtv", 0.05, 10, cache=cache, timer=t) == 2
+    assert tune.tuned_batch_fuse(batch, "vtv", 0.05, 10, cache=cache, timer=t) == 4
     assert len(t.calls) == 1
 
 
