@@ -48,7 +48,8 @@ typedef enum {
     SCI_ERR_ARG = 1,        /* null pointer, non-positive size, bad enum, lambda <= 0, ... */
     SCI_ERR_SHAPE = 2,      /* B > 32, or sizes whose element count overflows */
     SCI_ERR_CUDA = 3,       /* a CUDA runtime call or kernel launch failed */
-    SCI_ERR_NONFINITE = 4,  /* non-finite scalar argument */
+    SCI_ERR_NONFINITE = 4,  /* non-finite scalar argument, or non-finite input data when
+                               sci_params.check_input = 1 */
     SCI_ERR_TIMEOUT = 5,    /* reserved: a bounded device-side wait gave up */
     SCI_ERR_WORKSPACE = 6   /* work == NULL, misaligned, or work_bytes too small */
 } sci_status;
@@ -98,6 +99,12 @@ typedef struct {
                          The carried w lives in the workspace in the storage type: init = 1
                          starts it at 0, init = 0 resumes from what the previous call on
                          the same workspace left there. */
+    int check_input;  /* 1: before enqueueing the solve, count the non-finite entries of y
+                         (and of theta, u when init = 0) on the device, synchronise
+                         `stream`, and return SCI_ERR_NONFINITE if there are any (so the
+                         call blocks; SCI_ERR_ARG while `stream` is capturing).  0: no
+                         check (NaN or Inf in y then propagates into the outputs and the
+                         FP64 residual history). */
 } sci_params;
 
 /* Human-readable name of a status code (static string). */

@@ -10,9 +10,14 @@
 //                                                    ADMM: u + x, x from Eq. 24
 //   theta' = FGP prox of xt (S dual updates)
 //   ADMM: u' = u + x - theta' = xt - theta'
-// The projection is folded into the first FGP launch (which forms xt on the
-// fly) and the next residual into the last one, so one outer iteration is
-// S + 1 launches and no separate projection pass.
+// On the temporally blocked path one outer iteration is ceil(S/K) fused
+// launches: the first forms xt = theta + c_k r on the fly (no separate
+// projection pass), the last writes theta' (and u', x).  VTV tiles, which
+// hold every frame of a pixel, also form the next residual r in that last
+// launch; ATV / ITV2D tiles hold one frame, so one light residual pass
+// (128-bit loads) follows their last launch.  The per-update path
+// (fuse_k = -1) runs S launches of one dual update and an output kernel
+// that forms the next residual.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -47,7 +52,7 @@ std::vector<float> momentum_coeffs(int S, int dual = SCI_DUAL_FGP) {
 
 // ---- workspace layout ----
 struct Layout {
-    size_t rinv, r, partials, xt, p[4], theta_s, theta_s2, u_s, xprev, lmax, warm, total;
+    size_t rinv, r, r2, partials, xt, p[4], theta_s, theta_s2, u_s, xprev, lmax, warm, total;
 };
 
 // warm: room for the dual warm start's carried w (two ping-pong pairs of
@@ -60,6 +65,7 @@ Layout solver_layout(int nx, int ny, int B, int storage, bool admm, bool warm = 
     auto take = [&](size_t bytes) { size_t at = off; off += align256(bytes); return at; };
     L.rinv = take(n * 4);
     L.r = take(n * 4);
+    L.r2 = take(n * 4);  // the residual a VTV tile's last launch forms while its first launch read r
     L.partials = take((size_t)std::max(out_partial_count(g), kReduceParts) * 8);
     L.xt = take(N * es);
     for (int b = 0; b < 4; ++b) L.p[b] = take(2 * N * es);  // per-update path uses 3
@@ -68,7 +74,8 @@ Layout solver_layout(int nx, int ny, int B, int storage, bool admm, bool warm = 
                                 // while other CTAs write theta^(t+1)
     L.u_s = (storage != SCI_F32 && admm) ? take(N * es) : 0;
     L.xprev = take(N * es);  // FISTA: x^(t-1)
-    L.lmax = take(256);      // FISTA: the largest mask count
+    L.lmax = take(256);      // words 0-1: largest / smallest nonzero mask count (FISTA, TwIST);
+                             // bytes 16-27: TwIST's weights; bytes 64-67: check_input's count
     L.warm = warm ? take(4 * N * es) : 0;
     L.total = off;
     return L;
@@ -101,7 +108,24 @@ sci_status validate_params(const sci_params* p, bool admm) {
     if (p->dual != SCI_DUAL_FGP && p->dual != SCI_DUAL_CHAM && p->dual != SCI_DUAL_CLIP) return SCI_ERR_ARG;
     if (p->dual == SCI_DUAL_CLIP && p->tv != SCI_TV_ATV) return SCI_ERR_ARG;  // Clip is an ATV box
     if (p->warm_start != 0 && p->warm_start != 1) return SCI_ERR_ARG;
+    if (p->check_input != 0 && p->check_input != 1) return SCI_ERR_ARG;
     return SCI_OK;
+}
+
+// check_input: count the non-finite entries of the solve's input arrays on
+// the device (one word of the workspace), wait for the count, and report it.
+sci_status check_inputs_finite(const float* const* arrays, const long long* sizes, int count, unsigned* word,
+                               cudaStream_t s) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return SCI_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return SCI_ERR_ARG;  // the check must wait on the stream
+    if (cudaMemsetAsync(word, 0, sizeof(unsigned), s) != cudaSuccess) return SCI_ERR_CUDA;
+    for (int i = 0; i < count; ++i)
+        if (arrays[i] != nullptr) launch_count_nonfinite(arrays[i], sizes[i], word, s);
+    unsigned host = 0;
+    if (cudaMemcpyAsync(&host, word, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SCI_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SCI_ERR_CUDA;
+    return host ? SCI_ERR_NONFINITE : SCI_OK;
 }
 
 sci_status validate_work(void* work, size_t have, size_t need) {
@@ -190,6 +214,7 @@ int enqueue_solve(const SolveArgs& A, cudaStream_t s) {
     char* w = static_cast<char*>(A.work);
     float* rinv = reinterpret_cast<float*>(w + L.rinv);
     float* r = reinterpret_cast<float*>(w + L.r);
+    float* r_alt = reinterpret_cast<float*>(w + L.r2);
     double* partials = reinterpret_cast<double*>(w + L.partials);
     T* xt = reinterpret_cast<T*>(w + L.xt);
     T* P[4] = {reinterpret_cast<T*>(w + L.p[0]), reinterpret_cast<T*>(w + L.p[1]),
@@ -266,6 +291,13 @@ int enqueue_solve(const SolveArgs& A, cudaStream_t s) {
             base.bits = A.bits;
             base.r = r;
             base.warm = warm ? 1 : 0;
+            // VTV tiles form the next residual in their last launch (GAP and ADMM)
+            const bool fold_r = !last && !A.fista && fused_class(A.prm.tv, A.B) > 1;
+            if (fold_r) {
+                base.r_next = r_alt;
+                base.y = A.y;
+                base.rinv = rinv;
+            }
             FusedBufs<T> fb{theta, u, theta_alt, u, xt,
                             {P[0], P[0] + N, P[1], P[1] + N}, {P[2], P[2] + N, P[3], P[3] + N},
                             {Wm[wpar][0], Wm[wpar][1]}, {Wm[wpar ^ 1][0], Wm[wpar ^ 1][1]}};
@@ -286,6 +318,7 @@ int enqueue_solve(const SolveArgs& A, cudaStream_t s) {
                 continue;
             }
             std::swap(theta, theta_alt);
+            if (fold_r) std::swap(r, r_alt);
             if (A.fista) {
                 // theta holds x^(t); the residual metric is of x^(t)
                 if (metric) { launch_residual_norm<T>(theta, A.y, A.bits, g, partials, resid_slot, s); nk += 2; }
@@ -297,7 +330,7 @@ int enqueue_solve(const SolveArgs& A, cudaStream_t s) {
                 }
                 continue;
             }
-            if (!last) { launch_residual_field<T>(theta, u, A.y, A.bits, rinv, g, r, s); ++nk; }
+            if (!last && !fold_r) { launch_residual_field<T>(theta, u, A.y, A.bits, rinv, g, r, s); ++nk; }
             if (metric) { launch_residual_norm<T>(theta, A.y, A.bits, g, partials, resid_slot, s); nk += 2; }
             continue;
         }
@@ -460,6 +493,14 @@ sci_status solve_common(bool admm, const float* y, const uint32_t* bits, int nx,
     const Layout L = solver_layout(nx, ny, B, params->storage, admm, params->warm_start != 0);
     st = validate_work(work, work_bytes, L.total);
     if (st != SCI_OK) return st;
+    if (params->check_input) {
+        const long long n = (long long)nx * ny, N = n * B;
+        const float* arrays[3] = {y, params->init ? nullptr : theta, (params->init || !admm) ? nullptr : u};
+        const long long sizes[3] = {n, N, N};
+        st = check_inputs_finite(arrays, sizes, 3, reinterpret_cast<unsigned*>(static_cast<char*>(work) + L.lmax + 64),
+                                 (cudaStream_t)stream);
+        if (st != SCI_OK) return st;
+    }
     SolveArgs A{admm, fista || twist, twist, y, bits, nx, ny, B, *params, theta, u, x_out, resid, resid_every, work};
     return run_solve(A, (cudaStream_t)stream);
 }

@@ -171,13 +171,13 @@ __global__ void k_fgp_out(OutArgs a, const T* __restrict__ xt, const T* __restri
             const float ck = mask_bit(word, k);
             acc_theta += ck * thr;
             if (a.mode == OuterMode::Gap) {
-                acc += ck * thr;
+                acc = __fmaf_rn(ck, thr, acc);
                 if (a.x_out != nullptr) a.x_out[base] = x0;
             } else {
                 const float u_old = ld<T>(u, base);
                 const float u_new = round_trip<T>(x0 - thr);
                 st<T>(u, base, u_new);
-                acc += ck * (thr - u_new);
+                acc = __fmaf_rn(ck, thr - u_new, acc);
                 if (a.x_out != nullptr) a.x_out[base] = x0 - u_old;
             }
         }

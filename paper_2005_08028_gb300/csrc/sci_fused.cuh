@@ -661,11 +661,16 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
         }
     }
     __syncthreads();
+    // VTV tiles hold every frame of a pixel: form the next residual here (the
+    // per-pixel order of the separate residual pass)
+    const bool fold_r = F > 1 && a.r_next != nullptr && a.mode != OuterMode::Prox;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int r = r0 + q;
         if (!((in_m >> q) & 1u) || !col_int || r < H || r >= EH - H + 1) continue;
         const long long pix = (long long)(gi_top + q) * g.ny + gj;
+        const uint32_t word = fold_r ? __ldg(p.bits() + pix) : 0u;
+        float acc = 0.f;
 #pragma unroll
         for (int f = 0; f < F; ++f) {
             if (f >= nfr) break;
@@ -681,17 +686,23 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
                 continue;
             }
             st<T>(p.theta_out(), gidx, th);
+            const float thr = rt<T>(th);
+            float v = thr;
             if (a.mode == OuterMode::Gap) {
                 if (p.x_out() != nullptr) p.x_out()[gidx] = x0;
             } else {
-                st<T>(p.u_out(), gidx, x0 - rt<T>(th));
+                const float un = rt<T>(x0 - thr);
+                st<T>(p.u_out(), gidx, un);
                 if (p.x_out() != nullptr) p.x_out()[gidx] = x0 - th_own[sidx(q, f)];
+                v = thr - un;
             }
+            if (fold_r) acc = __fmaf_rn(mask_bit(word, f0 + f), v, acc);
             if (a.warm) {
                 st<T>(p.warm_out(0), gidx, el<F>(WH, q, f));
                 st<T>(p.warm_out(1), gidx, el<F>(WV, q, f));
             }
         }
+        if (fold_r) a.r_next[pix] = __ldg(a.rinv + pix) * (__ldg(a.y + pix) - acc);
     }
 }
 

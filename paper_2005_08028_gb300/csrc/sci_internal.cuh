@@ -31,6 +31,8 @@ void launch_project(const float* theta, const float* u, const float* y, const ui
 template <typename Tin, typename Tout>
 void launch_cast(const Tin* in, Tout* out, long long count, cudaStream_t s);
 void launch_zero(void* p, size_t bytes, cudaStream_t s);
+// *count += number of NaN / Inf entries of a[0..n)
+void launch_count_nonfinite(const float* a, long long n, unsigned* count, cudaStream_t s);
 // x = xt (sub = false) or x = xt - x (sub = true), xt in the given storage type.
 void launch_xt_minus(const void* xt, int storage, float* x, long long N, bool sub, cudaStream_t s);
 
@@ -114,6 +116,12 @@ struct FusedArgs {
     const uint32_t* bits;   // Gap / Admm: packed masks
     const float* r;         // Gap / Admm: residual field
     float* x_out;           // optional FP32 x^(t+1) (last launch only)
+    // Gap / Admm, last launch of a VTV tile (all frames of a pixel in one
+    // thread): the next projection's residual field r_next = rinv (y - sum_k
+    // c_k (theta'_k - u'_k)) at the tile's interior pixels (null: not formed)
+    float* r_next;
+    const float* y;
+    const float* rinv;
 };
 // Buffers of one fused launch.  A CTA reads its whole extended tile but
 // writes only its interior, so whatever a launch reads from a neighbour's

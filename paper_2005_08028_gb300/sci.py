@@ -40,7 +40,7 @@ class SciParams(C.Structure):
     _fields_ = [("tv", C.c_int), ("lam", C.c_float), ("rho", C.c_float),
                 ("outer_iters", C.c_int), ("inner_iters", C.c_int), ("storage", C.c_int),
                 ("fuse_k", C.c_int), ("init", C.c_int), ("use_graph", C.c_int), ("dual", C.c_int),
-                ("warm_start", C.c_int)]
+                ("warm_start", C.c_int), ("check_input", C.c_int)]
 
 
 class SciProblem(C.Structure):
@@ -232,15 +232,17 @@ def sci_tv_prox_noalloc(x: torch.Tensor, tv: str, lam: float, inner_iters: int) 
 DUAL = {"fgp": 0, "cham": 1, "clip": 2}
 
 
-def _params(tv, lam, rho, outer, inner, storage, fuse_k, init, use_graph, dual="fgp", warm_start=False):
+def _params(tv, lam, rho, outer, inner, storage, fuse_k, init, use_graph, dual="fgp", warm_start=False,
+            check_input=False):
     return SciParams(TV[tv], float(lam), float(rho), int(outer), int(inner), DTYPE[storage],
-                     int(fuse_k), int(init), int(use_graph), DUAL[dual], int(bool(warm_start)))
+                     int(fuse_k), int(init), int(use_graph), DUAL[dual], int(bool(warm_start)),
+                     int(bool(check_input)))
 
 
 def _solve(admm: bool, y, bits, B, tv, lam, outer, inner, rho=0.0, storage="f32", theta=None, u=None, fista=False,
            twist=False,
            init=None, x_out=None, resid=None, resid_every=0, fuse_k=0, use_graph=True, work=None, dual="fgp",
-           warm_start=False):
+           warm_start=False, check_input=False):
     _need_cuda(y, bits, theta, u, x_out, resid)
     nx, ny = y.shape
     dev = y.device
@@ -260,7 +262,7 @@ def _solve(admm: bool, y, bits, B, tv, lam, outer, inner, rho=0.0, storage="f32"
             raise ValueError("fuse_k='tuned' covers GAP, ADMM and FISTA; pass a depth for TwIST")
         fuse_k = tune.tuned_fuse("admm" if admm else ("fista" if fista else "gap"), y, bits, B, tv, lam, inner,
                                  rho=rho, storage=storage, dual=dual, work=work)
-    prm = _params(tv, lam, rho, outer, inner, storage, fuse_k, init, use_graph, dual, warm_start)
+    prm = _params(tv, lam, rho, outer, inner, storage, fuse_k, init, use_graph, dual, warm_start, check_input)
     lib = load()
     need = lib.sci_solver_workspace(nx, ny, B, C.byref(prm))
     wbuf = (work or Workspace(dev)).get(need)
@@ -289,7 +291,9 @@ def sci_gap_tv(y, bits, B, tv, lam, outer, inner, **kw):
     work (a Workspace reused across calls); dual ('fgp' or 'cham', the
     TVdenoise box of Algorithm 1); warm_start (carry the box's dual w from
     one TVdenoise call to the next; resuming with init=False continues from
-    the w the previous call left in the same work).  Reusing the same
+    the w the previous call left in the same work); check_input (count
+    NaN / Inf in y, and theta / u when resuming, on the device first and
+    raise SciError with SCI_ERR_NONFINITE; the call then waits for the GPU).  Reusing the same
     buffers lets the library replay its cached CUDA graph.
     """
     return _solve(False, y, bits, B, tv, lam, outer, inner, **kw)

@@ -221,3 +221,34 @@ def test_batched_workspace_planner(lib):
     prm = s.SciParams(2, 0.05, 0.0, 10, 5, 0, 0, 1, 1, 0)
     assert lib.sci_gap_tv_batched_workspace(_problems([(16, 16, 8)], ptr=None), 1, C.byref(prm)) == 0
     assert lib.sci_gap_tv_batched_workspace(_problems(mix), len(mix), None) == 0
+
+
+def test_fault_injection_on_the_host(lib):
+    """Failures made on the host, before any launch (no GPU needed): an empty
+    batch, one bad descriptor in an otherwise valid mixed batch (a null
+    measurement, B > 32, VTV with B > 24), options the batched driver does not
+    run, and check_input outside {0, 1}.  Each call returns its status
+    without touching the (never dereferenced) device pointers."""
+    import paper_2005_08028_gb300.sci as s
+    fake = C.c_void_p(0x10000)
+    mix = [(128, 128, 8), (256, 256, 8), (37, 70, 10), (48, 40, 24)]
+    prm = s.SciParams(2, 0.05, 0.0, 10, 5, 0, 0, 1, 1, 0, 0, 0)
+    big = 1 << 40
+    assert lib.sci_gap_tv_batched(_problems([]), 0, C.byref(prm), fake, big, None) == 1  # empty batch
+    assert lib.sci_gap_tv_batched_workspace(_problems([]), 0, C.byref(prm)) == 0
+    probs = _problems(mix)
+    probs[2].y = None  # one measurement without data
+    assert lib.sci_gap_tv_batched(probs, len(mix), C.byref(prm), fake, big, None) == 1
+    probs = _problems(mix)
+    probs[1].B = 40  # more frames than a mask word holds
+    assert lib.sci_gap_tv_batched(probs, len(mix), C.byref(prm), fake, big, None) == 2
+    probs = _problems(mix)
+    probs[3].B = 30  # VTV tiles hold at most 24 frames
+    assert lib.sci_gap_tv_batched(probs, len(mix), C.byref(prm), fake, big, None) == 2
+    for fields in ((2, 0.05, 0.0, 10, 5, 0, 0, 1, 1, 0, 1, 0),   # warm start
+                   (2, 0.05, 0.0, 10, 5, 0, 0, 1, 1, 0, 0, 1),   # check_input
+                   (0, 0.05, 0.0, 10, 5, 0, 0, 1, 1, 2, 0, 0)):  # Clip box
+        bad = s.SciParams(*fields)
+        assert lib.sci_gap_tv_batched(_problems(mix), len(mix), C.byref(bad), fake, big, None) == 1, fields
+    chk2 = s.SciParams(0, 0.05, 0.0, 10, 5, 0, 0, 1, 1, 0, 0, 2)
+    assert lib.sci_gap_tv(fake, fake, 8, 8, 2, C.byref(chk2), fake, fake, None, 0, fake, big, None) == 1
