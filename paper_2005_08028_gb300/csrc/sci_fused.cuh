@@ -17,13 +17,18 @@
 // sum inside one thread.  A warp covers 32 consecutive columns of one strip,
 // so global accesses are coalesced and the row tests below are warp-uniform.
 //
-// State: p, w (and, when registers allow, x-tilde and theta) of the owned
-// slots live in registers.  Vertical neighbours inside a strip are register
-// reads; shared memory carries only what other threads read: theta and w_h
-// of every slot (left/right neighbours) and w_v of each strip's last row.
-// No global memory is touched between the updates of one launch.  Where it
-// pays (see the configurations), rows whose results can no longer reach the
-// interior are skipped: the band that matters shrinks by one row per update.
+// State: p, w (and, when registers allow, x-tilde) of the owned slots live
+// in registers.  Vertical neighbours inside a strip are register reads;
+// shared memory carries what other threads read: theta and w_h of every slot
+// (left/right neighbours) and w_v of each strip's last row.  No global memory
+// is touched between the updates of one launch.  Where it pays (see the
+// configurations), rows whose results can no longer reach the interior are
+// skipped: the band that matters shrinks by one row per update.
+//
+// Two implementations: one-frame tiles (fused_tile_rows; ATV, ITV2D and the
+// Clip box) use scalar FP32 arithmetic on row-major shared arrays; VTV tiles
+// (fused_tile_impl) keep each thread's slots in one 128-bit-aligned shared
+// block and run pairs of frames through the packed FP32 instructions.
 //
 // This header holds the implementation; sci_fused_f32.cu, sci_fused_f16.cu and
 // sci_fused_bf16.cu each instantiate it for one storage type (SCI_FUSED_STORAGE),
@@ -118,22 +123,19 @@ struct FusedCfg {
     // right neighbours' blocks with 128-bit loads and edge columns need no
     // tests.  w_v of a strip's last row has blocks of BLKV words (one word for
     // one-frame tiles).
-    static constexpr int FP = F == 1 ? 1 : (F + 3) / 4 * 4;
+    static constexpr int FP = (F + 3) / 4 * 4;
     static constexpr int ES = Q * FP;                           // shared words of a thread's slots
     static constexpr int BLK = block_words(ES);
-    static constexpr int BLKV = F == 1 ? 1 : block_words(FP);
+    static constexpr int BLKV = block_words(FP);
     static constexpr int SROW = (EW + 2) * BLK;                 // one strip of a padded slot array
     static constexpr int A_TH = 0;                              // theta          [NS][EW + 2][BLK]
     static constexpr int A_WH = A_TH + NS * SROW;               // w_h (then p_h) [NS][EW + 2][BLK]
     static constexpr int A_WV = A_WH + NS * SROW;               // w_v (then p_v) of each strip's last row [NS][EW][BLKV]
     static constexpr int A_XT = A_WV + ((NS * EW * BLKV + 3) & ~3);  // x-tilde [NS][EW][BLK] (only when !REG)
-    static constexpr int A_TV = A_XT + (REG ? 0 : NS * EW * BLK);     // Clip box: theta_v of each strip's
-                                                                       // first row [NS + 1][EW] (one-frame
-                                                                       // tiles; the last row is never written)
-    static constexpr size_t SMEM = (size_t)(A_TV + (F == 1 ? (NS + 1) * EW : 0)) * sizeof(float);
+    static constexpr size_t SMEM = (size_t)(A_XT + (REG ? 0 : NS * EW * BLK)) * sizeof(float);
     static_assert(NT % EW == 0, "a CTA must cover whole rows");
     static_assert(EW % 32 == 0, "a warp must stay inside one strip row");
-    static_assert(F == 1 ? Q % 4 == 0 : F % 2 == 0, "rows (one frame) or frames pair up for packed arithmetic");
+    static_assert(F % 2 == 0, "frames pair up for packed arithmetic");
     static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
 };
 
@@ -187,8 +189,7 @@ struct BatchProb {
     __device__ T* warm_out(int) const { return nullptr; }
 };
 
-// One tile (bx, by) of frame bz (one-frame tiles) of one problem.  `a`
-// carries the launch-wide settings (K, halo, first/last, lambda, momentum),
+// One VTV tile (bx, by) of one problem.  `a` carries the launch-wide settings (K, halo, first/last, lambda, momentum),
 // `p` the problem's geometry and buffers.
 //
 // Per dual update (Algorithm 1, ATV-FGP box), in the order of scalar FP32
@@ -200,11 +201,10 @@ struct BatchProb {
 //           (ITV2D); a * min(1, rsqrt(n2_even + n2_odd)) with n2_par = fma(a_h, a_h,
 //           fma(a_v, a_v, n2_par)) over the frames of that parity (VTV)
 //   w     = fma(c, p - p_prev, p)
-// (In the first launch w = 0, and fma(-lambda, 0, xt) = xt exactly.)  One-frame
-// tiles pack pairs of rows of a thread's strip into float2 lanes; VTV tiles
-// pack pairs of frames of one pixel.  VTV tiles always update all F frames:
-// frames B..F-1 hold zeros, their a is zero and they add exact zeros to the
-// norm.
+// (In the first launch w = 0, and fma(-lambda, 0, xt) = xt exactly.)  The
+// tile packs pairs of frames of one pixel into float2 lanes and always
+// updates all F frames: frames B..F-1 hold zeros, their a is zero and they
+// add exact zeros to the norm.
 //
 // BORDER: the tile has rows outside the image or its last row, so the
 // gradient steps carry per-row factors (zero where a difference is not
@@ -217,15 +217,15 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
     constexpr int Q = Cfg::Q, F = Cfg::F, EW = Cfg::EW, EH = Cfg::EH, NS = Cfg::NS, FP = Cfg::FP;
     constexpr int NP = Cfg::NP, BLK = Cfg::BLK, BLKV = Cfg::BLKV, SROW = Cfg::SROW;
     constexpr bool REG = Cfg::REG, SKIP = Cfg::SKIP;
-    static_assert((F == 1) == (TV != SCI_TV_VTV), "one-frame tiles for ATV / ITV2D / Clip, frame tiles for VTV");
-    constexpr bool CLIP = TV == kTvClip;
+    static_assert(F > 1 && TV == SCI_TV_VTV, "frame tiles are for VTV (one-frame tiles: fused_tile_rows)");
 
     const Geo g = p.g();
     const int H = a.halo;
     const int TI = fused_interior(EH, H), TJ = fused_interior(EW, H);  // interior size
     const int gi0 = by * TI - H, gj0 = bx * TJ - H;
-    const int nfr = (F == 1) ? 1 : g.B;          // frames of the problem in this CTA
-    const int f0 = (F == 1) ? bz : 0;            // global frame of slot f = 0
+    const int nfr = g.B;                         // frames of the problem in this CTA
+    constexpr int f0 = 0;                        // global frame of slot f = 0 (bz unused)
+    (void)bz;
     const int tid = threadIdx.x;
     const int col = tid & (EW - 1);
     const int strip = tid >> Cfg::EW_LOG2;
@@ -246,7 +246,6 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
     float* const wv_own = smem + Cfg::A_WV + (strip * EW + col) * BLKV;
     const float* const wv_up = wv_own - EW * BLKV;
     float* const xt_own = smem + Cfg::A_XT + (strip * EW + col) * BLK;  // only when !REG
-    float* const tv_own = smem + Cfg::A_TV + strip * EW + col;           // Clip box only
     const bool has_up = strip > 0, has_down = strip < NS - 1;
 
     // per-row flags as bit masks (bit q: row r0 + q)
@@ -385,32 +384,22 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
             }
         }
     }
-    // Pair (q, f..f+1) of a register array as the 128-bit half it occupies in
-    // a shared block: rows of one-frame tiles pair as (2m, 2m+1) = words 2m..2m+1;
-    // frame tiles pair frames f, f+1 of row q = words q FP + f.
+    // A register pair (frames f, f+1 of row q) is the 128-bit half at words
+    // q FP + f of a shared block; the padding frames of a row store zeros.
     auto put_block = [&](float* blk, const float2* R) {
-        if constexpr (F == 1) {
 #pragma unroll
-            for (int c = 0; c < Q / 4; ++c) sts4(blk + 4 * c, R[2 * c], R[2 * c + 1]);
-        } else {
-#pragma unroll
-            for (int q = 0; q < Q; ++q)
-#pragma unroll
-                for (int c = 0; c < FP / 4; ++c) {
-                    const int e2 = (q * F + 4 * c) / 2;
-                    sts4(blk + q * FP + 4 * c, R[e2], 4 * c + 2 < F ? R[4 * c + 2 < F ? e2 + 1 : 0] : make_float2(0.f, 0.f));
-                }
-        }
-    };
-    auto put_last_row = [&](float* blk, const float2* R) {
-        if constexpr (F == 1) {
-            blk[0] = R[NP - 1].y;
-        } else {
+        for (int q = 0; q < Q; ++q)
 #pragma unroll
             for (int c = 0; c < FP / 4; ++c) {
-                const int e2 = ((Q - 1) * F + 4 * c) / 2;
-                sts4(blk + 4 * c, R[e2], 4 * c + 2 < F ? R[4 * c + 2 < F ? e2 + 1 : 0] : make_float2(0.f, 0.f));
+                const int e2 = (q * F + 4 * c) / 2;
+                sts4(blk + q * FP + 4 * c, R[e2], 4 * c + 2 < F ? R[4 * c + 2 < F ? e2 + 1 : 0] : make_float2(0.f, 0.f));
             }
+    };
+    auto put_last_row = [&](float* blk, const float2* R) {
+#pragma unroll
+        for (int c = 0; c < FP / 4; ++c) {
+            const int e2 = ((Q - 1) * F + 4 * c) / 2;
+            sts4(blk + 4 * c, R[e2], 4 * c + 2 < F ? R[4 * c + 2 < F ? e2 + 1 : 0] : make_float2(0.f, 0.f));
         }
     };
     put_block(wh_own, WH);
@@ -435,186 +424,91 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
 #pragma unroll kUnroll
     for (int s = 0; s < a.K; ++s) {
         const float2 c2 = dup2(a.coef[s]);
-        if constexpr (F == 1) {
-            // ---- theta = xt - lambda (D^T w), rows paired (Clip box: theta_h to
-            //      shared memory, theta_v kept in registers) ----
-            const float up_in = wv_up[0];
-            const float up = has_up ? up_in : 0.f;
-            float2 THV[CLIP ? NP : 1];
+        // rows whose p stays exact after this update: [1 + s, EH - 1 - s);
+        // theta is needed on those rows and the one below
+        const int rlo = 1 + s, rhi = EH - 1 - s;
+        const int qlo = SKIP ? max(rlo - r0, 0) : 0;
+        const int qhi_p = SKIP ? min(rhi - r0, Q) : Q, qhi_t = SKIP ? min(rhi + 1 - r0, Q) : Q;
+        // ---- theta = xt - lambda (D^T w), frames paired ----
 #pragma unroll
-            for (int c = 0; c < Q / 4; ++c) {
-                const float4 wl = lds4(wh_left + 4 * c);
+        for (int q = 0; q < Q; ++q) {
+            if (q < qlo || q >= qhi_t) continue;
+#pragma unroll
+            for (int c = 0; c < FP / 4; ++c) {
+                const float4 wl = lds4(wh_left + q * FP + 4 * c);
                 float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (!REG) xv = lds4(xt_own + 4 * c);
-                float2 th[2];
+                if (!REG) xv = lds4(xt_own + q * FP + 4 * c);
+                float4 wu = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (q == 0) {
+                    const float4 w = lds4(wv_up + 4 * c);
+                    if (has_up) wu = w;
+                }
+                float2 th[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const int m = 2 * c + h;
-                    const float wu0 = m == 0 ? up : WV[m > 0 ? m - 1 : 0].y;
-                    const float2 dv = make_float2(wu0 - WV[m].x, WV[m].x - WV[m].y);
-                    const float2 x2 = REG ? X[REG ? m : 0] : (h ? hi2(xv) : lo2(xv));
-                    if (CLIP) {
-                        th[h] = fma2(nlam2, sub2(h ? hi2(wl) : lo2(wl), WH[m]), x2);
-                        THV[CLIP ? m : 0] = fma2(nlam2, dv, x2);
-                    } else {
-                        th[h] = fma2(nlam2, add2(sub2(h ? hi2(wl) : lo2(wl), WH[m]), dv), x2);
-                    }
+                    if (4 * c + 2 * h >= F) continue;
+                    const int e2 = (q * F + 4 * c) / 2 + h;
+                    const float2 x2 = REG ? X[REG ? e2 : 0] : (h ? hi2(xv) : lo2(xv));
+                    const float2 wu2 = q > 0 ? WV[q > 0 ? e2 - F / 2 : 0] : (h ? hi2(wu) : lo2(wu));
+                    th[h] = fma2(nlam2, add2(sub2(h ? hi2(wl) : lo2(wl), WH[e2]), sub2(wu2, WV[e2])), x2);
                 }
-                sts4(th_own + 4 * c, th[0], th[1]);
+                sts4(th_own + q * FP + 4 * c, th[0], th[1]);
             }
-            if (CLIP) tv_own[0] = THV[0].x;
-            __syncthreads();
-            // ---- a = w + step * D theta, projection, momentum ----
-            const float down_in = CLIP ? tv_own[EW] : th_down[0];  // the next strip's first row
-            float4 tcur = lds4(th_own);
+        }
+        __syncthreads();
+        // ---- a = w + step * D theta (kept in the w registers), norm over frames,
+        //      projection onto the per-pixel ball, momentum ----
 #pragma unroll
-            for (int c = 0; c < Q / 4; ++c) {
-                const float4 tr = lds4(th_right + 4 * c);
-                float4 tnext = tcur;
-                if (c + 1 < Q / 4) tnext = lds4(th_own + 4 * (c + 1));
-                const float below_last = (c + 1 < Q / 4) ? tnext.x : (has_down ? down_in : tcur.w);
+        for (int q = 0; q < Q; ++q) {
+            if (q < qlo || q >= qhi_p) continue;
+            float2 sh = steph2, sv = stepv2;
+            if (BORDER) {
+                sh = dup2(fac(ah_m, q));
+                sv = dup2(fac(av_m, q));
+            }
+            float2 n2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int c = 0; c < FP / 4; ++c) {
+                const float4 tr = lds4(th_right + q * FP + 4 * c);
+                const float4 t0 = lds4(th_own + q * FP + 4 * c);
+                float4 td;
+                if (q < Q - 1) {
+                    td = lds4(th_own + (q + 1) * FP + 4 * c);
+                } else {
+                    const float4 d = lds4(th_down + 4 * c);
+                    td = has_down ? d : t0;
+                }
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const int m = 2 * c + h;
-                    const float2 t0 = h ? hi2(tcur) : lo2(tcur);
-                    const float below = h ? below_last : tcur.z;
-                    const float2 gh = sub2(h ? hi2(tr) : lo2(tr), t0);
-                    float2 gv = make_float2(t0.y - t0.x, below - t0.y);
-                    if (CLIP) {
-                        const float2 v0 = THV[CLIP ? m : 0];
-                        const float vb = m < NP - 1 ? THV[CLIP && m < NP - 1 ? m + 1 : 0].x
-                                                    : (has_down ? down_in : v0.y);
-                        gv = make_float2(v0.y - v0.x, vb - v0.y);
-                    }
-                    float2 sh = steph2, sv = stepv2;
-                    if (BORDER) {
-                        sh = make_float2(fac(ah_m, 2 * m), fac(ah_m, 2 * m + 1));
-                        sv = make_float2(fac(av_m, 2 * m), fac(av_m, 2 * m + 1));
-                    }
-                    float2 ah = fma2(gh, sh, WH[m]);
-                    float2 av = fma2(gv, sv, WV[m]);
-                    if (TV == SCI_TV_ATV || CLIP) {
-                        ah.x = fminf(fmaxf(ah.x, -1.f), 1.f);
-                        ah.y = fminf(fmaxf(ah.y, -1.f), 1.f);
-                        av.x = fminf(fmaxf(av.x, -1.f), 1.f);
-                        av.y = fminf(fmaxf(av.y, -1.f), 1.f);
-                    } else {
-                        // a / max(1, |a|) = a * min(1, 1/|a|); 1/sqrt(0) = inf gives 1
-                        const float2 nn = fma2(ah, ah, mul2(av, av));
-                        const float2 sc = make_float2(fminf(1.f, rsqrt_ftz(nn.x)), fminf(1.f, rsqrt_ftz(nn.y)));
-                        ah = mul2(ah, sc);
-                        av = mul2(av, sc);
-                    }
-                    if (CLIP) {  // no momentum: w = p
-                        WH[m] = ah;
-                        WV[m] = av;
-                    } else {
-                        WH[m] = fma2(c2, sub2(ah, PH[m]), ah);
-                        WV[m] = fma2(c2, sub2(av, PV[m]), av);
-                        PH[m] = ah;
-                        PV[m] = av;
-                    }
-                }
-                sts4(wh_own + 4 * c, WH[2 * c], WH[2 * c + 1]);
-                tcur = tnext;
-            }
-            wv_own[0] = WV[NP - 1].y;
-            __syncthreads();
-        } else {
-            // rows whose p stays exact after this update: [1 + s, EH - 1 - s);
-            // theta is needed on those rows and the one below
-            const int rlo = 1 + s, rhi = EH - 1 - s;
-            const int qlo = SKIP ? max(rlo - r0, 0) : 0;
-            const int qhi_p = SKIP ? min(rhi - r0, Q) : Q, qhi_t = SKIP ? min(rhi + 1 - r0, Q) : Q;
-            // ---- theta = xt - lambda (D^T w), frames paired ----
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                if (q < qlo || q >= qhi_t) continue;
-#pragma unroll
-                for (int c = 0; c < FP / 4; ++c) {
-                    const float4 wl = lds4(wh_left + q * FP + 4 * c);
-                    float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (!REG) xv = lds4(xt_own + q * FP + 4 * c);
-                    float4 wu = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (q == 0) {
-                        const float4 w = lds4(wv_up + 4 * c);
-                        if (has_up) wu = w;
-                    }
-                    float2 th[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        if (4 * c + 2 * h >= F) continue;
-                        const int e2 = (q * F + 4 * c) / 2 + h;
-                        const float2 x2 = REG ? X[REG ? e2 : 0] : (h ? hi2(xv) : lo2(xv));
-                        const float2 wu2 = q > 0 ? WV[q > 0 ? e2 - F / 2 : 0] : (h ? hi2(wu) : lo2(wu));
-                        th[h] = fma2(nlam2, add2(sub2(h ? hi2(wl) : lo2(wl), WH[e2]), sub2(wu2, WV[e2])), x2);
-                    }
-                    sts4(th_own + q * FP + 4 * c, th[0], th[1]);
+                    if (4 * c + 2 * h >= F) continue;
+                    const int e2 = (q * F + 4 * c) / 2 + h;
+                    const float2 tt = h ? hi2(t0) : lo2(t0);
+                    const float2 ah = fma2(sub2(h ? hi2(tr) : lo2(tr), tt), sh, WH[e2]);
+                    const float2 av = fma2(sub2(h ? hi2(td) : lo2(td), tt), sv, WV[e2]);
+                    WH[e2] = ah;
+                    WV[e2] = av;
+                    n2 = fma2(ah, ah, fma2(av, av, n2));
                 }
             }
-            __syncthreads();
-            // ---- a = w + step * D theta (kept in the w registers), norm over frames,
-            //      projection onto the per-pixel ball, momentum ----
+            const float2 vs = dup2(fminf(1.f, rsqrt_ftz(n2.x + n2.y)));
 #pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                if (q < qlo || q >= qhi_p) continue;
-                float2 sh = steph2, sv = stepv2;
-                if (BORDER) {
-                    sh = dup2(fac(ah_m, q));
-                    sv = dup2(fac(av_m, q));
-                }
-                float2 n2 = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int c = 0; c < FP / 4; ++c) {
-                    const float4 tr = lds4(th_right + q * FP + 4 * c);
-                    const float4 t0 = lds4(th_own + q * FP + 4 * c);
-                    float4 td;
-                    if (q < Q - 1) {
-                        td = lds4(th_own + (q + 1) * FP + 4 * c);
-                    } else {
-                        const float4 d = lds4(th_down + 4 * c);
-                        td = has_down ? d : t0;
-                    }
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        if (4 * c + 2 * h >= F) continue;
-                        const int e2 = (q * F + 4 * c) / 2 + h;
-                        const float2 tt = h ? hi2(t0) : lo2(t0);
-                        const float2 ah = fma2(sub2(h ? hi2(tr) : lo2(tr), tt), sh, WH[e2]);
-                        const float2 av = fma2(sub2(h ? hi2(td) : lo2(td), tt), sv, WV[e2]);
-                        WH[e2] = ah;
-                        WV[e2] = av;
-                        n2 = fma2(ah, ah, fma2(av, av, n2));
-                    }
-                }
-                const float2 vs = dup2(fminf(1.f, rsqrt_ftz(n2.x + n2.y)));
-#pragma unroll
-                for (int f = 0; f < F; f += 2) {
-                    const int e2 = (q * F + f) / 2;
-                    const float2 nh = mul2(WH[e2], vs), nv = mul2(WV[e2], vs);
-                    WH[e2] = fma2(c2, sub2(nh, PH[e2]), nh);
-                    WV[e2] = fma2(c2, sub2(nv, PV[e2]), nv);
-                    PH[e2] = nh;
-                    PV[e2] = nv;
-                }
-#pragma unroll
-                for (int c = 0; c < FP / 4; ++c) {
-                    const int e2 = (q * F + 4 * c) / 2;
-                    sts4(wh_own + q * FP + 4 * c, WH[e2],
-                         4 * c + 2 < F ? WH[4 * c + 2 < F ? e2 + 1 : 0] : make_float2(0.f, 0.f));
-                }
+            for (int f = 0; f < F; f += 2) {
+                const int e2 = (q * F + f) / 2;
+                const float2 nh = mul2(WH[e2], vs), nv = mul2(WV[e2], vs);
+                WH[e2] = fma2(c2, sub2(nh, PH[e2]), nh);
+                WV[e2] = fma2(c2, sub2(nv, PV[e2]), nv);
+                PH[e2] = nh;
+                PV[e2] = nv;
             }
-            put_last_row(wv_own, WV);
-            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < FP / 4; ++c) {
+                const int e2 = (q * F + 4 * c) / 2;
+                sts4(wh_own + q * FP + 4 * c, WH[e2],
+                     4 * c + 2 < F ? WH[4 * c + 2 < F ? e2 + 1 : 0] : make_float2(0.f, 0.f));
+            }
         }
-    }
-
-    if constexpr (CLIP) {  // the Clip box's p is its w
-#pragma unroll
-        for (int m = 0; m < NP; ++m) {
-            PH[m] = WH[m];
-            PV[m] = WV[m];
-        }
+        put_last_row(wv_own, WV);
+        __syncthreads();
     }
 
     // ---- epilogue ----
@@ -706,17 +600,327 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
     }
 }
 
+// ---------------------------------------------------------------- one-frame tiles
+//
+// ATV, ITV2D and the Clip box update every frame independently, so a CTA
+// holds one frame of its tile, each thread a vertical strip of Q rows of one
+// column with p, w, x-tilde and theta in registers.  Vertical neighbours are
+// register reads; shared memory carries theta and w_h of every slot (the
+// left / right neighbours) and w_v of each strip's last row, in row-major
+// arrays with one zero pad word at each row end, so edge columns need no
+// tests.  The arithmetic is scalar: packed pairs of rows, tried here, needed
+// aligned register pairs that pushed this 128-register tile into spilling
+// inside the update loop, which cost more than the halved arithmetic issue.
+template <int NT_, int Q_, int EW_LOG2_>
+struct RowCfg {
+    static constexpr int NT = NT_;            // threads per CTA
+    static constexpr int Q = Q_;              // rows per strip (pixels per thread)
+    static constexpr int F = 1;               // one frame per CTA (blockIdx.z picks it)
+    static constexpr int EW_LOG2 = EW_LOG2_;
+    static constexpr int EW = 1 << EW_LOG2;   // tile width (columns)
+    static constexpr int NS = NT / EW;        // strips
+    static constexpr int EH = NS * Q;         // tile height (rows)
+    // slot (r, c) of a slot array sits at 1 + r * LD + c; words 0, LD, 2 LD, ...
+    // are the pad words (zero) left of column 0 and right of column EW - 1
+    static constexpr int LD = EW + 1;
+    static constexpr int FPP = EH * LD + 1;
+    // shared memory: theta, w_h, and (Clip box) theta_v slot arrays [FPP]; w_v [NS][EW]
+    static constexpr size_t SMEM = ((size_t)FPP * 3 + (size_t)NS * EW) * sizeof(float);
+    static_assert(NT % EW == 0, "a CTA must cover whole rows");
+    static_assert(EW % 32 == 0, "a warp must stay inside one strip row");
+};
+
+// One tile (bx, by) of frame bz.  Per dual update, in the scalar order the
+// one-update-per-launch kernel follows (the two agree bit for bit):
+//   theta = fma(-lambda, (w_h,left - w_h) + (w_v,up - w_v), xt)
+//   a_h = fma(theta_right - theta, step_h, w_h), a_v likewise downwards
+//   p = clamp(a, -1, 1) (ATV, Clip) or a * min(1, rsqrt(fma(a_h, a_h, a_v a_v))) (ITV2D)
+//   w = fma(c, p - p_prev, p)  (Clip: w = p)
+// The Clip box (kTvClip) forms theta_h = fma(-lambda, w_h,left - w_h, xt) and
+// theta_v = fma(-lambda, w_v,up - w_v, xt) and takes each direction's
+// gradient of its own theta.
+template <typename T, int TV, class Cfg, class Prob>
+__device__ __forceinline__ void fused_tile_rows(const FusedArgs& a, const Prob& p, int bx, int by, int bz,
+                                                float* smem) {
+    constexpr int Q = Cfg::Q, EW = Cfg::EW, EH = Cfg::EH, NS = Cfg::NS, LD = Cfg::LD, FP = Cfg::FPP;
+    constexpr bool CLIP = TV == kTvClip;
+    float* s_th = smem;                      // [FPP] theta (Clip: theta_h)
+    float* s_wh = s_th + FP;                 // [FPP]
+    float* s_tv = s_wh + FP;                 // [FPP] Clip box: theta_v
+    float* s_wv = s_tv + FP;                 // [NS][EW]: w_v of each strip's last row
+
+    const Geo g = p.g();
+    const int H = a.halo;
+    const int TI = fused_interior(EH, H), TJ = fused_interior(EW, H);
+    const int gi0 = by * TI - H, gj0 = bx * TJ - H;
+    const int f0 = bz;
+    const int tid = threadIdx.x;
+    const int col = tid & (EW - 1);
+    const int strip = tid >> Cfg::EW_LOG2;
+    const int r0 = strip * Q;
+    const int gj = gj0 + col;
+    const bool col_in = gj >= 0 && gj < g.ny;
+    const bool col_int = col >= H && col < EW - H + 1;
+    const int gi_top = gi0 + r0;
+
+    unsigned in_m = 0, ah_m = 0, av_m = 0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int gi = gi_top + q;
+        const bool in = col_in && gi >= 0 && gi < g.nx;
+        in_m |= (unsigned)in << q;
+        ah_m |= (unsigned)(in && gj < g.ny - 1) << q;
+        av_m |= (unsigned)(in && gi < g.nx - 1) << q;
+    }
+    // Strips whose rows all lie inside the image and above its last row need
+    // no row masks (warp-uniform): the column conditions fold into per-thread
+    // steps, zero where the gradient component is defined as zero; w stays
+    // zero there, so the masked and unmasked forms agree.
+    const bool rows_inner = gi_top >= 0 && gi_top + Q - 1 < g.nx - 1;
+    const float step_h = (col_in && gj < g.ny - 1) ? a.step : 0.f;
+    const float step_v = col_in ? a.step : 0.f;
+
+    float ph[Q], pv[Q], wh[Q], wv[Q], xr[Q], thr[Q];
+
+    // ---- loads for the whole extended tile, all issued before any is used ----
+    const long long fbase = (long long)f0 * g.n;
+    const long long pix_top = (long long)gi_top * g.ny + gj;
+    auto pix_of = [&](int q) -> long long { return ((in_m >> q) & 1u) ? pix_top + (long long)q * g.ny : 0; };
+    const bool warm_first = a.first && a.warm;  // w from the previous TVdenoise, p = 0
+    if (!a.first) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const long long gidx = fbase + pix_of(q);
+            ph[q] = ldraw<T>(p.st_in(0), gidx);
+            pv[q] = ldraw<T>(p.st_in(1), gidx);
+            wh[q] = ldraw<T>(p.st_in(2), gidx);
+            wv[q] = ldraw<T>(p.st_in(3), gidx);
+        }
+    } else if (warm_first) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const long long gidx = fbase + pix_of(q);
+            wh[q] = ldraw<T>(p.warm_in(0), gidx);
+            wv[q] = ldraw<T>(p.warm_in(1), gidx);
+        }
+    }
+    if (a.mode == OuterMode::Prox) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) xr[q] = __ldg(p.xin() + fbase + pix_of(q));
+    } else if (a.first) {
+        uint32_t word[Q];
+        float rv[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const long long pix = pix_of(q);
+            word[q] = __ldg(p.bits() + pix);
+            rv[q] = __ldg(p.r() + pix);
+            xr[q] = ldraw<T>(p.theta_in(), fbase + pix);
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) xr[q] = rt<T>(cvraw<T>(xr[q]) + mask_bit(word[q], f0) * rv[q]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) xr[q] = ldraw<T>(p.xt(), fbase + pix_of(q));
+#pragma unroll
+        for (int q = 0; q < Q; ++q) xr[q] = cvraw<T>(xr[q]);
+    }
+    if (!a.first || warm_first) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            ph[q] = cvraw<T>(ph[q]);
+            pv[q] = cvraw<T>(pv[q]);
+            wh[q] = cvraw<T>(wh[q]);
+            wv[q] = cvraw<T>(wv[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const bool in = (in_m >> q) & 1u;
+        if (!in) xr[q] = 0.f;
+        if (a.first || !in) {
+            ph[q] = 0.f;
+            pv[q] = 0.f;
+        }
+        if ((a.first && !a.warm) || !in) {
+            wh[q] = 0.f;
+            wv[q] = 0.f;
+        }
+        s_wh[1 + (r0 + q) * LD + col] = wh[q];
+        if (q == Q - 1) s_wv[strip * EW + col] = wv[q];
+    }
+    for (int e = tid; e < EH + 1; e += Cfg::NT) {  // pad words
+        s_th[e * LD] = 0.f;
+        s_wh[e * LD] = 0.f;
+        s_tv[e * LD] = 0.f;
+    }
+    __syncthreads();
+
+    const float lam = a.lambda, step = a.step;
+    // two updates per loop trip let the compiler alternate registers instead
+    // of copying the loop-carried duals (ITV2D gains; ATV and Clip do not)
+    constexpr int kUnroll = (TV == SCI_TV_ITV2D) ? 2 : 1;
+#pragma unroll kUnroll
+    for (int s = 0; s < a.K; ++s) {
+        const bool skip_theta = a.first && !a.warm && s == 0;  // w = 0 there: theta = xt
+        // ---- theta = xt - lambda (D^T w) ----
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int o = 1 + (r0 + q) * LD + col;
+            float th = xr[q], tv = xr[q];
+            if (!skip_theta) {
+                const float wl = s_wh[o - 1];
+                float wu;
+                if (q > 0) wu = wv[q > 0 ? q - 1 : 0];
+                else wu = strip > 0 ? s_wv[(strip - 1) * EW + col] : 0.f;
+                if (CLIP) {
+                    th = __fmaf_rn(-lam, wl - wh[q], xr[q]);
+                    tv = __fmaf_rn(-lam, wu - wv[q], xr[q]);
+                } else {
+                    th = __fmaf_rn(-lam, (wl - wh[q]) + (wu - wv[q]), xr[q]);
+                }
+            }
+            thr[q] = th;
+            s_th[o] = th;
+            if (CLIP) s_tv[o] = tv;
+        }
+        __syncthreads();
+        // ---- a = w + step * D theta, projection, momentum ----
+        const float c = a.coef[s];
+        auto dual_step = [&](auto masked_c) {
+            constexpr bool MASKED = decltype(masked_c)::value;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const bool mh = (ah_m >> q) & 1u, mv = (av_m >> q) & 1u;
+                const int o = 1 + (r0 + q) * LD + col;
+                const float t0 = thr[q];
+                const float tr = s_th[o + 1];
+                float dv;
+                if (CLIP) {
+                    const float v0 = s_tv[o];
+                    const float vd = (r0 + q < EH - 1) ? s_tv[o + LD] : v0;
+                    dv = vd - v0;
+                } else {
+                    float td;
+                    if (q < Q - 1) td = thr[q < Q - 1 ? q + 1 : 0];
+                    else td = (r0 + q < EH - 1) ? s_th[o + LD] : t0;
+                    dv = td - t0;
+                }
+                float ah, av;
+                if (MASKED) {
+                    ah = mh ? fmaf(tr - t0, step, wh[q]) : 0.f;
+                    av = mv ? fmaf(dv, step, wv[q]) : 0.f;
+                } else {
+                    ah = fmaf(tr - t0, step_h, wh[q]);
+                    av = fmaf(dv, step_v, wv[q]);
+                }
+                if (TV == SCI_TV_ATV || CLIP) {
+                    ah = fminf(fmaxf(ah, -1.f), 1.f);
+                    av = fminf(fmaxf(av, -1.f), 1.f);
+                } else {
+                    // a / max(1, |a|) = a * min(1, 1/|a|); 1/sqrt(0) = inf gives 1
+                    const float sc = fminf(1.f, rsqrt_ftz(fmaf(ah, ah, av * av)));
+                    ah *= sc;
+                    av *= sc;
+                }
+                if (CLIP) {
+                    wh[q] = ah;
+                    wv[q] = av;
+                } else {
+                    wh[q] = fmaf(c, ah - ph[q], ah);
+                    wv[q] = fmaf(c, av - pv[q], av);
+                }
+                ph[q] = ah;
+                pv[q] = av;
+                s_wh[o] = wh[q];
+                if (q == Q - 1) s_wv[strip * EW + col] = wv[q];
+            }
+        };
+        if (rows_inner) dual_step(std::false_type{});
+        else dual_step(std::true_type{});
+        __syncthreads();
+    }
+
+    // ---- epilogue ----
+    if (!a.last) {
+        // carry x-tilde (first launch of a solve), p and w of the interior
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int r = r0 + q;
+            if (!((in_m >> q) & 1u) || !col_int || r < H || r >= EH - H + 1) continue;
+            const long long gidx = fbase + (long long)(gi_top + q) * g.ny + gj;
+            if (a.first && a.mode != OuterMode::Prox) st<T>(p.xt(), gidx, xr[q]);
+            st<T>(p.st_out(0), gidx, ph[q]);
+            st<T>(p.st_out(1), gidx, pv[q]);
+            st<T>(p.st_out(2), gidx, wh[q]);
+            st<T>(p.st_out(3), gidx, wv[q]);
+        }
+        return;
+    }
+    // theta = xt - lambda D^T p needs p_h of the left neighbour and p_v of the
+    // row above: stage them where w_h / w_v were (the loop ended with a barrier).
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        s_wh[1 + (r0 + q) * LD + col] = ph[q];
+        if (q == Q - 1) s_wv[strip * EW + col] = pv[q];
+    }
+    // x^(t+1) = xt - u^(t) for ADMM (only when x is requested): u^(t) is read
+    // before u^(t+1) overwrites it, into the thread's own theta slots (free now)
+    if (a.mode == OuterMode::Admm && p.x_out() != nullptr) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int r = r0 + q;
+            const bool mine = ((in_m >> q) & 1u) && col_int && r >= H && r < EH - H + 1;
+            const long long pix = mine ? (long long)(gi_top + q) * g.ny + gj : 0;
+            s_th[1 + r * LD + col] = mine ? ldg<T>(p.u_in(), fbase + pix) : 0.f;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int r = r0 + q;
+        if (!((in_m >> q) & 1u) || !col_int || r < H || r >= EH - H + 1) continue;
+        const int o = 1 + r * LD + col;
+        const float pl = s_wh[o - 1];
+        float pu;
+        if (q > 0) pu = pv[q > 0 ? q - 1 : 0];
+        else pu = strip > 0 ? s_wv[(strip - 1) * EW + col] : 0.f;
+        const float x0 = xr[q];
+        const float th = __fmaf_rn(-lam, (pl - ph[q]) + (pu - pv[q]), x0);
+        const long long gidx = fbase + (long long)(gi_top + q) * g.ny + gj;
+        if (a.mode == OuterMode::Prox) {
+            p.theta_f32()[gidx] = th;
+            continue;
+        }
+        st<T>(p.theta_out(), gidx, th);
+        if (a.mode == OuterMode::Gap) {
+            if (p.x_out() != nullptr) p.x_out()[gidx] = x0;
+        } else {
+            st<T>(p.u_out(), gidx, x0 - rt<T>(th));
+            if (p.x_out() != nullptr) p.x_out()[gidx] = x0 - s_th[o];
+        }
+        if (a.warm) {
+            st<T>(p.warm_out(0), gidx, wh[q]);
+            st<T>(p.warm_out(1), gidx, wv[q]);
+        }
+    }
+}
+
 // A tile all of whose rows lie inside the image and above its last row runs
 // the interior form; the others the border form.
 template <typename T, int TV, class Cfg, class Prob>
 __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, int bx, int by, int bz,
                                            float* smem) {
-    const Geo g = p.g();
-    const int gi0 = by * fused_interior(Cfg::EH, a.halo) - a.halo;
-    if (gi0 >= 0 && gi0 + Cfg::EH - 1 < g.nx - 1)
-        fused_tile_impl<T, TV, Cfg, false>(a, p, bx, by, bz, smem);
-    else
-        fused_tile_impl<T, TV, Cfg, true>(a, p, bx, by, bz, smem);
+    if constexpr (Cfg::F == 1) {
+        fused_tile_rows<T, TV, Cfg>(a, p, bx, by, bz, smem);
+    } else {
+        const Geo g = p.g();
+        const int gi0 = by * fused_interior(Cfg::EH, a.halo) - a.halo;
+        if (gi0 >= 0 && gi0 + Cfg::EH - 1 < g.nx - 1)
+            fused_tile_impl<T, TV, Cfg, false>(a, p, bx, by, bz, smem);
+        else
+            fused_tile_impl<T, TV, Cfg, true>(a, p, bx, by, bz, smem);
+    }
 }
 
 // ---------------------------------------------------------------- configurations
@@ -724,8 +928,8 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
 // One-frame tiles (16-row strips) update every row: skipping rows would idle
 // whole strips and stall the others at the barriers.  The VTV tiles have
 // 1- or 2-row strips, where skipping balances well and saves work.
-using CfgF1 = FusedCfg<512, 16, 1, 7, true, false>;    // 128 x 64 tile, one frame
-using CfgF1s = FusedCfg<256, 8, 1, 6, true, false>;    // 64 x 32 tile, one frame (small images)
+using CfgF1 = RowCfg<512, 16, 7>;    // 128 x 64 tile, one frame
+using CfgF1s = RowCfg<256, 8, 6>;    // 64 x 32 tile, one frame (small images)
 using CfgV8 = FusedCfg<512, 2, 8, 5, true, true>;      // 32 x 32 tile, up to 8 frames
 using CfgV10 = FusedCfg<512, 2, 10, 5, false, true>;   // 32 x 32 tile, up to 10 frames
 using CfgV16 = FusedCfg<256, 2, 16, 5, false, true>;   // 32 x 16 tile, up to 16 frames
