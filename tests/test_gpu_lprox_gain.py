@@ -49,19 +49,33 @@ def _measurements(pkg, count, seed, size=(128, 128, 8)):
     return cases, torch.stack(ys), torch.stack(bits)
 
 
-def test_learned_gap_tv_against_plain(pkg_mod, trained):
+def test_learned_gap_tv_gain(pkg_mod, trained):
+    """What the trained network gains, on held-out measurements (T = 30 outer
+    iterations, no fallback checks):
+    - over the method without a denoiser (the projection of Phi^T y alone,
+      which further GAP iterations leave unchanged): at least 3 dB;
+    - against the 10 FGP updates it stands in for, at equal outer iterations:
+      within 0.3 dB either way.
+    At equal wall time it does not pay: one application costs about 114 kFLOP
+    per voxel on the tensor cores against about 200 FP32 operations for 10
+    FGP updates (the benchmark's learned section reports both rates)."""
     pkg, _ = pkg_mod
     net = trained[0]
     cases, y, bits = _measurements(pkg, 4, 5100)
     B, T = 8, 30
     x_l, _, fell, _ = pkg.sci_gap_tv_lprox(net, y, bits, B, T)
-    ps_l, ps_p = [], []
+    ps_l, ps_p, ps_0 = [], [], []
     for k, c in enumerate(cases):
         x_p, _, _ = pkg.sci_gap_tv(y[k].contiguous(), bits[k].contiguous(), B, "vtv", 0.05, T, 10)
+        y64 = y[k].cpu().numpy().astype(np.float64)
+        x_0 = O.gap_project(O.adjoint(y64, c.masks), y64, c.masks)
         ps_l.append(O.psnr(x_l[k].cpu().numpy(), c.x_gt))
         ps_p.append(O.psnr(x_p.cpu().numpy(), c.x_gt))
-    # the learned prox keeps the reconstruction within 1 dB of plain GAP-TV
-    assert np.mean(ps_l) >= np.mean(ps_p) - 1.0, (ps_l, ps_p)
+        ps_0.append(O.psnr(x_0, c.x_gt))
+    gain_none = float(np.mean(ps_l) - np.mean(ps_0))
+    gain_fgp = float(np.mean(ps_l) - np.mean(ps_p))
+    assert gain_none >= 3.0, (ps_l, ps_0)
+    assert abs(gain_fgp) <= 0.3, (ps_l, ps_p)
     assert not any(fell)
 
 
