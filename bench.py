@@ -859,7 +859,8 @@ def _learned(pkg, torch, dev, stream, flush):
     flush.zero_()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    x_l, _, fell, _ = pkg.sci_gap_tv_lprox(net, y, bits, 10, T, check_every=every, resid_limit=limit, work=work)
+    x_l, _, fell, hist_l = pkg.sci_gap_tv_lprox(net, y, bits, 10, T, check_every=every, resid_limit=limit,
+                                                work=work)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms_l = e0.elapsed_time(e1)
@@ -888,6 +889,22 @@ def _learned(pkg, torch, dev, stream, flush):
         return float(np.mean(ps))
 
     p_l, p_p = mean_psnr([x_l[k] for k in range(64)]), mean_psnr(xo)
+    # The fallback rule's behaviour: plain GAP-TV's own residual curves on the
+    # same 64 measurements (untimed), against the calibration band, and the
+    # learned run's residual over plain's at each checkpoint.
+    curves_t = []
+    for k in range(64):
+        _, _, r = pkg.sci_gap_tv(y[k].contiguous(), bits[k].contiguous(), 10, "vtv", lam, T, S, resid_every=every,
+                                 theta=th, work=pw)
+        curves_t.append(r.cpu().numpy())
+    Pc, Lc, cal = np.array(curves_t), np.array(hist_l), np.array(curves)
+    diag = {"calibration_spread_rel": round(float((cal.std(axis=0) / cal.mean(axis=0)).max()), 4),
+            "plain_outside_band": int(((Pc / np.array(limit)) > 1.05).any(axis=1).sum()),
+            "learned_outside_band": int(((Lc / np.array(limit)) > 1.05).any(axis=1).sum()),
+            "learned_over_plain_residual_mean": [round(float(v), 4) for v in (Lc / Pc).mean(axis=0)],
+            "learned_over_plain_residual_max": round(float((Lc / Pc).max()), 4),
+            "reading": "the 5% band is narrower than the residual's spread across videos and than the "
+                       "learned/plain residual gap on the same measurement at equal PSNR"}
     # tensor-core conv throughput on activations of this size
     act = torch.randn((64, 10, 512, 512, 32), device=dev).to(torch.bfloat16)
     wt = (0.05 * torch.randn((27, 32, 32), device=dev)).to(torch.bfloat16)
@@ -908,6 +925,7 @@ def _learned(pkg, torch, dev, stream, flush):
                       "heldout_mse_vs_identity": round(mse_net / mse_id, 4)},
             "learned": {"value": N * T / (ms_l * 1e-3), "unit": UNIT, "ms": round(ms_l, 1),
                         "mean_psnr_db": round(p_l, 4), "fallbacks": int(sum(fell))},
+            "fallback_diagnostics": diag,
             "plain_f32": {"value": N * T / (ms_p * 1e-3), "unit": UNIT, "ms": round(ms_p, 1),
                           "mean_psnr_db": round(p_p, 4)},
             "psnr_delta_learned_vs_plain_db": round(p_l - p_p, 4),
