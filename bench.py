@@ -732,18 +732,20 @@ def _fista(pkg, torch, dev, stream, flush, c, y, bits, x_gt, psnr_gap):
 
 
 def _fuse_tuning(pkg, c, y, bits):
-    """sci_tune_fuse on each of the six reconstructions (4 outer iterations per
-    probe, median of 5 CUDA-event timings): per-candidate ms, the chosen
-    depth and the library default.  A failure is reported in the section."""
+    """sci_tune_launch on each of the six reconstructions: every (fuse depth,
+    tile class) pair the library can run (4 outer iterations per probe, median
+    of 5 CUDA-event timings), the chosen pair and the library default (0, 0).
+    A failure is reported in the section."""
     from paper_2005_08028_gb300 import tune
-    out = {"probe": "4 outer iterations, median of 5, ms per probe"}
+    out = {"probe": "4 outer iterations, median of 5, ms per probe; keys are 'fuse_k@tile'"}
     try:
         for algo, tv in COMBOS:
-            cands = tune.fuse_candidates(tv, c["B"], c["inner"])
-            best, ms = pkg.sci_tune_fuse(algo, y, bits, c["B"], tv, c["lam"], c["inner"], cands,
-                                         rho=c["rho"] if algo == "admm" else 0.0, probe_iters=4, reps=5)
-            out[f"{algo}_{tv}"] = {"best": best, "default": cands[0],
-                                   "ms": {str(k): round(m, 4) for k, m in zip(cands, ms)}}
+            cands = tune.launch_candidates(tv, c["B"], c["inner"])
+            best, ms = pkg.sci_tune_launch(algo, y, bits, c["B"], tv, c["lam"], c["inner"], cands,
+                                           rho=c["rho"] if algo == "admm" else 0.0, probe_iters=4, reps=5)
+            out[f"{algo}_{tv}"] = {"best": list(cands[best]), "default": [0, 0],
+                                   "default_depth": pkg.sci_fused_updates(tv, c["B"], c["inner"], 0),
+                                   "ms": {f"{k}@{t}": round(m, 4) for (k, t), m in zip(cands, ms)}}
     except Exception as e:  # noqa: BLE001 -- the section reports its own failure
         out["error"] = f"{type(e).__name__}: {e}"
     return out

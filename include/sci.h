@@ -105,6 +105,13 @@ typedef struct {
                          call blocks; SCI_ERR_ARG while `stream` is capturing).  0: no
                          check (NaN or Inf in y then propagates into the outputs and the
                          FP64 residual history). */
+    int tile;         /* tile class of the temporally blocked kernel: 0 = library choice;
+                         otherwise one that sci_tile_classes lists for the TV form and
+                         frame count: 1 = one-frame 64 x 128 pixels (512 threads x 16
+                         rows), 2 = one-frame 32 x 64 (256 x 8), 8 / 10 = VTV 32 x 32 for
+                         up to 8 / 10 frames, 16 / 24 = VTV 32 x 16 for up to 16 / 24
+                         frames (SCI_ERR_ARG otherwise; the batched driver takes 0 only).
+                         With FP32 storage every class gives the same bits. */
 } sci_params;
 
 /* Human-readable name of a status code (static string). */
@@ -370,6 +377,15 @@ long long sci_last_solve_launches(void);
  * one-launch-per-update kernels serve; -1: invalid arguments). */
 int sci_fused_updates(int tv, int B, int inner_iters, int fuse_k);
 
+/* Tile classes (sci_params.tile) that can run this TV form and frame count,
+ * the library's default first: written to out[0..max), the number that fit
+ * returned (0 for VTV with B > 24, which runs the per-update kernels). */
+int sci_tile_classes(int tv, int B, int* out, int max);
+
+/* sci_fused_updates for a given tile class (0: the default class); -1 for a
+ * class that does not fit. */
+int sci_fused_updates_tile(int tv, int B, int inner_iters, int fuse_k, int tile);
+
 /* Outer loop that sci_tune_fuse times. */
 typedef enum { SCI_ALGO_GAP = 0, SCI_ALGO_ADMM = 1, SCI_ALGO_FISTA = 2 } sci_algo;
 
@@ -396,6 +412,18 @@ sci_status sci_tune_fuse(int algo, const float* y, const uint32_t* bits, int nx,
                          const sci_params* params, float* theta, float* u, void* work,
                          size_t work_bytes, const int* candidates, int n_candidates,
                          int probe_iters, int reps, float* ms, int* best, sci_stream_t stream);
+
+/*
+ * Launch-shape autotuner: as sci_tune_fuse, over n_candidates pairs
+ * (fuse_ks[i], tiles[i]) (HOST arrays; each pair as params->fuse_k and
+ * params->tile).  ms[i] receives pair i's median milliseconds per solve and
+ * *best (HOST int) the index of the fastest pair.  Same limits and errors as
+ * sci_tune_fuse.
+ */
+sci_status sci_tune_launch(int algo, const float* y, const uint32_t* bits, int nx, int ny, int B,
+                           const sci_params* params, float* theta, float* u, void* work, size_t work_bytes,
+                           const int* fuse_ks, const int* tiles, int n_candidates, int probe_iters, int reps,
+                           float* ms, int* best, sci_stream_t stream);
 
 /*
  * The same for sci_gap_tv_batched: one K for every tile class of the batch

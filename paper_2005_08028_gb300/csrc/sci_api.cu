@@ -109,6 +109,7 @@ sci_status validate_params(const sci_params* p, bool admm) {
     if (p->dual == SCI_DUAL_CLIP && p->tv != SCI_TV_ATV) return SCI_ERR_ARG;  // Clip is an ATV box
     if (p->warm_start != 0 && p->warm_start != 1) return SCI_ERR_ARG;
     if (p->check_input != 0 && p->check_input != 1) return SCI_ERR_ARG;
+    if (p->tile < 0) return SCI_ERR_ARG;
     return SCI_OK;
 }
 
@@ -138,9 +139,9 @@ sci_status validate_work(void* work, size_t have, size_t need) {
 // Dual updates per fused launch: fuse_k = -1 turns temporal blocking off;
 // otherwise the largest count the tile halo allows (halo = K + 1), capped by
 // fuse_k when it is positive.  Returns 0 when the per-update kernels serve.
-int choose_fuse(int tv, int B, int S, int fuse_k) {
+int choose_fuse(int tv, int B, int S, int fuse_k, int tile = 0) {
     if (fuse_k < 0) return 0;
-    const int maxh = fused_max_halo(tv, B);
+    const int maxh = tile != 0 ? fused_class_max_halo(tile) : fused_max_halo(tv, B);
     if (maxh < 2) return 0;
     int K = std::min(maxh - 1, default_fuse(tv));
     if (fuse_k > 0) K = std::min(fuse_k, maxh - 1);
@@ -279,7 +280,7 @@ int enqueue_solve(const SolveArgs& A, cudaStream_t s) {
     const std::vector<float> coef = momentum_coeffs(S, A.prm.dual);
     const OuterMode mode = A.admm ? OuterMode::Admm : OuterMode::Gap;
     const int nparts = out_partial_count(g);
-    const int K = choose_fuse(A.prm.tv, A.B, S, A.prm.fuse_k);
+    const int K = choose_fuse(A.prm.tv, A.B, S, A.prm.fuse_k, A.prm.tile);
     for (int t = 0; t < T_outer; ++t) {
         const bool last = t == T_outer - 1;
         const bool metric = A.resid != nullptr && A.resid_every > 0 && ((t + 1) % A.resid_every == 0);
@@ -291,8 +292,9 @@ int enqueue_solve(const SolveArgs& A, cudaStream_t s) {
             base.bits = A.bits;
             base.r = r;
             base.warm = warm ? 1 : 0;
+            base.cls = A.prm.tile;
             // VTV tiles form the next residual in their last launch (GAP and ADMM)
-            const bool fold_r = !last && !A.fista && fused_class(A.prm.tv, A.B) > 1;
+            const bool fold_r = !last && !A.fista && A.prm.tv == SCI_TV_VTV;
             if (fold_r) {
                 base.r_next = r_alt;
                 base.y = A.y;
@@ -487,8 +489,10 @@ sci_status solve_common(bool admm, const float* y, const uint32_t* bits, int nx,
     sci_status st = validate_params(params, admm);
     if (st != SCI_OK) return st;
     if (resid_every < 0 || (resid_every > 0 && resid == nullptr)) return SCI_ERR_ARG;
+    if (params->tile != 0 && !fused_class_fits(params->tv, B, params->tile)) return SCI_ERR_ARG;
     // the dual warm start runs on the temporally blocked path of GAP and ADMM only
-    if (params->warm_start && (fista || twist || choose_fuse(params->tv, B, params->inner_iters, params->fuse_k) == 0))
+    if (params->warm_start &&
+        (fista || twist || choose_fuse(params->tv, B, params->inner_iters, params->fuse_k, params->tile) == 0))
         return SCI_ERR_ARG;
     const Layout L = solver_layout(nx, ny, B, params->storage, admm, params->warm_start != 0);
     st = validate_work(work, work_bytes, L.total);
@@ -674,6 +678,28 @@ long long sci_last_solve_launches(void) { return g_last_launches; }
 int sci_fused_updates(int tv, int B, int inner_iters, int fuse_k) {
     if (tv < SCI_TV_ATV || tv > SCI_TV_VTV || B < 1 || inner_iters < 1 || fuse_k < -1) return -1;
     return choose_fuse(tv, B, inner_iters, fuse_k);
+}
+
+int sci_fused_updates_tile(int tv, int B, int inner_iters, int fuse_k, int tile) {
+    if (tv < SCI_TV_ATV || tv > SCI_TV_VTV || B < 1 || inner_iters < 1 || fuse_k < -1) return -1;
+    if (tile != 0 && (B > 32 || !fused_class_fits(tv, B, tile))) return -1;
+    return choose_fuse(tv, B, inner_iters, fuse_k, tile);
+}
+
+int sci_tile_classes(int tv, int B, int* out, int max) {
+    if (tv < SCI_TV_ATV || tv > SCI_TV_VTV || B < 1 || B > 32 || (out == nullptr && max > 0)) return 0;
+    const int def = fused_class(tv, B);
+    if (def == 0) return 0;
+    int n = 0;
+    auto put = [&](int c) {
+        if (n < max) out[n] = c;
+        ++n;
+    };
+    put(def);
+    const int all[6] = {1, 2, 8, 10, 16, 24};
+    for (int c : all)
+        if (c != def && fused_class_fits(tv, B, c)) put(c);
+    return n;
 }
 
 size_t sci_reduce_workspace(void) { return (size_t)kReduceParts * sizeof(double); }

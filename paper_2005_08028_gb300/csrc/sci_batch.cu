@@ -105,7 +105,7 @@ sci_status make_plan(const sci_problem* probs, int count, const sci_params* prm,
     if (prm->storage < SCI_F32 || prm->storage > SCI_F16 || prm->fuse_k < -1) return SCI_ERR_ARG;
     // the batched driver runs the FGP and Chambolle boxes, without the dual warm start
     if (prm->dual != SCI_DUAL_FGP && prm->dual != SCI_DUAL_CHAM) return SCI_ERR_ARG;
-    if (prm->warm_start != 0 || prm->check_input != 0) return SCI_ERR_ARG;
+    if (prm->warm_start != 0 || prm->check_input != 0 || prm->tile != 0) return SCI_ERR_ARG;
     for (int i = 0; i < count; ++i) {
         const sci_problem& p = probs[i];
         if (p.nx <= 0 || p.ny <= 0 || p.B <= 0 || p.y == nullptr || p.bits == nullptr || p.theta == nullptr)

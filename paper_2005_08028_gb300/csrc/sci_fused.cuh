@@ -1010,17 +1010,23 @@ constexpr int type_slot(int tv, int cfg) {
 
 template <typename T, int TV>
 bool launch_tv(const FusedArgs& a, const FusedBufs<T>& b, cudaStream_t s) {
-    // if constexpr: each TV form instantiates only the tiles it can launch
+    // if constexpr: each TV form instantiates only the tiles it can launch.
+    // a.cls = 0: the library's class; otherwise the class asked for (checked
+    // against the TV form and frame count by the caller).
     if constexpr (TV != SCI_TV_VTV) {
-        if (a.halo <= 8 && (long long)a.g.nx * a.g.ny < 192LL * 192)
-            return launch_cfg<T, TV, CfgF1s>(type_slot<T>(TV, 1), a, b, s);
+        const bool small = a.cls == 2 ||
+                           (a.cls == 0 && a.halo <= 8 && (long long)a.g.nx * a.g.ny < 192LL * 192);
+        if (small) return launch_cfg<T, TV, CfgF1s>(type_slot<T>(TV, 1), a, b, s);
         return launch_cfg<T, TV, CfgF1>(type_slot<T>(TV, 0), a, b, s);
     } else {
-        if (a.g.B <= 8) return launch_cfg<T, TV, CfgV8>(type_slot<T>(TV, 2), a, b, s);
-        if (a.g.B <= 10) return launch_cfg<T, TV, CfgV10>(type_slot<T>(TV, 3), a, b, s);
-        if (a.g.B <= 16) return launch_cfg<T, TV, CfgV16>(type_slot<T>(TV, 4), a, b, s);
-        if (a.g.B <= 24) return launch_cfg<T, TV, CfgV24>(type_slot<T>(TV, 5), a, b, s);
-        return false;
+        const int c = a.cls != 0 ? a.cls : fused_class(SCI_TV_VTV, a.g.B);
+        switch (c) {
+            case 8: return launch_cfg<T, TV, CfgV8>(type_slot<T>(TV, 2), a, b, s);
+            case 10: return launch_cfg<T, TV, CfgV10>(type_slot<T>(TV, 3), a, b, s);
+            case 16: return launch_cfg<T, TV, CfgV16>(type_slot<T>(TV, 4), a, b, s);
+            case 24: return launch_cfg<T, TV, CfgV24>(type_slot<T>(TV, 5), a, b, s);
+            default: return false;
+        }
     }
 }
 
@@ -1049,10 +1055,26 @@ int fused_class(int tv, int B) {
     return 0;
 }
 
+bool fused_class_fits(int tv, int B, int cls) {
+    if (tv != SCI_TV_VTV) return cls == 1 || cls == 2;
+    return (cls == 8 || cls == 10 || cls == 16 || cls == 24) && B <= cls;
+}
+
+int fused_class_max_halo(int cls) {
+    switch (cls) {
+        case 1: return 20;            // 64 x 128 one-frame tile
+        case 2: return 12;            // 32 x 64 one-frame tile
+        case 8: case 10: return 8;    // 32 x 32 VTV tiles
+        case 16: case 24: return 4;   // 32 x 16 VTV tiles
+        default: return 0;
+    }
+}
+
 void fused_class_dims(int cls, int* EH, int* EW) {
     int h = 0, w = 0;
     switch (cls) {
         case 1: dims_of<CfgF1>(h, w); break;
+        case 2: dims_of<CfgF1s>(h, w); break;
         case 8: dims_of<CfgV8>(h, w); break;
         case 10: dims_of<CfgV10>(h, w); break;
         case 16: dims_of<CfgV16>(h, w); break;

@@ -109,6 +109,7 @@ struct FusedArgs {
     int last;               // 1: write theta (and u, x_out); 0: carry p, w (and x-tilde)
     int warm;               // dual warm start: the first launch starts from w = warm_in (p = 0),
                             // the last one also writes its final w to warm_out
+    int cls;                // tile class to launch (0: the library's choice for the TV form and B)
     float lambda, step;     // lambda and 1/(8 lambda)
     float coef[kMaxFuse];   // momentum coefficients of this launch's updates
     const float* xin;       // Prox mode: the prox input
@@ -166,6 +167,12 @@ __host__ __device__ inline int fused_interior(int extent, int halo) { return ext
 
 // Largest halo the fused kernel supports for this TV / frame count (0: none).
 int fused_max_halo(int tv, int B);
+// Tile classes: 1 = one-frame 64 x 128 (512 threads x 16 rows), 2 = one-frame
+// 32 x 64 (256 x 8), 8 / 10 = VTV 32 x 32 for up to 8 / 10 frames, 16 / 24 =
+// VTV 32 x 16 for up to 16 / 24 frames.  Whether a class runs this TV form
+// and frame count, and the largest halo its tile allows.
+bool fused_class_fits(int tv, int B, int cls);
+int fused_class_max_halo(int cls);
 // Tile configuration class for this TV / frame count (0: none) and its tile size.
 int fused_class(int tv, int B);
 void fused_class_dims(int cls, int* EH, int* EW);

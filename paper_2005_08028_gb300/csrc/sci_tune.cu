@@ -6,6 +6,9 @@
 // candidate runs a short solve, timed with CUDA events on the caller's stream.
 // With FP32 storage every depth gives bit-identical results; with 16-bit
 // storage the duals carried between launches are rounded where launches end.
+// sci_tune_launch times (depth, tile class) pairs: the tile classes that fit a
+// TV form and frame count trade the tile's area (the useful share at a given
+// halo) against threads and registers per CTA.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -92,6 +95,37 @@ sci_status sci_tune_fuse(int algo, const float* y, const uint32_t* bits, int nx,
         }
     };
     return time_candidates(run, candidates, n_candidates, reps, ms, best, (cudaStream_t)stream);
+}
+
+sci_status sci_tune_launch(int algo, const float* y, const uint32_t* bits, int nx, int ny, int B,
+                           const sci_params* params, float* theta, float* u, void* work, size_t work_bytes,
+                           const int* fuse_ks, const int* tiles, int n_candidates, int probe_iters, int reps,
+                           float* ms, int* best, sci_stream_t stream) {
+    if (params == nullptr || tiles == nullptr || !args_ok(fuse_ks, n_candidates, probe_iters, reps, ms, best))
+        return SCI_ERR_ARG;
+    if (algo < SCI_ALGO_GAP || algo > SCI_ALGO_FISTA || (algo == SCI_ALGO_ADMM && u == nullptr)) return SCI_ERR_ARG;
+    for (int i = 0; i < n_candidates; ++i)
+        if (tiles[i] < 0) return SCI_ERR_ARG;
+    std::vector<int> idx((size_t)n_candidates);
+    for (int i = 0; i < n_candidates; ++i) idx[(size_t)i] = i;
+    sci_params p = *params;
+    p.outer_iters = probe_iters;
+    p.init = 1;
+    p.use_graph = 0;
+    auto run = [&](int i) -> sci_status {
+        p.fuse_k = fuse_ks[i];
+        p.tile = tiles[i];
+        switch (algo) {
+            case SCI_ALGO_ADMM:
+                return sci_admm_tv(y, bits, nx, ny, B, &p, theta, u, nullptr, nullptr, 0, work, work_bytes, stream);
+            case SCI_ALGO_FISTA:
+                return sci_fista_tv(y, bits, nx, ny, B, &p, theta, nullptr, nullptr, 0, work, work_bytes, stream);
+            default:
+                return sci_gap_tv(y, bits, nx, ny, B, &p, theta, nullptr, nullptr, 0, work, work_bytes, stream);
+        }
+    };
+    // candidates are indices into the pair arrays; the best one is returned as an index
+    return time_candidates(run, idx.data(), n_candidates, reps, ms, best, (cudaStream_t)stream);
 }
 
 sci_status sci_tune_fuse_batched(const sci_problem* problems, int count, const sci_params* params, void* work,

@@ -17,6 +17,7 @@ __all__ = [
     "sci_project", "sci_tv_prox", "sci_gap_tv", "sci_admm_tv", "sci_fista_tv", "sci_twist_tv", "sci_sqdiff_f64",
     "sci_residual_f64", "sci_graph_cache_clear", "sci_tv_prox_noalloc", "sci_last_solve_launches", "sci_fused_updates", "Batch", "SciProblem",
     "sci_gap_tv_batched", "sci_last_batch_launches", "ALGO", "sci_tune_fuse", "sci_tune_fuse_batched",
+    "sci_tune_launch", "sci_tile_classes", "sci_fused_updates_tile",
     "sci_conv3d_c32_bf16", "LearnedProx", "sci_gap_tv_lprox", "Workspace", "SciParams",
 ]
 
@@ -40,7 +41,7 @@ class SciParams(C.Structure):
     _fields_ = [("tv", C.c_int), ("lam", C.c_float), ("rho", C.c_float),
                 ("outer_iters", C.c_int), ("inner_iters", C.c_int), ("storage", C.c_int),
                 ("fuse_k", C.c_int), ("init", C.c_int), ("use_graph", C.c_int), ("dual", C.c_int),
-                ("warm_start", C.c_int), ("check_input", C.c_int)]
+                ("warm_start", C.c_int), ("check_input", C.c_int), ("tile", C.c_int)]
 
 
 class SciProblem(C.Structure):
@@ -74,6 +75,11 @@ _SIGS = {
     "sci_tv_prox_noalloc_max_voxels": (C.c_longlong, []),
     "sci_last_solve_launches": (C.c_longlong, []),
     "sci_fused_updates": (_i, [_i, _i, _i, _i]),
+    "sci_fused_updates_tile": (_i, [_i, _i, _i, _i, _i]),
+    "sci_tile_classes": (_i, [_i, _i, C.POINTER(C.c_int), _i]),
+    "sci_tune_launch": (_i, [_i, _vp, _vp, _i, _i, _i, C.POINTER(SciParams), _vp, _vp, _vp, _sz,
+                             C.POINTER(C.c_int), C.POINTER(C.c_int), _i, _i, _i, C.POINTER(C.c_float),
+                             C.POINTER(C.c_int), _vp]),
     "sci_tune_fuse": (_i, [_i, _vp, _vp, _i, _i, _i, C.POINTER(SciParams), _vp, _vp, _vp, _sz,
                            C.POINTER(_i), _i, _i, _i, C.POINTER(_f), C.POINTER(_i), _vp]),
     "sci_tune_fuse_batched": (_i, [C.POINTER(SciProblem), _i, C.POINTER(SciParams), _vp, _sz,
@@ -233,16 +239,16 @@ DUAL = {"fgp": 0, "cham": 1, "clip": 2}
 
 
 def _params(tv, lam, rho, outer, inner, storage, fuse_k, init, use_graph, dual="fgp", warm_start=False,
-            check_input=False):
+            check_input=False, tile=0):
     return SciParams(TV[tv], float(lam), float(rho), int(outer), int(inner), DTYPE[storage],
                      int(fuse_k), int(init), int(use_graph), DUAL[dual], int(bool(warm_start)),
-                     int(bool(check_input)))
+                     int(bool(check_input)), int(tile))
 
 
 def _solve(admm: bool, y, bits, B, tv, lam, outer, inner, rho=0.0, storage="f32", theta=None, u=None, fista=False,
            twist=False,
            init=None, x_out=None, resid=None, resid_every=0, fuse_k=0, use_graph=True, work=None, dual="fgp",
-           warm_start=False, check_input=False):
+           warm_start=False, check_input=False, tile=0):
     _need_cuda(y, bits, theta, u, x_out, resid)
     nx, ny = y.shape
     dev = y.device
@@ -260,9 +266,10 @@ def _solve(admm: bool, y, bits, B, tv, lam, outer, inner, rho=0.0, storage="f32"
         from . import tune
         if twist:
             raise ValueError("fuse_k='tuned' covers GAP, ADMM and FISTA; pass a depth for TwIST")
-        fuse_k = tune.tuned_fuse("admm" if admm else ("fista" if fista else "gap"), y, bits, B, tv, lam, inner,
-                                 rho=rho, storage=storage, dual=dual, work=work)
-    prm = _params(tv, lam, rho, outer, inner, storage, fuse_k, init, use_graph, dual, warm_start, check_input)
+        fuse_k, tile = tune.tuned_launch("admm" if admm else ("fista" if fista else "gap"), y, bits, B, tv, lam,
+                                         inner, rho=rho, storage=storage, dual=dual, work=work)
+    prm = _params(tv, lam, rho, outer, inner, storage, fuse_k, init, use_graph, dual, warm_start, check_input,
+                  tile)
     lib = load()
     need = lib.sci_solver_workspace(nx, ny, B, C.byref(prm))
     wbuf = (work or Workspace(dev)).get(need)
@@ -392,6 +399,42 @@ def sci_tune_fuse(algo, y, bits, B, tv, lam, inner, candidates, rho=0.0, storage
     _check("sci_tune_fuse", lib.sci_tune_fuse(ALGO[algo], _ptr(y), _ptr(bits), nx, ny, int(B), C.byref(prm),
                                               _ptr(theta), _ptr(u), _ptr(wbuf), wbuf.numel(), c_arr, len(cands),
                                               int(probe_iters), int(reps), ms, C.byref(best), _stream(dev)))
+    return int(best.value), [float(v) for v in ms]
+
+
+def sci_tile_classes(tv: str, B: int) -> list[int]:
+    """Tile classes (sci_params.tile) that can run this TV form and frame
+    count, the library's default first ([] when none: VTV with B > 24)."""
+    out = (C.c_int * 8)()
+    n = int(load().sci_tile_classes(TV[tv], int(B), out, 8))
+    return [int(out[i]) for i in range(min(n, 8))]
+
+
+def sci_fused_updates_tile(tv: str, B: int, inner_iters: int, fuse_k: int = 0, tile: int = 0) -> int:
+    """Dual updates per fused launch for a tile class (-1: the class does not fit)."""
+    return int(load().sci_fused_updates_tile(TV[tv], int(B), int(inner_iters), int(fuse_k), int(tile)))
+
+
+def sci_tune_launch(algo, y, bits, B, tv, lam, inner, pairs, rho=0.0, storage="f32", dual="fgp",
+                    probe_iters=2, reps=3, work=None):
+    """sci_tune_fuse over (fuse_k, tile) pairs.  Returns (index of the fastest
+    pair, [median ms per pair])."""
+    _need_cuda(y, bits)
+    nx, ny = y.shape
+    dev = y.device
+    theta = torch.empty((B, nx, ny), dtype=torch.float32, device=dev)
+    u = torch.empty_like(theta) if algo == "admm" else None
+    prm = _params(tv, lam, rho, probe_iters, inner, storage, 0, True, False, dual)
+    lib = load()
+    wbuf = (work or Workspace(dev)).get(lib.sci_solver_workspace(nx, ny, B, C.byref(prm)))
+    n = len(pairs)
+    ks = (C.c_int * n)(*[int(k) for k, _ in pairs])
+    ts = (C.c_int * n)(*[int(t) for _, t in pairs])
+    ms = (C.c_float * n)()
+    best = C.c_int(0)
+    _check("sci_tune_launch", lib.sci_tune_launch(ALGO[algo], _ptr(y), _ptr(bits), nx, ny, int(B), C.byref(prm),
+                                                  _ptr(theta), _ptr(u), _ptr(wbuf), wbuf.numel(), ks, ts, n,
+                                                  int(probe_iters), int(reps), ms, C.byref(best), _stream(dev)))
     return int(best.value), [float(v) for v in ms]
 
 

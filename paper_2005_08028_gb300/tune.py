@@ -1,4 +1,4 @@
-"""Fuse-depth autotuner driver with a JSON cache.
+"""Launch-shape autotuner driver (fuse depth and tile class) with a JSON cache.
 
 How many FGP dual updates K one temporally blocked launch runs decides the
 tile's halo, hence the useful share of every tile, against the number of
@@ -12,6 +12,11 @@ runs on the same GPU model reuse it without timing.  With FP32 storage
 every K gives bit-identical results, so the cache changes speed, never
 output; with 16-bit storage the duals carried from one launch to the next are
 rounded to 16 bits, and K moves those roundings.
+
+The tile class (sci_params.tile) is tuned beside K for single solves
+(tuned_launch): each class that fits the TV form and frame count trades the
+tile's area, hence its useful share at a given halo, against the threads and
+registers one CTA holds.
 
 The cache file is $SCI_TUNE_CACHE, else ~/.cache/paper_2005_08028_gb300/fuse.json.
 """
@@ -56,6 +61,23 @@ class FuseCache:
         if isinstance(e, dict) and isinstance(e.get("fuse_k"), int):
             return e["fuse_k"]
         return None
+
+    def get_launch(self, key: str) -> tuple[int, int] | None:
+        e = self._d.get(key)
+        if isinstance(e, dict) and isinstance(e.get("fuse_k"), int) and isinstance(e.get("tile"), int):
+            return e["fuse_k"], e["tile"]
+        return None
+
+    def put_launch(self, key: str, pair: tuple[int, int], candidates: list[tuple[int, int]],
+                   ms: list[float]) -> None:
+        """Store one (fuse_k, tile) entry, merging as put does."""
+        merged = self._load()
+        merged.update(self._d)
+        merged[key] = {"fuse_k": int(pair[0]), "tile": int(pair[1]),
+                       "candidates": [[int(k), int(t)] for k, t in candidates],
+                       "ms": [round(float(m), 6) for m in ms]}
+        self._d = merged
+        self.save()
 
     def put(self, key: str, fuse_k: int, candidates: list[int], ms: list[float]) -> None:
         """Store one entry.  The file is read again first, so entries that
@@ -108,6 +130,49 @@ def fuse_candidates(tv: str, B: int, inner: int, per_update: bool = True) -> lis
     if per_update:
         out.append(-1)
     return out
+
+
+def launch_candidates(tv: str, B: int, inner: int, per_update: bool = True) -> list[tuple[int, int]]:
+    """(fuse_k, tile) pairs giving the distinct launch shapes the library can
+    run for this TV form, frame count and S: the library's default (0, 0)
+    first, then every tile class that fits with each distinct depth (deepest
+    first), then (-1, 0) (one launch per update) when per_update."""
+    classes = S.sci_tile_classes(tv, int(B))
+    default = (S.sci_fused_updates(tv, int(B), int(inner), 0), classes[0] if classes else 0)
+    out, seen = [(0, 0)], {default}
+    for c in classes:
+        for k in range(int(inner), 0, -1):
+            eff = S.sci_fused_updates_tile(tv, int(B), int(inner), k, c)
+            if eff > 0 and (eff, c) not in seen:
+                seen.add((eff, c))
+                out.append((eff, c))
+    if per_update:
+        out.append((-1, 0))
+    return out
+
+
+def tuned_launch(algo: str, y: torch.Tensor, bits: torch.Tensor, B: int, tv: str, lam: float, inner: int, *,
+                 rho: float = 0.0, storage: str = "f32", dual: str = "fgp", cache: FuseCache | None = None,
+                 probe_iters: int = 2, reps: int = 3, timer=None, work=None) -> tuple[int, int]:
+    """(fuse_k, tile) for this solve: the cached choice, else timed over
+    launch_candidates (timer defaults to sci.sci_tune_launch) and stored."""
+    nx, ny = int(y.shape[0]), int(y.shape[1])
+    with _lock:
+        cache = cache if cache is not None else FuseCache()
+        key = solve_key(device_name(y.device), algo, tv, nx, ny, int(B), int(inner), storage, dual) + "|launch"
+        got = cache.get_launch(key)
+        if got is not None:
+            return got
+        cands = launch_candidates(tv, int(B), int(inner))
+        if len(cands) == 1:
+            best, ms = 0, [0.0]
+        else:
+            kw = {} if work is None else {"work": work}
+            best, ms = (timer or S.sci_tune_launch)(algo, y, bits, B, tv, lam, inner, cands, rho=rho,
+                                                    storage=storage, dual=dual, probe_iters=probe_iters,
+                                                    reps=reps, **kw)
+        cache.put_launch(key, cands[best], cands, ms)
+        return cands[best]
 
 
 def batch_fuse_candidates(tv: str, Bs: list[int], inner: int) -> list[int]:

@@ -51,8 +51,8 @@ def test_tuned_solve_is_bitwise_the_default_solve(pkg, monkeypatch, tmp_path, al
     assert torch.equal(got, ref)
     entries = json.loads(path.read_text())
     (key, e), = entries.items()
-    assert f"|{algo}|{tv}|200x330x{B}|S10|f32|fgp" in key
-    assert e["fuse_k"] in e["candidates"] and len(e["ms"]) == len(e["candidates"])
+    assert f"|{algo}|{tv}|200x330x{B}|S10|f32|fgp|launch" in key
+    assert [e["fuse_k"], e["tile"]] in e["candidates"] and len(e["ms"]) == len(e["candidates"])
     assert torch.equal(solve(fuse_k="tuned"), ref)  # cache hit
 
 
@@ -79,3 +79,36 @@ def test_tuned_batch_is_bitwise_the_default_batch(pkg, monkeypatch, tmp_path):
     assert "|batched|vtv|" in key and "|S10|f32|fgp" in key
     with pytest.raises(ValueError):
         pkg.sci_gap_tv_batched(batch, "vtv", 0.05, 4, 10, fuse_k="tuned", init=False)
+
+
+@pytest.mark.parametrize("algo", ["gap", "admm"])
+@pytest.mark.parametrize("tv,B", [("atv", 3), ("itv2d", 2), ("vtv", 8), ("vtv", 10)])
+def test_every_tile_class_is_bitwise_the_default(pkg, algo, tv, B):
+    """With FP32 storage the tile class, like the depth, changes only the
+    launch shape: every class that fits gives the default solve's bits."""
+    nx, ny = 150, 210
+    case, y = make_problem(nx, ny, B, 300 + B, sigma=0.01)
+    bits = pkg.sci_masks_pack(to_dev(case.masks))
+
+    def solve(tile, k):
+        if algo == "gap":
+            return pkg.sci_gap_tv(to_dev(y), bits, B, tv, 0.05, 3, 7, tile=tile, fuse_k=k)[0].cpu().numpy()
+        return pkg.sci_admm_tv(to_dev(y), bits, B, tv, 0.05, 0.01, 3, 7, tile=tile, fuse_k=k)[0].cpu().numpy()
+
+    ref = solve(0, 0)
+    for t in pkg.sci_tile_classes(tv, B):
+        for k in (0, 2, 7):
+            np.testing.assert_array_equal(solve(t, k), ref, err_msg=f"tile={t}, fuse_k={k}")
+
+
+def test_tuned_launch_picks_a_candidate_and_keeps_the_bits(pkg, monkeypatch, tmp_path):
+    from paper_2005_08028_gb300 import tune
+    monkeypatch.setenv("SCI_TUNE_CACHE", str(tmp_path / "fuse.json"))
+    B, nx, ny = 10, 128, 160
+    case, y = make_problem(nx, ny, B, 77, sigma=0.01)
+    bits = pkg.sci_masks_pack(to_dev(case.masks))
+    pair = tune.tuned_launch("gap", to_dev(y), bits, B, "vtv", 0.05, 10)
+    assert pair in tune.launch_candidates("vtv", B, 10)
+    a = pkg.sci_gap_tv(to_dev(y), bits, B, "vtv", 0.05, 4, 10, fuse_k="tuned")[0].cpu().numpy()
+    b = pkg.sci_gap_tv(to_dev(y), bits, B, "vtv", 0.05, 4, 10)[0].cpu().numpy()
+    np.testing.assert_array_equal(a, b)

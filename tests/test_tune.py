@@ -206,3 +206,65 @@ def test_bench_tuning_section_reports_choices_and_failures(lib):
             raise S.SciError("sci_tune_fuse", 3)
 
     assert "SCI_ERR_CUDA" in bench._fuse_tuning(Broken, c, None, None)["error"]
+
+
+@pytest.mark.parametrize("tv", ["atv", "itv2d", "vtv"])
+@pytest.mark.parametrize("B", [1, 8, 10, 16, 24])
+@pytest.mark.parametrize("inner", [1, 5, 10])
+def test_launch_candidates_cover_every_class_and_depth(lib, tv, B, inner):
+    c = tune.launch_candidates(tv, B, inner)
+    assert c[0] == (0, 0) and c[-1] == (-1, 0) and len(set(c)) == len(c)
+    classes = S.sci_tile_classes(tv, B)
+    assert classes[0] == (1 if tv != "vtv" else min(x for x in (8, 10, 16, 24) if x >= B))
+    for k, t in c[1:-1]:
+        assert t in classes and 1 <= k <= inner and S.sci_fused_updates_tile(tv, B, inner, k, t) == k
+    for t in classes:  # every class is offered (unless its only depth is the default's)
+        depths = {S.sci_fused_updates_tile(tv, B, inner, k, t) for k in range(1, inner + 1)}
+        offered = {k for k, tt in c if tt == t}
+        default = (S.sci_fused_updates(tv, B, inner, 0), classes[0])
+        assert depths - offered <= ({default[0]} if t == default[1] else set())
+
+
+def test_tile_class_queries(lib):
+    assert S.sci_tile_classes("atv", 10) == [1, 2] and S.sci_tile_classes("itv2d", 3) == [1, 2]
+    assert S.sci_tile_classes("vtv", 8) == [8, 10, 16, 24]
+    assert S.sci_tile_classes("vtv", 11) == [16, 24] and S.sci_tile_classes("vtv", 25) == []
+    assert S.sci_fused_updates_tile("vtv", 12, 10, 0, 10) == -1  # 12 frames do not fit a 10-frame tile
+    assert S.sci_fused_updates_tile("vtv", 8, 10, 10, 16) == 3   # 32 x 16 tiles: halo <= 4
+    assert S.sci_fused_updates_tile("atv", 8, 20, 20, 2) == 11   # 32 x 64 tiles: halo <= 12
+    assert S.sci_fused_updates_tile("atv", 8, 10, 0, 8) == -1    # a VTV class for ATV
+
+
+def test_tuned_launch_caches_the_pair(lib, tmp_path):
+    cache = tune.FuseCache(str(tmp_path / "f.json"))
+    y = torch.zeros(64, 64)
+    calls = []
+
+    def timer(algo, yy, bb, B, tv, lam, inner, pairs, **kw):
+        calls.append(list(pairs))
+        i = pairs.index((3, 2)) if (3, 2) in pairs else 0
+        return i, [1.0 if j == i else 2.0 for j in range(len(pairs))]
+
+    assert tune.tuned_launch("gap", y, y, 4, "atv", 0.05, 10, cache=cache, timer=timer) == (3, 2)
+    assert tune.tuned_launch("gap", y, y, 4, "atv", 0.05, 10, cache=cache, timer=timer) == (3, 2)
+    assert len(calls) == 1 and calls[0] == tune.launch_candidates("atv", 4, 10)
+    again = tune.FuseCache(str(tmp_path / "f.json"))
+    key = tune.solve_key(tune.device_name(y.device), "gap", "atv", 64, 64, 4, 10, "f32", "fgp") + "|launch"
+    assert again.get_launch(key) == (3, 2)
+
+
+def test_c_abi_rejects_bad_tiles_before_any_launch(lib):
+    fake = C.c_void_p(0x10000)
+    big = 1 << 40
+    for tv, B, tile in ((2, 12, 10), (0, 4, 8), (1, 4, 3), (0, 4, -1)):
+        prm = S.SciParams(tv, 0.05, 0.0, 10, 5, 0, 0, 1, 1, 0, 0, 0, tile)
+        assert lib.sci_gap_tv(fake, fake, 8, 8, B, C.byref(prm), fake, fake, None, 0, fake, big, None) == 1
+    ks = (C.c_int * 2)(0, 3)
+    ts = (C.c_int * 2)(0, -1)
+    ms = (C.c_float * 2)()
+    best = C.c_int(0)
+    prm = S.SciParams(0, 0.05, 0.0, 10, 5, 0, 0, 1, 1, 0, 0, 0, 0)
+    assert lib.sci_tune_launch(0, fake, fake, 8, 8, 2, C.byref(prm), fake, None, fake, big, ks, ts, 2, 2, 3, ms,
+                               C.byref(best), None) == 1
+    assert lib.sci_tune_launch(0, fake, fake, 8, 8, 2, C.byref(prm), fake, None, fake, big, ks, None, 2, 2, 3, ms,
+                               C.byref(best), None) == 1
