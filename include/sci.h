@@ -107,8 +107,11 @@ typedef struct {
                          FP64 residual history). */
     int tile;         /* tile class of the temporally blocked kernel: 0 = library choice;
                          otherwise one that sci_tile_classes lists for the TV form and
-                         frame count: 1 = one-frame 64 x 128 pixels (512 threads x 16
-                         rows), 2 = one-frame 32 x 64 (256 x 8), 8 / 10 = VTV 32 x 32 for
+                         frame count: 1 = one-frame 64 x 128 pixels (512 threads, each
+                         a 4 x 4 pixel block), 2 = one-frame 32 x 64 (256 threads, each
+                         8 rows of a column), 3 = one-frame 64 x 128 (512 threads, each
+                         16 rows of a column), 4 = one-frame 32 x 64 (256 threads, each a
+                         2 x 4 block), 8 / 10 = VTV 32 x 32 for
                          up to 8 / 10 frames, 16 / 24 = VTV 32 x 16 for up to 16 / 24
                          frames (SCI_ERR_ARG otherwise; the batched driver takes 0 only).
                          With FP32 storage every class gives the same bits. */

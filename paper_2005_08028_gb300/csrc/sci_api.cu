@@ -696,7 +696,7 @@ int sci_tile_classes(int tv, int B, int* out, int max) {
         ++n;
     };
     put(def);
-    const int all[6] = {1, 2, 8, 10, 16, 24};
+    const int all[8] = {1, 2, 3, 4, 8, 10, 16, 24};
     for (int c : all)
         if (c != def && fused_class_fits(tv, B, c)) put(c);
     return n;

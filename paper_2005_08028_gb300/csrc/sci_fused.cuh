@@ -104,6 +104,7 @@ __host__ __device__ constexpr int block_words(int n) {
 // Compile-time tile configuration.
 template <int NT_, int Q_, int F_, int EW_LOG2_, bool REG_, bool SKIP_>
 struct FusedCfg {
+    static constexpr bool MICRO = false;
     static constexpr int NT = NT_;            // threads per CTA
     static constexpr int Q = Q_;              // rows per strip (pixels per thread)
     static constexpr int F = F_;              // frames held per CTA
@@ -613,6 +614,7 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
 // inside the update loop, which cost more than the halved arithmetic issue.
 template <int NT_, int Q_, int EW_LOG2_>
 struct RowCfg {
+    static constexpr bool MICRO = false;
     static constexpr int NT = NT_;            // threads per CTA
     static constexpr int Q = Q_;              // rows per strip (pixels per thread)
     static constexpr int F = 1;               // one frame per CTA (blockIdx.z picks it)
@@ -907,12 +909,435 @@ __device__ __forceinline__ void fused_tile_rows(const FusedArgs& a, const Prob& 
     }
 }
 
+// One-frame micro-tiles: thread (ty, tx) owns the MR x MC block of slots at
+// rows ty MR .. ty MR + MR - 1 and columns tx MC .. tx MC + MC - 1 of an
+// extended tile of (NT / TX) MR rows by TX MC columns.  A slot's left, right,
+// up and down neighbours are the thread's own registers except on the block's
+// edges, so one dual update exchanges four short vectors per thread through
+// shared memory -- theta of its first column and first row, w_h of its last
+// column and w_v of its last row -- where a one-column strip exchanges every
+// slot's theta and w_h.
+template <int NT_, int TX_LOG2_, int MR_, int MC_>
+struct MicroCfg {
+    static constexpr bool MICRO = true;
+    static constexpr int NT = NT_;            // threads per CTA
+    static constexpr int F = 1;               // one frame per CTA (blockIdx.z picks it)
+    static constexpr int TX_LOG2 = TX_LOG2_;
+    static constexpr int TX = 1 << TX_LOG2;   // threads along a tile row
+    static constexpr int TY = NT / TX;        // threads along a tile column
+    static constexpr int MR = MR_, MC = MC_;  // block rows and columns per thread
+    static constexpr int EW = TX * MC;        // tile width (columns)
+    static constexpr int EH = TY * MR;        // tile height (rows)
+    // Exchange arrays, in floats: one vector per thread, with zero pads where
+    // a tile-edge thread reads past the tile.
+    //   XL: theta (Clip: theta_h) of the block's first column, [TY][TX + 2] x MR, pads at tx = -1 and TX
+    //   XT: theta (Clip: theta_v) of the block's first row,    [TY + 1][TX] x MC, pad row TY
+    //   WR: w_h (at the end p_h) of the block's last column,   [TY][TX + 2] x MR, pads at tx = -1 and TX
+    //   WB: w_v (at the end p_v) of the block's last row,      [TY + 1][TX] x MC, pad row -1 first
+    static constexpr int A_XL = 0;
+    static constexpr int A_XT = A_XL + TY * (TX + 2) * MR;
+    static constexpr int A_WR = A_XT + (TY + 1) * TX * MC;
+    static constexpr int A_WB = A_WR + TY * (TX + 2) * MR;
+    static constexpr size_t SMEM = (size_t)(A_WB + (TY + 1) * TX * MC) * sizeof(float);
+    static_assert(NT % TX == 0 && TX >= 8, "whole rows of threads");
+    static_assert((MR == 2 || MR == 4) && (MC == 2 || MC == 4), "vectors of 2 or 4 floats");
+};
+
+template <int N>
+__device__ __forceinline__ void ldv(const float* p, float (&v)[N]) {
+    if constexpr (N == 4) {
+        const float4 t = *reinterpret_cast<const float4*>(p);
+        v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
+    } else {
+        const float2 t = *reinterpret_cast<const float2*>(p);
+        v[0] = t.x, v[1] = t.y;
+    }
+}
+template <int N>
+__device__ __forceinline__ void stv(float* p, const float (&v)[N]) {
+    if constexpr (N == 4)
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    else
+        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+}
+
+// One tile (bx, by) of frame bz on micro-tiles.  The arithmetic of every slot
+// is fused_tile_rows's, operation for operation, so the two give the same
+// bits at every interior voxel; only the tile edges, which the halo keeps away
+// from the interior, read other pad values.
+template <typename T, int TV, class Cfg, class Prob>
+__device__ __forceinline__ void fused_tile_micro(const FusedArgs& a, const Prob& p, int bx, int by, int bz,
+                                                 float* smem) {
+    constexpr int MR = Cfg::MR, MC = Cfg::MC, TX = Cfg::TX, TY = Cfg::TY, EW = Cfg::EW, EH = Cfg::EH;
+    constexpr bool CLIP = TV == kTvClip;
+
+    const Geo g = p.g();
+    const int H = a.halo;
+    const int TI = fused_interior(EH, H), TJ = fused_interior(EW, H);
+    const int gi0 = by * TI - H, gj0 = bx * TJ - H;
+    const int tid = threadIdx.x;
+    const int tx = tid & (TX - 1), ty = tid >> Cfg::TX_LOG2;
+    const int r0 = ty * MR, c0 = tx * MC;  // the block's first row and column in the tile
+    const int gi_top = gi0 + r0, gj_left = gj0 + c0;
+    const long long fbase = (long long)bz * g.n;
+
+    float* const xl_own = smem + Cfg::A_XL + (ty * (TX + 2) + tx + 1) * MR;
+    float* const xt_own = smem + Cfg::A_XT + (ty * TX + tx) * MC;
+    float* const wr_own = smem + Cfg::A_WR + (ty * (TX + 2) + tx + 1) * MR;
+    float* const wb_own = smem + Cfg::A_WB + ((ty + 1) * TX + tx) * MC;
+    const float* const xl_right = xl_own + MR;
+    const float* const xt_down = xt_own + TX * MC;
+    const float* const wr_left = wr_own - MR;
+    const float* const wb_up = wb_own - TX * MC;
+
+    // row / column flags (bit i: row r0 + i; bit j: column c0 + j)
+    unsigned rin = 0, rv = 0, cin = 0, chm = 0;
+#pragma unroll
+    for (int i = 0; i < MR; ++i) {
+        const int gi = gi_top + i;
+        rin |= (unsigned)(gi >= 0 && gi < g.nx) << i;
+        rv |= (unsigned)(gi >= 0 && gi < g.nx - 1) << i;
+    }
+#pragma unroll
+    for (int j = 0; j < MC; ++j) {
+        const int gj = gj_left + j;
+        cin |= (unsigned)(gj >= 0 && gj < g.ny) << j;
+        chm |= (unsigned)(gj >= 0 && gj < g.ny - 1) << j;
+    }
+    // Blocks whose rows all lie inside the image and above its last row -- the
+    // same for every thread of a warp when a warp is one row of threads -- need
+    // no masks: the column conditions fold into one horizontal step per
+    // column, zero outside the image and on its last column, where w_h starts
+    // at zero and so stays zero.  The vertical step needs no column factor:
+    // outside the image theta and w_v stay exactly zero once w_h does.
+    const bool rows_inner = rv == (1u << MR) - 1;
+    float step_h[MC];
+#pragma unroll
+    for (int j = 0; j < MC; ++j) step_h[j] = ((chm >> j) & 1u) ? a.step : 0.f;
+    auto in_ij = [&](int i, int j) { return ((rin >> i) & (cin >> j) & 1u) != 0; };
+    auto own_ij = [&](int i, int j) {  // an interior slot of this tile, inside the image
+        const int r = r0 + i, c = c0 + j;
+        return in_ij(i, j) && r >= H && r < EH - H + 1 && c >= H && c < EW - H + 1;
+    };
+    auto gidx_of = [&](int i, int j) -> long long {
+        return in_ij(i, j) ? fbase + (long long)(gi_top + i) * g.ny + gj_left + j : fbase;
+    };
+
+    float xr[MR][MC], ph[MR][MC], pv[MR][MC], wh[MR][MC], wv[MR][MC], th[MR][MC];
+    float tv[CLIP ? MR : 1][CLIP ? MC : 1];  // Clip box: theta_v
+    (void)tv;
+    // The Clip box's p is its w: ph / pv stay unused there.
+    auto& PH = [&]() -> float(&)[MR][MC] { if constexpr (CLIP) return wh; else return ph; }();
+    auto& PV = [&]() -> float(&)[MR][MC] { if constexpr (CLIP) return wv; else return pv; }();
+
+    // ---- loads for the whole extended tile, all issued before any is used ----
+    const bool warm_first = a.first && a.warm;  // w from the previous TVdenoise, p = 0
+    if (!a.first) {
+#pragma unroll
+        for (int i = 0; i < MR; ++i)
+#pragma unroll
+            for (int j = 0; j < MC; ++j) {
+                const long long gi = gidx_of(i, j);
+                if constexpr (!CLIP) {
+                    ph[i][j] = ldraw<T>(p.st_in(0), gi);
+                    pv[i][j] = ldraw<T>(p.st_in(1), gi);
+                }
+                wh[i][j] = ldraw<T>(p.st_in(2), gi);
+                wv[i][j] = ldraw<T>(p.st_in(3), gi);
+            }
+    } else if (warm_first) {
+#pragma unroll
+        for (int i = 0; i < MR; ++i)
+#pragma unroll
+            for (int j = 0; j < MC; ++j) {
+                const long long gi = gidx_of(i, j);
+                wh[i][j] = ldraw<T>(p.warm_in(0), gi);
+                wv[i][j] = ldraw<T>(p.warm_in(1), gi);
+            }
+    }
+    if (a.mode == OuterMode::Prox) {
+#pragma unroll
+        for (int i = 0; i < MR; ++i)
+#pragma unroll
+            for (int j = 0; j < MC; ++j) xr[i][j] = __ldg(p.xin() + gidx_of(i, j));
+    } else if (a.first) {
+        uint32_t word[MR][MC];
+        float rr[MR][MC];
+#pragma unroll
+        for (int i = 0; i < MR; ++i)
+#pragma unroll
+            for (int j = 0; j < MC; ++j) {
+                const long long pix = gidx_of(i, j) - fbase;
+                word[i][j] = __ldg(p.bits() + pix);
+                rr[i][j] = __ldg(p.r() + pix);
+                xr[i][j] = ldraw<T>(p.theta_in(), fbase + pix);
+            }
+#pragma unroll
+        for (int i = 0; i < MR; ++i)
+#pragma unroll
+            for (int j = 0; j < MC; ++j)
+                xr[i][j] = rt<T>(cvraw<T>(xr[i][j]) + mask_bit(word[i][j], bz) * rr[i][j]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < MR; ++i)
+#pragma unroll
+            for (int j = 0; j < MC; ++j) xr[i][j] = cvraw<T>(ldraw<T>(p.xt(), gidx_of(i, j)));
+    }
+#pragma unroll
+    for (int i = 0; i < MR; ++i)
+#pragma unroll
+        for (int j = 0; j < MC; ++j) {
+            const bool in = in_ij(i, j);
+            if (!a.first || warm_first) {
+                if constexpr (!CLIP) {
+                    ph[i][j] = cvraw<T>(ph[i][j]);
+                    pv[i][j] = cvraw<T>(pv[i][j]);
+                }
+                wh[i][j] = cvraw<T>(wh[i][j]);
+                wv[i][j] = cvraw<T>(wv[i][j]);
+            }
+            if (!in) xr[i][j] = 0.f;
+            if constexpr (!CLIP) {
+                if (a.first || !in) {
+                    ph[i][j] = 0.f;
+                    pv[i][j] = 0.f;
+                }
+            }
+            if ((a.first && !a.warm) || !in) {
+                wh[i][j] = 0.f;
+                wv[i][j] = 0.f;
+            }
+        }
+
+    // zero pads, then publish w_h of the last column and w_v of the last row
+    constexpr int NPAD = 2 * TY + TX;  // XL / WR pad blocks, then one XT / WB pad row
+    for (int e = tid; e < NPAD; e += Cfg::NT) {
+        float* xl;
+        float* wr;
+        if (e < 2 * TY) {
+            const int row = e >> 1, at = (e & 1) ? TX + 1 : 0;
+            xl = smem + Cfg::A_XL + (row * (TX + 2) + at) * MR;
+            wr = smem + Cfg::A_WR + (row * (TX + 2) + at) * MR;
+#pragma unroll
+            for (int i = 0; i < MR; ++i) xl[i] = wr[i] = 0.f;
+        } else {
+            const int c = e - 2 * TY;
+#pragma unroll
+            for (int j = 0; j < MC; ++j) {
+                smem[Cfg::A_XT + (TY * TX + c) * MC + j] = 0.f;
+                smem[Cfg::A_WB + c * MC + j] = 0.f;
+            }
+        }
+    }
+    {
+        float vr[MR], vb[MC];
+#pragma unroll
+        for (int i = 0; i < MR; ++i) vr[i] = wh[i][MC - 1];
+#pragma unroll
+        for (int j = 0; j < MC; ++j) vb[j] = wv[MR - 1][j];
+        stv<MR>(wr_own, vr);
+        stv<MC>(wb_own, vb);
+    }
+    __syncthreads();
+
+    const float lam = a.lambda, step = a.step;
+    constexpr int kUnroll = CLIP ? 1 : 2;
+#pragma unroll kUnroll
+    for (int s = 0; s < a.K; ++s) {
+        const bool skip_theta = a.first && !a.warm && s == 0;  // w = 0 there: theta = xt
+        // ---- theta = xt - lambda (D^T w) ----
+        {
+            float wl[MR], wu[MC];
+            ldv<MR>(wr_left, wl);
+            ldv<MC>(wb_up, wu);
+#pragma unroll
+            for (int i = 0; i < MR; ++i)
+#pragma unroll
+                for (int j = 0; j < MC; ++j) {
+                    float t = xr[i][j], v = xr[i][j];
+                    if (!skip_theta) {
+                        const float l = j > 0 ? wh[i][j > 0 ? j - 1 : 0] : wl[i];
+                        const float u = i > 0 ? wv[i > 0 ? i - 1 : 0][j] : wu[j];
+                        if constexpr (CLIP) {
+                            t = __fmaf_rn(-lam, l - wh[i][j], xr[i][j]);
+                            v = __fmaf_rn(-lam, u - wv[i][j], xr[i][j]);
+                        } else {
+                            t = __fmaf_rn(-lam, (l - wh[i][j]) + (u - wv[i][j]), xr[i][j]);
+                        }
+                    }
+                    th[i][j] = t;
+                    if constexpr (CLIP) tv[i][j] = v;
+                }
+            float vl[MR], vt[MC];
+#pragma unroll
+            for (int i = 0; i < MR; ++i) vl[i] = th[i][0];
+#pragma unroll
+            for (int j = 0; j < MC; ++j) {
+                if constexpr (CLIP) vt[j] = tv[0][j];
+                else vt[j] = th[0][j];
+            }
+            stv<MR>(xl_own, vl);
+            stv<MC>(xt_own, vt);
+        }
+        __syncthreads();
+        // ---- a = w + step * D theta, projection, momentum ----
+        const float c = a.coef[s];
+        float tr[MR], td[MC];
+        ldv<MR>(xl_right, tr);
+        ldv<MC>(xt_down, td);
+        auto dual_step = [&](auto masked_c) {
+            constexpr bool MASKED = decltype(masked_c)::value;
+            // the flags pass through an empty asm each update, so the per-slot
+            // tests are formed here rather than held in registers across the loop
+            unsigned m_rin = rin, m_chm = chm, m_rv = rv, m_cin = cin;
+            asm volatile("" : "+r"(m_rin), "+r"(m_chm), "+r"(m_rv), "+r"(m_cin));
+#pragma unroll
+            for (int i = 0; i < MR; ++i)
+#pragma unroll
+                for (int j = 0; j < MC; ++j) {
+                    const float t0 = th[i][j];
+                    const float trt = j < MC - 1 ? th[i][j < MC - 1 ? j + 1 : 0] : tr[i];
+                    float dv;
+                    if constexpr (CLIP) {
+                        const float v0 = tv[i][j];
+                        dv = (i < MR - 1 ? tv[i < MR - 1 ? i + 1 : 0][j] : td[j]) - v0;
+                    } else {
+                        dv = (i < MR - 1 ? th[i < MR - 1 ? i + 1 : 0][j] : td[j]) - t0;
+                    }
+                    float ah, av;
+                    if constexpr (MASKED) {
+                        const bool mh = ((m_rin >> i) & (m_chm >> j) & 1u) != 0;
+                        const bool mv = ((m_rv >> i) & (m_cin >> j) & 1u) != 0;
+                        ah = mh ? fmaf(trt - t0, step, wh[i][j]) : 0.f;
+                        av = mv ? fmaf(dv, step, wv[i][j]) : 0.f;
+                    } else {
+                        ah = fmaf(trt - t0, step_h[j], wh[i][j]);
+                        av = fmaf(dv, step, wv[i][j]);
+                    }
+                    if constexpr (TV == SCI_TV_ATV || CLIP) {
+                        ah = fminf(fmaxf(ah, -1.f), 1.f);
+                        av = fminf(fmaxf(av, -1.f), 1.f);
+                    } else {
+                        const float sc = fminf(1.f, rsqrt_ftz(fmaf(ah, ah, av * av)));
+                        ah *= sc;
+                        av *= sc;
+                    }
+                    if constexpr (CLIP) {
+                        wh[i][j] = ah;
+                        wv[i][j] = av;
+                    } else {
+                        wh[i][j] = fmaf(c, ah - ph[i][j], ah);
+                        wv[i][j] = fmaf(c, av - pv[i][j], av);
+                        ph[i][j] = ah;
+                        pv[i][j] = av;
+                    }
+                }
+        };
+        if (rows_inner) dual_step(std::false_type{});
+        else dual_step(std::true_type{});
+        {
+            float vr[MR], vb[MC];
+#pragma unroll
+            for (int i = 0; i < MR; ++i) vr[i] = wh[i][MC - 1];
+#pragma unroll
+            for (int j = 0; j < MC; ++j) vb[j] = wv[MR - 1][j];
+            stv<MR>(wr_own, vr);
+            stv<MC>(wb_own, vb);
+        }
+        __syncthreads();
+    }
+
+    // ---- epilogue ----
+    // fresh copies of the block origin: the epilogue's addresses are then formed
+    // here rather than kept live across the update loop
+    int e_top = gi_top, e_left = gj_left;
+    unsigned e_rin = rin, e_cin = cin;
+    asm volatile("" : "+r"(e_top), "+r"(e_left), "+r"(e_rin), "+r"(e_cin));
+    auto in_e = [&](int i, int j) { return ((e_rin >> i) & (e_cin >> j) & 1u) != 0; };
+    auto own_e = [&](int i, int j) {
+        const int r = r0 + i, c = c0 + j;
+        return in_e(i, j) && r >= H && r < EH - H + 1 && c >= H && c < EW - H + 1;
+    };
+    auto gidx_of_e = [&](int i, int j) -> long long {
+        return in_e(i, j) ? fbase + (long long)(e_top + i) * g.ny + e_left + j : fbase;
+    };
+    if (!a.last) {
+        // carry x-tilde (first launch of a solve), p and w of the interior
+#pragma unroll
+        for (int i = 0; i < MR; ++i)
+#pragma unroll
+            for (int j = 0; j < MC; ++j) {
+                if (!own_e(i, j)) continue;
+                const long long gi = gidx_of_e(i, j);
+                if (a.first && a.mode != OuterMode::Prox) st<T>(p.xt(), gi, xr[i][j]);
+                st<T>(p.st_out(0), gi, PH[i][j]);
+                st<T>(p.st_out(1), gi, PV[i][j]);
+                st<T>(p.st_out(2), gi, wh[i][j]);
+                st<T>(p.st_out(3), gi, wv[i][j]);
+            }
+        return;
+    }
+    // theta = xt - lambda D^T p reads p_h of the left neighbour and p_v of the
+    // row above: publish the block's last column / row of p where w was (the
+    // loop ended with a barrier, and no one reads w any more).
+    {
+        float vr[MR], vb[MC];
+#pragma unroll
+        for (int i = 0; i < MR; ++i) vr[i] = PH[i][MC - 1];
+#pragma unroll
+        for (int j = 0; j < MC; ++j) vb[j] = PV[MR - 1][j];
+        stv<MR>(wr_own, vr);
+        stv<MC>(wb_own, vb);
+    }
+    // ADMM with x requested: x^(t+1) = xt - u^(t), u^(t) read (into the free
+    // theta registers) before u^(t+1) overwrites it
+    const bool want_xu = a.mode == OuterMode::Admm && p.x_out() != nullptr;
+    if (want_xu) {
+#pragma unroll
+        for (int i = 0; i < MR; ++i)
+#pragma unroll
+            for (int j = 0; j < MC; ++j) th[i][j] = own_e(i, j) ? ldg<T>(p.u_in(), gidx_of_e(i, j)) : 0.f;
+    }
+    __syncthreads();
+    float pl[MR], pu[MC];
+    ldv<MR>(wr_left, pl);
+    ldv<MC>(wb_up, pu);
+#pragma unroll
+    for (int i = 0; i < MR; ++i)
+#pragma unroll
+        for (int j = 0; j < MC; ++j) {
+            if (!own_e(i, j)) continue;
+            const float l = j > 0 ? PH[i][j > 0 ? j - 1 : 0] : pl[i];
+            const float u = i > 0 ? PV[i > 0 ? i - 1 : 0][j] : pu[j];
+            const float x0 = xr[i][j];
+            const float t = __fmaf_rn(-lam, (l - PH[i][j]) + (u - PV[i][j]), x0);
+            const long long gi = gidx_of_e(i, j);
+            if (a.mode == OuterMode::Prox) {
+                p.theta_f32()[gi] = t;
+                continue;
+            }
+            st<T>(p.theta_out(), gi, t);
+            if (a.mode == OuterMode::Gap) {
+                if (p.x_out() != nullptr) p.x_out()[gi] = x0;
+            } else {
+                st<T>(p.u_out(), gi, x0 - rt<T>(t));
+                if (want_xu) p.x_out()[gi] = x0 - th[i][j];
+            }
+            if (a.warm) {
+                st<T>(p.warm_out(0), gi, wh[i][j]);
+                st<T>(p.warm_out(1), gi, wv[i][j]);
+            }
+        }
+}
+
 // A tile all of whose rows lie inside the image and above its last row runs
 // the interior form; the others the border form.
 template <typename T, int TV, class Cfg, class Prob>
 __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, int bx, int by, int bz,
                                            float* smem) {
-    if constexpr (Cfg::F == 1) {
+    if constexpr (Cfg::MICRO) {
+        fused_tile_micro<T, TV, Cfg>(a, p, bx, by, bz, smem);
+    } else if constexpr (Cfg::F == 1) {
         fused_tile_rows<T, TV, Cfg>(a, p, bx, by, bz, smem);
     } else {
         const Geo g = p.g();
@@ -931,6 +1356,8 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
 // 1- or 2-row strips, where skipping balances well and saves work.
 using CfgF1 = RowCfg<512, 16, 7>;    // 128 x 64 tile, one frame
 using CfgF1s = RowCfg<256, 8, 6>;    // 64 x 32 tile, one frame (small images)
+using CfgM1 = MicroCfg<512, 5, 4, 4>;   // 128 x 64 tile of 4 x 4 blocks, one frame
+using CfgM1s = MicroCfg<256, 4, 2, 4>;  // 64 x 32 tile of 2 x 4 blocks, one frame
 using CfgV8 = FusedCfg<512, 2, 8, 5, true, true>;      // 32 x 32 tile, up to 8 frames
 using CfgV10 = FusedCfg<512, 2, 10, 5, false, true>;   // 32 x 32 tile, up to 10 frames
 using CfgV16 = FusedCfg<256, 2, 16, 5, false, true>;   // 32 x 16 tile, up to 16 frames
@@ -1005,7 +1432,7 @@ bool launch_cfg(int slot, const FusedArgs& a, const FusedBufs<T>& b, cudaStream_
 // One "attribute set" flag word per (storage type, TV kernel code, configuration).
 template <typename T>
 constexpr int type_slot(int tv, int cfg) {
-    return (std::is_same<T, float>::value ? 0 : (std::is_same<T, __half>::value ? 1 : 2)) * 28 + tv * 7 + cfg;
+    return (std::is_same<T, float>::value ? 0 : (std::is_same<T, __half>::value ? 1 : 2)) * 32 + tv * 8 + cfg;
 }
 
 template <typename T, int TV>
@@ -1014,10 +1441,14 @@ bool launch_tv(const FusedArgs& a, const FusedBufs<T>& b, cudaStream_t s) {
     // a.cls = 0: the library's class; otherwise the class asked for (checked
     // against the TV form and frame count by the caller).
     if constexpr (TV != SCI_TV_VTV) {
+        // classes 1 and 3: 64 x 128 tiles (4 x 4 blocks / 16-row strips);
+        // 2 and 4: 32 x 64 tiles (8-row strips / 2 x 4 blocks)
+        if (a.cls == 3) return launch_cfg<T, TV, CfgF1>(type_slot<T>(TV, 0), a, b, s);
+        if (a.cls == 4) return launch_cfg<T, TV, CfgM1s>(type_slot<T>(TV, 7), a, b, s);
         const bool small = a.cls == 2 ||
                            (a.cls == 0 && a.halo <= 8 && (long long)a.g.nx * a.g.ny < 192LL * 192);
         if (small) return launch_cfg<T, TV, CfgF1s>(type_slot<T>(TV, 1), a, b, s);
-        return launch_cfg<T, TV, CfgF1>(type_slot<T>(TV, 0), a, b, s);
+        return launch_cfg<T, TV, CfgM1>(type_slot<T>(TV, 6), a, b, s);
     } else {
         const int c = a.cls != 0 ? a.cls : fused_class(SCI_TV_VTV, a.g.B);
         switch (c) {
@@ -1056,14 +1487,14 @@ int fused_class(int tv, int B) {
 }
 
 bool fused_class_fits(int tv, int B, int cls) {
-    if (tv != SCI_TV_VTV) return cls == 1 || cls == 2;
+    if (tv != SCI_TV_VTV) return cls >= 1 && cls <= 4;
     return (cls == 8 || cls == 10 || cls == 16 || cls == 24) && B <= cls;
 }
 
 int fused_class_max_halo(int cls) {
     switch (cls) {
-        case 1: return 20;            // 64 x 128 one-frame tile
-        case 2: return 12;            // 32 x 64 one-frame tile
+        case 1: case 3: return 20;    // 64 x 128 one-frame tiles
+        case 2: case 4: return 12;    // 32 x 64 one-frame tiles
         case 8: case 10: return 8;    // 32 x 32 VTV tiles
         case 16: case 24: return 4;   // 32 x 16 VTV tiles
         default: return 0;
@@ -1073,8 +1504,10 @@ int fused_class_max_halo(int cls) {
 void fused_class_dims(int cls, int* EH, int* EW) {
     int h = 0, w = 0;
     switch (cls) {
-        case 1: dims_of<CfgF1>(h, w); break;
+        case 1: dims_of<CfgM1>(h, w); break;
         case 2: dims_of<CfgF1s>(h, w); break;
+        case 3: dims_of<CfgF1>(h, w); break;
+        case 4: dims_of<CfgM1s>(h, w); break;
         case 8: dims_of<CfgV8>(h, w); break;
         case 10: dims_of<CfgV10>(h, w); break;
         case 16: dims_of<CfgV16>(h, w); break;

@@ -101,6 +101,24 @@ def test_every_tile_class_is_bitwise_the_default(pkg, algo, tv, B):
             np.testing.assert_array_equal(solve(t, k), ref, err_msg=f"tile={t}, fuse_k={k}")
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("tv,dual", [("atv", "fgp"), ("itv2d", "fgp"), ("atv", "clip")])
+def test_one_frame_tile_layouts_agree_bitwise(pkg, storage, tv, dual):
+    """The one-frame tiles come in two thread layouts (4 x 4 / 2 x 4 pixel
+    blocks and 16- / 8-row column strips) of two sizes.  At one depth they
+    round the carried duals at the same points, so even with 16-bit storage
+    every layout and size gives the same bits; a 300 x 420 image spans several
+    tiles of each with ragged last ones."""
+    B, nx, ny = 3, 300, 420
+    case, y = make_problem(nx, ny, B, 900, sigma=0.01)
+    bits = pkg.sci_masks_pack(to_dev(case.masks))
+    for k in (3, 10):
+        outs = {t: pkg.sci_gap_tv(to_dev(y), bits, B, tv, 0.05, 3, 10, tile=t, fuse_k=k, storage=storage,
+                                  dual=dual)[1].cpu().numpy() for t in (1, 2, 3, 4)}
+        for t in (2, 3, 4):
+            np.testing.assert_array_equal(outs[t], outs[1], err_msg=f"tile={t}, fuse_k={k}")
+
+
 def test_tuned_launch_picks_a_candidate_and_keeps_the_bits(pkg, monkeypatch, tmp_path):
     from paper_2005_08028_gb300 import tune
     monkeypatch.setenv("SCI_TUNE_CACHE", str(tmp_path / "fuse.json"))

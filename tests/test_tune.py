@@ -189,21 +189,26 @@ def test_bench_tuning_section_reports_choices_and_failures(lib):
     calls = []
 
     class Fake:
+        sci_fused_updates = staticmethod(S.sci_fused_updates)
+
         @staticmethod
-        def sci_tune_fuse(algo, y, bits, B, tv, lam, inner, cands, rho=0.0, probe_iters=2, reps=3):
+        def sci_tune_launch(algo, y, bits, B, tv, lam, inner, cands, rho=0.0, probe_iters=2, reps=3):
             calls.append((algo, tv, rho, probe_iters, reps))
-            return cands[0], [1.0 + i for i in range(len(cands))]
+            return 0, [1.0 + i for i in range(len(cands))]
 
     out = bench._fuse_tuning(Fake, c, None, None)
     assert set(out) == {"probe"} | {f"{a}_{t}" for a, t in bench.COMBOS}
-    assert out["gap_vtv"]["best"] == out["gap_vtv"]["default"] == S.sci_fused_updates("vtv", 10, 10, 0)
-    assert list(out["admm_atv"]["ms"]) == [str(k) for k in tune.fuse_candidates("atv", 10, 10)]
+    assert out["gap_vtv"]["best"] == out["gap_vtv"]["default"] == [0, 0]
+    assert out["gap_vtv"]["default_depth"] == S.sci_fused_updates("vtv", 10, 10, 0)
+    assert list(out["admm_atv"]["ms"]) == [f"{k}@{t}" for k, t in tune.launch_candidates("atv", 10, 10)]
     assert [r for _, _, r, _, _ in calls] == [0.0] * 3 + [0.01] * 3
 
     class Broken:
+        sci_fused_updates = staticmethod(S.sci_fused_updates)
+
         @staticmethod
-        def sci_tune_fuse(*a, **k):
-            raise S.SciError("sci_tune_fuse", 3)
+        def sci_tune_launch(*a, **k):
+            raise S.SciError("sci_tune_launch", 3)
 
     assert "SCI_ERR_CUDA" in bench._fuse_tuning(Broken, c, None, None)["error"]
 
@@ -226,7 +231,7 @@ def test_launch_candidates_cover_every_class_and_depth(lib, tv, B, inner):
 
 
 def test_tile_class_queries(lib):
-    assert S.sci_tile_classes("atv", 10) == [1, 2] and S.sci_tile_classes("itv2d", 3) == [1, 2]
+    assert S.sci_tile_classes("atv", 10) == [1, 2, 3, 4] and S.sci_tile_classes("itv2d", 3) == [1, 2, 3, 4]
     assert S.sci_tile_classes("vtv", 8) == [8, 10, 16, 24]
     assert S.sci_tile_classes("vtv", 11) == [16, 24] and S.sci_tile_classes("vtv", 25) == []
     assert S.sci_fused_updates_tile("vtv", 12, 10, 0, 10) == -1  # 12 frames do not fit a 10-frame tile
@@ -256,7 +261,7 @@ def test_tuned_launch_caches_the_pair(lib, tmp_path):
 def test_c_abi_rejects_bad_tiles_before_any_launch(lib):
     fake = C.c_void_p(0x10000)
     big = 1 << 40
-    for tv, B, tile in ((2, 12, 10), (0, 4, 8), (1, 4, 3), (0, 4, -1)):
+    for tv, B, tile in ((2, 12, 10), (0, 4, 8), (1, 4, 5), (2, 4, 3), (0, 4, -1)):
         prm = S.SciParams(tv, 0.05, 0.0, 10, 5, 0, 0, 1, 1, 0, 0, 0, tile)
         assert lib.sci_gap_tv(fake, fake, 8, 8, B, C.byref(prm), fake, fake, None, 0, fake, big, None) == 1
     ks = (C.c_int * 2)(0, 3)
