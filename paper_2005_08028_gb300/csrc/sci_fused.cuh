@@ -913,10 +913,14 @@ __device__ __forceinline__ void fused_tile_rows(const FusedArgs& a, const Prob& 
 // rows ty MR .. ty MR + MR - 1 and columns tx MC .. tx MC + MC - 1 of an
 // extended tile of (NT / TX) MR rows by TX MC columns.  A slot's left, right,
 // up and down neighbours are the thread's own registers except on the block's
-// edges, so one dual update exchanges four short vectors per thread through
-// shared memory -- theta of its first column and first row, w_h of its last
-// column and w_v of its last row -- where a one-column strip exchanges every
-// slot's theta and w_h.
+// edges, so one dual update exchanges four short vectors per thread -- theta
+// of its first column and first row, w_h of its last column and w_v of its
+// last row -- where a one-column strip exchanges every slot's theta and w_h.
+// A warp holds whole rows of threads, so the left and right neighbours are
+// the adjacent lanes: theta and w_h cross by warp shuffles (one 32-bit word
+// per lane per cycle), and only the vertical vectors go through shared
+// memory, as 64-bit halves (a 128-bit shared access moves half as many bytes
+// per cycle as two 64-bit ones).
 template <int NT_, int TX_LOG2_, int MR_, int MC_>
 struct MicroCfg {
     static constexpr bool MICRO = true;
@@ -928,37 +932,31 @@ struct MicroCfg {
     static constexpr int MR = MR_, MC = MC_;  // block rows and columns per thread
     static constexpr int EW = TX * MC;        // tile width (columns)
     static constexpr int EH = TY * MR;        // tile height (rows)
-    // Exchange arrays, in floats: one vector per thread, with zero pads where
-    // a tile-edge thread reads past the tile.
-    //   XL: theta (Clip: theta_h) of the block's first column, [TY][TX + 2] x MR, pads at tx = -1 and TX
-    //   XT: theta (Clip: theta_v) of the block's first row,    [TY + 1][TX] x MC, pad row TY
-    //   WR: w_h (at the end p_h) of the block's last column,   [TY][TX + 2] x MR, pads at tx = -1 and TX
-    //   WB: w_v (at the end p_v) of the block's last row,      [TY + 1][TX] x MC, pad row -1 first
-    static constexpr int A_XL = 0;
-    static constexpr int A_XT = A_XL + TY * (TX + 2) * MR;
-    static constexpr int A_WR = A_XT + (TY + 1) * TX * MC;
-    static constexpr int A_WB = A_WR + TY * (TX + 2) * MR;
-    static constexpr size_t SMEM = (size_t)(A_WB + (TY + 1) * TX * MC) * sizeof(float);
-    static_assert(NT % TX == 0 && TX >= 8, "whole rows of threads");
-    static_assert((MR == 2 || MR == 4) && (MC == 2 || MC == 4), "vectors of 2 or 4 floats");
+    // Exchange arrays, in floats: one 4-vector per thread as two float2 halves
+    // (columns 0-1, then 2-3: HALF floats apart), entry (row, tx) at float2
+    // index row TX + tx, so a warp's 64-bit accesses are conflict-free; zero
+    // pad rows where a tile-edge thread reads past the tile.
+    //   XT: theta (Clip: theta_v) of the block's first row, rows 0 .. TY - 1 = ty, pad row TY
+    //   WB: w_v (at the end p_v) of the block's last row,    rows 1 .. TY = ty + 1, pad row 0
+    static constexpr int HALF = (TY + 1) * TX * 2;
+    static constexpr int A_XT = 0;
+    static constexpr int A_WB = A_XT + 2 * HALF;
+    static constexpr size_t SMEM = (size_t)(A_WB + 2 * HALF) * sizeof(float);
+    static_assert(NT % TX == 0 && TX >= 8 && TX <= 32 && 32 % TX == 0, "whole rows of threads in each warp");
+    static_assert((MR == 2 || MR == 4) && MC == 4, "blocks of 2 or 4 rows by 4 columns");
 };
 
-template <int N>
-__device__ __forceinline__ void ldv(const float* p, float (&v)[N]) {
-    if constexpr (N == 4) {
-        const float4 t = *reinterpret_cast<const float4*>(p);
-        v[0] = t.x, v[1] = t.y, v[2] = t.z, v[3] = t.w;
-    } else {
-        const float2 t = *reinterpret_cast<const float2*>(p);
-        v[0] = t.x, v[1] = t.y;
-    }
+// A 4-vector of an exchange array: two float2 halves HALF floats apart.
+template <int HALF>
+__device__ __forceinline__ void ld4h(const float* base, int idx, float (&v)[4]) {
+    const float2 lo = reinterpret_cast<const float2*>(base)[idx];
+    const float2 hi = reinterpret_cast<const float2*>(base + HALF)[idx];
+    v[0] = lo.x, v[1] = lo.y, v[2] = hi.x, v[3] = hi.y;
 }
-template <int N>
-__device__ __forceinline__ void stv(float* p, const float (&v)[N]) {
-    if constexpr (N == 4)
-        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-    else
-        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+template <int HALF>
+__device__ __forceinline__ void st4h(float* base, int idx, const float (&v)[4]) {
+    reinterpret_cast<float2*>(base)[idx] = make_float2(v[0], v[1]);
+    reinterpret_cast<float2*>(base + HALF)[idx] = make_float2(v[2], v[3]);
 }
 
 // One tile (bx, by) of frame bz on micro-tiles.  The arithmetic of every slot
@@ -981,14 +979,23 @@ __device__ __forceinline__ void fused_tile_micro(const FusedArgs& a, const Prob&
     const int gi_top = gi0 + r0, gj_left = gj0 + c0;
     const long long fbase = (long long)bz * g.n;
 
-    float* const xl_own = smem + Cfg::A_XL + (ty * (TX + 2) + tx + 1) * MR;
-    float* const xt_own = smem + Cfg::A_XT + (ty * TX + tx) * MC;
-    float* const wr_own = smem + Cfg::A_WR + (ty * (TX + 2) + tx + 1) * MR;
-    float* const wb_own = smem + Cfg::A_WB + ((ty + 1) * TX + tx) * MC;
-    const float* const xl_right = xl_own + MR;
-    const float* const xt_down = xt_own + TX * MC;
-    const float* const wr_left = wr_own - MR;
-    const float* const wb_up = wb_own - TX * MC;
+    constexpr int HALF = Cfg::HALF;
+    float* const XT = smem + Cfg::A_XT;
+    float* const WB = smem + Cfg::A_WB;
+    const int xt_own = ty * TX + tx, xt_down = xt_own + TX;  // exchange-array entries
+    const int wb_own = (ty + 1) * TX + tx, wb_up = wb_own - TX;
+    // w_h / p_h of the left neighbour's last column, theta of the right
+    // neighbour's first column: adjacent lanes (zero past the tile's edges,
+    // which the halo keeps away from the interior).  Every lane of the CTA
+    // runs every shuffle: the loop trip counts are uniform.
+    auto from_left = [&](float v) {
+        const float t = __shfl_up_sync(0xffffffffu, v, 1);
+        return tx > 0 ? t : 0.f;
+    };
+    auto from_right = [&](float v) {
+        const float t = __shfl_down_sync(0xffffffffu, v, 1);
+        return tx < TX - 1 ? t : 0.f;
+    };
 
     // row / column flags (bit i: row r0 + i; bit j: column c0 + j)
     unsigned rin = 0, rv = 0, cin = 0, chm = 0;
@@ -1109,34 +1116,17 @@ __device__ __forceinline__ void fused_tile_micro(const FusedArgs& a, const Prob&
             }
         }
 
-    // zero pads, then publish w_h of the last column and w_v of the last row
-    constexpr int NPAD = 2 * TY + TX;  // XL / WR pad blocks, then one XT / WB pad row
-    for (int e = tid; e < NPAD; e += Cfg::NT) {
-        float* xl;
-        float* wr;
-        if (e < 2 * TY) {
-            const int row = e >> 1, at = (e & 1) ? TX + 1 : 0;
-            xl = smem + Cfg::A_XL + (row * (TX + 2) + at) * MR;
-            wr = smem + Cfg::A_WR + (row * (TX + 2) + at) * MR;
-#pragma unroll
-            for (int i = 0; i < MR; ++i) xl[i] = wr[i] = 0.f;
-        } else {
-            const int c = e - 2 * TY;
-#pragma unroll
-            for (int j = 0; j < MC; ++j) {
-                smem[Cfg::A_XT + (TY * TX + c) * MC + j] = 0.f;
-                smem[Cfg::A_WB + c * MC + j] = 0.f;
-            }
-        }
+    // zero the pad rows (XT row TY, WB row 0), then publish w_v of the last row
+    if (tid < TX) {
+        const float zero[4] = {0.f, 0.f, 0.f, 0.f};
+        st4h<HALF>(XT, TY * TX + tid, zero);
+        st4h<HALF>(WB, tid, zero);
     }
     {
-        float vr[MR], vb[MC];
-#pragma unroll
-        for (int i = 0; i < MR; ++i) vr[i] = wh[i][MC - 1];
+        float vb[MC];
 #pragma unroll
         for (int j = 0; j < MC; ++j) vb[j] = wv[MR - 1][j];
-        stv<MR>(wr_own, vr);
-        stv<MC>(wb_own, vb);
+        st4h<HALF>(WB, wb_own, vb);
     }
     __syncthreads();
 
@@ -1148,8 +1138,9 @@ __device__ __forceinline__ void fused_tile_micro(const FusedArgs& a, const Prob&
         // ---- theta = xt - lambda (D^T w) ----
         {
             float wl[MR], wu[MC];
-            ldv<MR>(wr_left, wl);
-            ldv<MC>(wb_up, wu);
+#pragma unroll
+            for (int i = 0; i < MR; ++i) wl[i] = from_left(wh[i][MC - 1]);
+            ld4h<HALF>(WB, wb_up, wu);
 #pragma unroll
             for (int i = 0; i < MR; ++i)
 #pragma unroll
@@ -1168,23 +1159,21 @@ __device__ __forceinline__ void fused_tile_micro(const FusedArgs& a, const Prob&
                     th[i][j] = t;
                     if constexpr (CLIP) tv[i][j] = v;
                 }
-            float vl[MR], vt[MC];
-#pragma unroll
-            for (int i = 0; i < MR; ++i) vl[i] = th[i][0];
+            float vt[MC];
 #pragma unroll
             for (int j = 0; j < MC; ++j) {
                 if constexpr (CLIP) vt[j] = tv[0][j];
                 else vt[j] = th[0][j];
             }
-            stv<MR>(xl_own, vl);
-            stv<MC>(xt_own, vt);
+            st4h<HALF>(XT, xt_own, vt);
         }
         __syncthreads();
         // ---- a = w + step * D theta, projection, momentum ----
         const float c = a.coef[s];
         float tr[MR], td[MC];
-        ldv<MR>(xl_right, tr);
-        ldv<MC>(xt_down, td);
+#pragma unroll
+        for (int i = 0; i < MR; ++i) tr[i] = from_right(th[i][0]);  // Clip: theta_h
+        ld4h<HALF>(XT, xt_down, td);
         auto dual_step = [&](auto masked_c) {
             constexpr bool MASKED = decltype(masked_c)::value;
             // the flags pass through an empty asm each update, so the per-slot
@@ -1236,13 +1225,10 @@ __device__ __forceinline__ void fused_tile_micro(const FusedArgs& a, const Prob&
         if (rows_inner) dual_step(std::false_type{});
         else dual_step(std::true_type{});
         {
-            float vr[MR], vb[MC];
-#pragma unroll
-            for (int i = 0; i < MR; ++i) vr[i] = wh[i][MC - 1];
+            float vb[MC];
 #pragma unroll
             for (int j = 0; j < MC; ++j) vb[j] = wv[MR - 1][j];
-            stv<MR>(wr_own, vr);
-            stv<MC>(wb_own, vb);
+            st4h<HALF>(WB, wb_own, vb);
         }
         __syncthreads();
     }
@@ -1277,17 +1263,17 @@ __device__ __forceinline__ void fused_tile_micro(const FusedArgs& a, const Prob&
             }
         return;
     }
-    // theta = xt - lambda D^T p reads p_h of the left neighbour and p_v of the
-    // row above: publish the block's last column / row of p where w was (the
-    // loop ended with a barrier, and no one reads w any more).
-    {
-        float vr[MR], vb[MC];
+    // theta = xt - lambda D^T p reads p_h of the left neighbour (a shuffle)
+    // and p_v of the row above: publish the block's last row of p where w_v
+    // was (the loop ended with a barrier, and no one reads w_v any more).
+    float pl[MR], pu[MC];
 #pragma unroll
-        for (int i = 0; i < MR; ++i) vr[i] = PH[i][MC - 1];
+    for (int i = 0; i < MR; ++i) pl[i] = from_left(PH[i][MC - 1]);
+    {
+        float vb[MC];
 #pragma unroll
         for (int j = 0; j < MC; ++j) vb[j] = PV[MR - 1][j];
-        stv<MR>(wr_own, vr);
-        stv<MC>(wb_own, vb);
+        st4h<HALF>(WB, wb_own, vb);
     }
     // ADMM with x requested: x^(t+1) = xt - u^(t), u^(t) read (into the free
     // theta registers) before u^(t+1) overwrites it
@@ -1299,9 +1285,7 @@ __device__ __forceinline__ void fused_tile_micro(const FusedArgs& a, const Prob&
             for (int j = 0; j < MC; ++j) th[i][j] = own_e(i, j) ? ldg<T>(p.u_in(), gidx_of_e(i, j)) : 0.f;
     }
     __syncthreads();
-    float pl[MR], pu[MC];
-    ldv<MR>(wr_left, pl);
-    ldv<MC>(wb_up, pu);
+    ld4h<HALF>(WB, wb_up, pu);
 #pragma unroll
     for (int i = 0; i < MR; ++i)
 #pragma unroll
