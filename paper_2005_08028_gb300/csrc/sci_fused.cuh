@@ -17,18 +17,19 @@
 // sum inside one thread.  A warp covers 32 consecutive columns of one strip,
 // so global accesses are coalesced and the row tests below are warp-uniform.
 //
-// State: p, w (and, when registers allow, x-tilde) of the owned slots live
-// in registers.  Vertical neighbours inside a strip are register reads;
-// shared memory carries what other threads read: theta and w_h of every slot
-// (left/right neighbours) and w_v of each strip's last row.  No global memory
-// is touched between the updates of one launch.  Where it pays (see the
+// State: p, w (and, when registers allow, x-tilde and theta) of the owned
+// slots live in registers.  Vertical neighbours inside a strip are register
+// reads; horizontal neighbours are adjacent lanes of a warp and cross by
+// shuffles; shared memory carries what crosses between strips (theta of a
+// strip's first row, w_v of its last row).  No global memory is touched
+// between the updates of one launch.  Where it pays (see the
 // configurations), rows whose results can no longer reach the interior are
 // skipped: the band that matters shrinks by one row per update.
 //
-// Two implementations: one-frame tiles (fused_tile_rows; ATV, ITV2D and the
-// Clip box) use scalar FP32 arithmetic on row-major shared arrays; VTV tiles
-// (fused_tile_impl) keep each thread's slots in one 128-bit-aligned shared
-// block and run pairs of frames through the packed FP32 instructions.
+// Three implementations: one-frame tiles on column strips (fused_tile_rows)
+// or on 4 x 4 pixel blocks (fused_tile_micro; ATV, ITV2D and the Clip box)
+// use scalar FP32 arithmetic; VTV tiles (fused_tile_impl) run pairs of
+// frames through the packed FP32 instructions.
 //
 // This header holds the implementation; sci_fused_f32.cu, sci_fused_f16.cu and
 // sci_fused_bf16.cu each instantiate it for one storage type (SCI_FUSED_STORAGE),
@@ -86,19 +87,14 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
-__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
-__device__ __forceinline__ void sts4(float* p, float2 a, float2 b) {
-    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+// A frame pair of a neighbouring lane (zero past the edge of the strip row).
+__device__ __forceinline__ float2 shfl_up2(float2 v, bool edge) {
+    const float x = __shfl_up_sync(0xffffffffu, v.x, 1), y = __shfl_up_sync(0xffffffffu, v.y, 1);
+    return edge ? make_float2(0.f, 0.f) : make_float2(x, y);
 }
-__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
-__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
-
-// Words of a per-thread shared-memory block holding n floats: n rounded up to
-// a multiple of 4 whose quotient by 4 is odd.  Consecutive columns' blocks then
-// start 16-byte aligned, and the 8 lanes of each phase of a 128-bit access
-// fall on 8 different 16-byte bank groups.
-__host__ __device__ constexpr int block_words(int n) {
-    return ((n + 3) / 4) % 2 == 1 ? ((n + 3) / 4) * 4 : ((n + 3) / 4) * 4 + 4;
+__device__ __forceinline__ float2 shfl_down2(float2 v, bool edge) {
+    const float x = __shfl_down_sync(0xffffffffu, v.x, 1), y = __shfl_down_sync(0xffffffffu, v.y, 1);
+    return edge ? make_float2(0.f, 0.f) : make_float2(x, y);
 }
 
 // Compile-time tile configuration.
@@ -116,26 +112,24 @@ struct FusedCfg {
     static constexpr bool SKIP = SKIP_;       // skip rows that can no longer reach the interior
     static constexpr int E = F * Q;           // slots per thread
     static constexpr int NP = E / 2;          // packed register pairs per thread: element (q, f) is q F + f
-    // Shared memory, in floats.  Every thread's slots form one block of BLK
-    // words, element (q, f) at q FP + f with each row's frames padded to a
-    // multiple of 4 (FP), so rows and groups of 4 frames move as 128-bit
-    // words.  The blocks of a strip sit column by column, with one zero pad
-    // block on each side (columns -1 and EW): a thread reads its left and
-    // right neighbours' blocks with 128-bit loads and edge columns need no
-    // tests.  w_v of a strip's last row has blocks of BLKV words (one word for
-    // one-frame tiles).
-    static constexpr int FP = (F + 3) / 4 * 4;
-    static constexpr int ES = Q * FP;                           // shared words of a thread's slots
-    static constexpr int BLK = block_words(ES);
-    static constexpr int BLKV = block_words(FP);
-    static constexpr int SROW = (EW + 2) * BLK;                 // one strip of a padded slot array
-    static constexpr int A_TH = 0;                              // theta          [NS][EW + 2][BLK]
-    static constexpr int A_WH = A_TH + NS * SROW;               // w_h (then p_h) [NS][EW + 2][BLK]
-    static constexpr int A_WV = A_WH + NS * SROW;               // w_v (then p_v) of each strip's last row [NS][EW][BLKV]
-    static constexpr int A_XT = A_WV + ((NS * EW * BLKV + 3) & ~3);  // x-tilde [NS][EW][BLK] (only when !REG)
-    static constexpr size_t SMEM = (size_t)(A_XT + (REG ? 0 : NS * EW * BLK)) * sizeof(float);
+    // Shared memory, in float2 words (frame pairs).  A warp is one row of a
+    // strip, so a slot's left and right neighbours are adjacent lanes and
+    // cross by warp shuffles; shared memory carries what crosses between
+    // strips, and x-tilde and theta where they do not fit in registers
+    // (REG: both in registers, only each strip's first row of theta shared).
+    // Word (row q, pair k, column c) of a strip sits at (q NPR + k) EW + c, so
+    // a warp's 64-bit accesses are conflict-free (a 128-bit shared access
+    // moves half as many bytes per cycle as two 64-bit ones).
+    static constexpr int NPR = F / 2;                     // frame pairs per row
+    static constexpr int RW = NPR * EW;                   // float2 words of one tile row
+    static constexpr int TS = REG ? RW : Q * RW;          // theta words per strip
+    static constexpr int A_TH = 0;                        // theta [NS][TS]
+    static constexpr int A_WV = A_TH + NS * TS;           // w_v (then p_v) of each strip's last row [NS][NPR][EW]
+    static constexpr int A_U = A_WV + NS * RW;            // ADMM u^(t) for x in the last launch [NS][Q][NPR][EW]
+    static constexpr int A_XT = A_U + NS * Q * RW;        // x-tilde [NS][Q][NPR][EW] (only when !REG)
+    static constexpr size_t SMEM = (size_t)(A_XT + (REG ? 0 : NS * Q * RW)) * sizeof(float2);
     static_assert(NT % EW == 0, "a CTA must cover whole rows");
-    static_assert(EW % 32 == 0, "a warp must stay inside one strip row");
+    static_assert(EW == 32, "a warp is one strip row");
     static_assert(F % 2 == 0, "frames pair up for packed arithmetic");
     static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
 };
@@ -215,8 +209,8 @@ struct BatchProb {
 template <typename T, int TV, class Cfg, bool BORDER, class Prob>
 __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& p, int bx, int by, int bz,
                                                 float* smem) {
-    constexpr int Q = Cfg::Q, F = Cfg::F, EW = Cfg::EW, EH = Cfg::EH, NS = Cfg::NS, FP = Cfg::FP;
-    constexpr int NP = Cfg::NP, BLK = Cfg::BLK, BLKV = Cfg::BLKV, SROW = Cfg::SROW;
+    constexpr int Q = Cfg::Q, F = Cfg::F, EW = Cfg::EW, EH = Cfg::EH, NS = Cfg::NS;
+    constexpr int NP = Cfg::NP, NPR = Cfg::NPR, RW = Cfg::RW, TS = Cfg::TS;
     constexpr bool REG = Cfg::REG, SKIP = Cfg::SKIP;
     static_assert(F > 1 && TV == SCI_TV_VTV, "frame tiles are for VTV (one-frame tiles: fused_tile_rows)");
 
@@ -228,25 +222,25 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
     constexpr int f0 = 0;                        // global frame of slot f = 0 (bz unused)
     (void)bz;
     const int tid = threadIdx.x;
-    const int col = tid & (EW - 1);
-    const int strip = tid >> Cfg::EW_LOG2;
+    const int col = tid & (EW - 1);              // = the lane
+    const int strip = tid >> Cfg::EW_LOG2;       // = the warp
     const int r0 = strip * Q;                    // first row of the strip
     const int gj = gj0 + col;
     const bool col_in = gj >= 0 && gj < g.ny;
     const bool col_int = col >= H && col < EW - H + 1;
     const int gi_top = gi0 + r0;
+    const bool first_col = col == 0, last_col = col == EW - 1;
 
-    // This thread's blocks and its neighbours'.  th_down (strip NS - 1) and
-    // wv_up (strip 0) then point at other, valid shared words, whose values
-    // are replaced before use.
-    float* const th_own = smem + Cfg::A_TH + strip * SROW + (col + 1) * BLK;
-    float* const wh_own = smem + Cfg::A_WH + strip * SROW + (col + 1) * BLK;
-    const float* const th_right = th_own + BLK;
-    const float* const wh_left = wh_own - BLK;
-    const float* const th_down = th_own + SROW;
-    float* const wv_own = smem + Cfg::A_WV + (strip * EW + col) * BLKV;
-    const float* const wv_up = wv_own - EW * BLKV;
-    float* const xt_own = smem + Cfg::A_XT + (strip * EW + col) * BLK;  // only when !REG
+    // Shared float2 words: theta (REG: of the strip's first row only), w_v of
+    // the strip's last row, and the strips above / below (strip-uniform tests
+    // guard the reads past the first and last strip).
+    float2* const sm2 = reinterpret_cast<float2*>(smem);
+    float2* const th_own = sm2 + Cfg::A_TH + strip * TS + col;   // (q, k) at (q NPR + k) EW
+    float2* const wv_own = sm2 + Cfg::A_WV + strip * RW + col;
+    const float2* const th_down = th_own + TS;   // read only when has_down
+    const float2* const wv_up = wv_own - RW;     // read only when has_up
+    float2* const u_own = sm2 + Cfg::A_U + strip * Q * RW + col;   // [q][k] at (q NPR + k) EW
+    float2* const xt_own = sm2 + Cfg::A_XT + strip * Q * RW + col;  // only when !REG
     const bool has_up = strip > 0, has_down = strip < NS - 1;
 
     // per-row flags as bit masks (bit q: row r0 + q)
@@ -265,7 +259,7 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
     auto fac = [&](unsigned m, int q) -> float { return ((m >> q) & 1u) ? step : 0.f; };
 
     float2 PH[NP], PV[NP], WH[NP], WV[NP];
-    float2 X[REG ? NP : 1];
+    float2 X[REG ? NP : 1], TH[REG ? NP : 1];
 
     // ---- load x-tilde (and the carried duals) for the whole extended tile ----
     // Every load is issued unconditionally -- a pixel outside the image reads
@@ -385,35 +379,13 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
             }
         }
     }
-    // A register pair (frames f, f+1 of row q) is the 128-bit half at words
-    // q FP + f of a shared block; the padding frames of a row store zeros.
-    auto put_block = [&](float* blk, const float2* R) {
+    // a register pair (row q, frames 2k, 2k + 1) is element q NPR + k
+    if (!REG) {
 #pragma unroll
-        for (int q = 0; q < Q; ++q)
-#pragma unroll
-            for (int c = 0; c < FP / 4; ++c) {
-                const int e2 = (q * F + 4 * c) / 2;
-                sts4(blk + q * FP + 4 * c, R[e2], 4 * c + 2 < F ? R[4 * c + 2 < F ? e2 + 1 : 0] : make_float2(0.f, 0.f));
-            }
-    };
-    auto put_last_row = [&](float* blk, const float2* R) {
-#pragma unroll
-        for (int c = 0; c < FP / 4; ++c) {
-            const int e2 = ((Q - 1) * F + 4 * c) / 2;
-            sts4(blk + 4 * c, R[e2], 4 * c + 2 < F ? R[4 * c + 2 < F ? e2 + 1 : 0] : make_float2(0.f, 0.f));
-        }
-    };
-    put_block(wh_own, WH);
-    if (!REG) put_block(xt_own, XS);
-    put_last_row(wv_own, WV);
-    // zero pad blocks (columns -1 and EW of every strip) of theta and w_h
-    for (int e = tid; e < NS * 2 * (BLK / 4); e += Cfg::NT) {
-        const int s = e / (2 * (BLK / 4)), rem = e - s * 2 * (BLK / 4);
-        const int side = rem / (BLK / 4), w4 = rem - side * (BLK / 4);
-        const int off = s * SROW + (side ? (EW + 1) * BLK : 0) + 4 * w4;
-        *reinterpret_cast<float4*>(smem + Cfg::A_TH + off) = make_float4(0.f, 0.f, 0.f, 0.f);
-        *reinterpret_cast<float4*>(smem + Cfg::A_WH + off) = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int e2 = 0; e2 < NP; ++e2) xt_own[e2 * EW] = XS[e2];
     }
+#pragma unroll
+    for (int k = 0; k < NPR; ++k) wv_own[k * EW] = WV[(Q - 1) * NPR + k];
     __syncthreads();
 
     const float2 nlam2 = dup2(-a.lambda);
@@ -426,34 +398,27 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
     for (int s = 0; s < a.K; ++s) {
         const float2 c2 = dup2(a.coef[s]);
         // rows whose p stays exact after this update: [1 + s, EH - 1 - s);
-        // theta is needed on those rows and the one below
+        // theta is needed on those rows and the one below (strip-uniform, so
+        // every lane of a warp runs the same shuffles)
         const int rlo = 1 + s, rhi = EH - 1 - s;
         const int qlo = SKIP ? max(rlo - r0, 0) : 0;
         const int qhi_p = SKIP ? min(rhi - r0, Q) : Q, qhi_t = SKIP ? min(rhi + 1 - r0, Q) : Q;
-        // ---- theta = xt - lambda (D^T w), frames paired ----
+        // ---- theta = xt - lambda (D^T w), frames paired; w_h of the left
+        //      neighbour by shuffle, w_v of the row above from the strip above ----
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             if (q < qlo || q >= qhi_t) continue;
 #pragma unroll
-            for (int c = 0; c < FP / 4; ++c) {
-                const float4 wl = lds4(wh_left + q * FP + 4 * c);
-                float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (!REG) xv = lds4(xt_own + q * FP + 4 * c);
-                float4 wu = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (q == 0) {
-                    const float4 w = lds4(wv_up + 4 * c);
-                    if (has_up) wu = w;
-                }
-                float2 th[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (4 * c + 2 * h >= F) continue;
-                    const int e2 = (q * F + 4 * c) / 2 + h;
-                    const float2 x2 = REG ? X[REG ? e2 : 0] : (h ? hi2(xv) : lo2(xv));
-                    const float2 wu2 = q > 0 ? WV[q > 0 ? e2 - F / 2 : 0] : (h ? hi2(wu) : lo2(wu));
-                    th[h] = fma2(nlam2, add2(sub2(h ? hi2(wl) : lo2(wl), WH[e2]), sub2(wu2, WV[e2])), x2);
-                }
-                sts4(th_own + q * FP + 4 * c, th[0], th[1]);
+            for (int k = 0; k < NPR; ++k) {
+                const int e2 = q * NPR + k;
+                const float2 wl = shfl_up2(WH[e2], first_col);
+                float2 wu = make_float2(0.f, 0.f);
+                if (q > 0) wu = WV[q > 0 ? e2 - NPR : 0];
+                else if (has_up) wu = wv_up[k * EW];
+                const float2 x2 = REG ? X[REG ? e2 : 0] : xt_own[e2 * EW];
+                const float2 t = fma2(nlam2, add2(sub2(wl, WH[e2]), sub2(wu, WV[e2])), x2);
+                if (REG) TH[REG ? e2 : 0] = t;
+                if (!REG || q == 0) th_own[e2 * EW] = t;
             }
         }
         __syncthreads();
@@ -469,51 +434,41 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
             }
             float2 n2 = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int c = 0; c < FP / 4; ++c) {
-                const float4 tr = lds4(th_right + q * FP + 4 * c);
-                const float4 t0 = lds4(th_own + q * FP + 4 * c);
-                float4 td;
-                if (q < Q - 1) {
-                    td = lds4(th_own + (q + 1) * FP + 4 * c);
-                } else {
-                    const float4 d = lds4(th_down + 4 * c);
-                    td = has_down ? d : t0;
-                }
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (4 * c + 2 * h >= F) continue;
-                    const int e2 = (q * F + 4 * c) / 2 + h;
-                    const float2 tt = h ? hi2(t0) : lo2(t0);
-                    const float2 ah = fma2(sub2(h ? hi2(tr) : lo2(tr), tt), sh, WH[e2]);
-                    const float2 av = fma2(sub2(h ? hi2(td) : lo2(td), tt), sv, WV[e2]);
-                    WH[e2] = ah;
-                    WV[e2] = av;
-                    n2 = fma2(ah, ah, fma2(av, av, n2));
-                }
+            for (int k = 0; k < NPR; ++k) {
+                const int e2 = q * NPR + k;
+                const float2 tt = REG ? TH[REG ? e2 : 0] : th_own[e2 * EW];
+                const float2 tr = shfl_down2(tt, last_col);
+                float2 td = tt;
+                if (q < Q - 1) td = REG ? TH[REG && q < Q - 1 ? e2 + NPR : 0] : th_own[(e2 + NPR) * EW];
+                else if (has_down) td = th_down[k * EW];
+                const float2 ah = fma2(sub2(tr, tt), sh, WH[e2]);
+                const float2 av = fma2(sub2(td, tt), sv, WV[e2]);
+                WH[e2] = ah;
+                WV[e2] = av;
+                n2 = fma2(ah, ah, fma2(av, av, n2));
             }
             const float2 vs = dup2(fminf(1.f, rsqrt_ftz(n2.x + n2.y)));
 #pragma unroll
-            for (int f = 0; f < F; f += 2) {
-                const int e2 = (q * F + f) / 2;
+            for (int k = 0; k < NPR; ++k) {
+                const int e2 = q * NPR + k;
                 const float2 nh = mul2(WH[e2], vs), nv = mul2(WV[e2], vs);
                 WH[e2] = fma2(c2, sub2(nh, PH[e2]), nh);
                 WV[e2] = fma2(c2, sub2(nv, PV[e2]), nv);
                 PH[e2] = nh;
                 PV[e2] = nv;
             }
-#pragma unroll
-            for (int c = 0; c < FP / 4; ++c) {
-                const int e2 = (q * F + 4 * c) / 2;
-                sts4(wh_own + q * FP + 4 * c, WH[e2],
-                     4 * c + 2 < F ? WH[4 * c + 2 < F ? e2 + 1 : 0] : make_float2(0.f, 0.f));
-            }
         }
-        put_last_row(wv_own, WV);
+#pragma unroll
+        for (int k = 0; k < NPR; ++k) wv_own[k * EW] = WV[(Q - 1) * NPR + k];
         __syncthreads();
     }
 
     // ---- epilogue ----
-    auto sidx = [&](int q, int f) { return q * FP + f; };  // element (q, f) of a shared block
+    auto x_of = [&](int q, int f) -> float {  // x-tilde of slot (q, f)
+        if constexpr (REG) return el<F>(X, q, f);
+        const float2 v = xt_own[((q * F + f) >> 1) * EW];
+        return (f & 1) ? v.y : v.x;
+    };
     if (!a.last) {
         // carry x-tilde (first launch of a solve), p and w of the interior
 #pragma unroll
@@ -525,8 +480,7 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
             for (int f = 0; f < F; ++f) {
                 if (f >= nfr) break;
                 const long long gidx = (long long)(f0 + f) * g.n + pix;
-                if (a.first && a.mode != OuterMode::Prox)
-                    st<T>(p.xt(), gidx, REG ? el<F>(X, q, f) : xt_own[sidx(q, f)]);
+                if (a.first && a.mode != OuterMode::Prox) st<T>(p.xt(), gidx, x_of(q, f));
                 st<T>(p.st_out(0), gidx, el<F>(PH, q, f));
                 st<T>(p.st_out(1), gidx, el<F>(PV, q, f));
                 st<T>(p.st_out(2), gidx, el<F>(WH, q, f));
@@ -535,30 +489,42 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
         }
         return;
     }
-    // theta = xt - lambda D^T p needs p_h of the left neighbour and p_v of the
-    // row above: stage them where w_h / w_v were (the loop ended with a barrier).
-    put_block(wh_own, PH);
-    put_last_row(wv_own, PV);
+    // theta = xt - lambda D^T p needs p_h of the left neighbour (a shuffle,
+    // into the theta registers or words, free now) and p_v of the row above
+    // (staged where w_v was: the loop ended with a barrier).
+#pragma unroll
+    for (int e2 = 0; e2 < NP; ++e2) {
+        const float2 pl = shfl_up2(PH[e2], first_col);
+        if (REG) TH[REG ? e2 : 0] = pl;
+        else th_own[e2 * EW] = pl;
+    }
+#pragma unroll
+    for (int k = 0; k < NPR; ++k) wv_own[k * EW] = PV[(Q - 1) * NPR + k];
     // x^(t+1) = xt - u^(t) for ADMM (only when x is requested): u^(t) is read
-    // before u^(t+1) overwrites it.  Issue every load first (into the thread's
-    // own theta block, free now) so none waits behind a store it might alias.
-    if (a.mode == OuterMode::Admm && p.x_out() != nullptr) {
+    // before u^(t+1) overwrites it.  Issue every load first (into the
+    // thread's own words of a shared array) so none waits behind a store it
+    // might alias.
+    const bool want_xu = a.mode == OuterMode::Admm && p.x_out() != nullptr;
+    if (want_xu) {
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const int r = r0 + q;
             const bool mine = ((in_m >> q) & 1u) && col_int && r >= H && r < EH - H + 1;
             const long long pix = mine ? (long long)(gi_top + q) * g.ny + gj : 0;
 #pragma unroll
-            for (int f = 0; f < F; ++f) {
-                if (f >= nfr) break;
-                th_own[sidx(q, f)] = mine ? ldg<T>(p.u_in(), (long long)(f0 + f) * g.n + pix) : 0.f;
+            for (int k = 0; k < NPR; ++k) {
+                const int f = 2 * k;
+                float2 uv = make_float2(0.f, 0.f);
+                if (mine && f < nfr) uv.x = ldg<T>(p.u_in(), (long long)(f0 + f) * g.n + pix);
+                if (mine && f + 1 < nfr) uv.y = ldg<T>(p.u_in(), (long long)(f0 + f + 1) * g.n + pix);
+                u_own[(q * NPR + k) * EW] = uv;
             }
         }
     }
     __syncthreads();
     // VTV tiles hold every frame of a pixel: form the next residual here (the
     // per-pixel order of the separate residual pass)
-    const bool fold_r = F > 1 && a.r_next != nullptr && a.mode != OuterMode::Prox;
+    const bool fold_r = a.r_next != nullptr && a.mode != OuterMode::Prox;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int r = r0 + q;
@@ -569,11 +535,21 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
 #pragma unroll
         for (int f = 0; f < F; ++f) {
             if (f >= nfr) break;
-            const float pl = wh_left[sidx(q, f)];
-            float pu;
-            if (q > 0) pu = el<F>(PV, q > 0 ? q - 1 : 0, f);
-            else pu = has_up ? wv_up[f] : 0.f;
-            const float x0 = REG ? el<F>(X, q, f) : xt_own[sidx(q, f)];
+            float pl;
+            if constexpr (REG) {
+                pl = el<F>(TH, q, f);
+            } else {
+                const float2 v = th_own[((q * F + f) >> 1) * EW];
+                pl = (f & 1) ? v.y : v.x;
+            }
+            float pu = 0.f;
+            if (q > 0) {
+                pu = el<F>(PV, q > 0 ? q - 1 : 0, f);
+            } else if (has_up) {
+                const float2 v = wv_up[(f >> 1) * EW];
+                pu = (f & 1) ? v.y : v.x;
+            }
+            const float x0 = x_of(q, f);
             const float th = __fmaf_rn(-a.lambda, (pl - el<F>(PH, q, f)) + (pu - el<F>(PV, q, f)), x0);
             const long long gidx = (long long)(f0 + f) * g.n + pix;
             if (a.mode == OuterMode::Prox) {
@@ -588,7 +564,10 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
             } else {
                 const float un = rt<T>(x0 - thr);
                 st<T>(p.u_out(), gidx, un);
-                if (p.x_out() != nullptr) p.x_out()[gidx] = x0 - th_own[sidx(q, f)];
+                if (want_xu) {
+                    const float2 uv = u_own[((q * F + f) >> 1) * EW];
+                    p.x_out()[gidx] = x0 - ((f & 1) ? uv.y : uv.x);
+                }
                 v = thr - un;
             }
             if (fold_r) acc = __fmaf_rn(mask_bit(word, f0 + f), v, acc);
