@@ -87,14 +87,15 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
-// A frame pair of a neighbouring lane (zero past the edge of the strip row).
-__device__ __forceinline__ float2 shfl_up2(float2 v, bool edge) {
-    const float x = __shfl_up_sync(0xffffffffu, v.x, 1), y = __shfl_up_sync(0xffffffffu, v.y, 1);
-    return edge ? make_float2(0.f, 0.f) : make_float2(x, y);
+// A frame pair of the left / right lane.  The first / last lane gets its own
+// value back: the tile's edge columns lie in its halo, and with a halo of
+// K + 1 (left) and K (right) no value read there reaches the interior within
+// K updates, so any finite stand-in for the missing neighbour serves.
+__device__ __forceinline__ float2 shfl_up2(float2 v) {
+    return make_float2(__shfl_up_sync(0xffffffffu, v.x, 1), __shfl_up_sync(0xffffffffu, v.y, 1));
 }
-__device__ __forceinline__ float2 shfl_down2(float2 v, bool edge) {
-    const float x = __shfl_down_sync(0xffffffffu, v.x, 1), y = __shfl_down_sync(0xffffffffu, v.y, 1);
-    return edge ? make_float2(0.f, 0.f) : make_float2(x, y);
+__device__ __forceinline__ float2 shfl_down2(float2 v) {
+    return make_float2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
 }
 
 // Compile-time tile configuration.
@@ -229,7 +230,6 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
     const bool col_in = gj >= 0 && gj < g.ny;
     const bool col_int = col >= H && col < EW - H + 1;
     const int gi_top = gi0 + r0;
-    const bool first_col = col == 0, last_col = col == EW - 1;
 
     // Shared float2 words: theta (REG: of the strip's first row only), w_v of
     // the strip's last row, and the strips above / below (strip-uniform tests
@@ -411,7 +411,7 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
 #pragma unroll
             for (int k = 0; k < NPR; ++k) {
                 const int e2 = q * NPR + k;
-                const float2 wl = shfl_up2(WH[e2], first_col);
+                const float2 wl = shfl_up2(WH[e2]);
                 float2 wu = make_float2(0.f, 0.f);
                 if (q > 0) wu = WV[q > 0 ? e2 - NPR : 0];
                 else if (has_up) wu = wv_up[k * EW];
@@ -437,7 +437,7 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
             for (int k = 0; k < NPR; ++k) {
                 const int e2 = q * NPR + k;
                 const float2 tt = REG ? TH[REG ? e2 : 0] : th_own[e2 * EW];
-                const float2 tr = shfl_down2(tt, last_col);
+                const float2 tr = shfl_down2(tt);
                 float2 td = tt;
                 if (q < Q - 1) td = REG ? TH[REG && q < Q - 1 ? e2 + NPR : 0] : th_own[(e2 + NPR) * EW];
                 else if (has_down) td = th_down[k * EW];
@@ -494,7 +494,7 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
     // (staged where w_v was: the loop ended with a barrier).
 #pragma unroll
     for (int e2 = 0; e2 < NP; ++e2) {
-        const float2 pl = shfl_up2(PH[e2], first_col);
+        const float2 pl = shfl_up2(PH[e2]);
         if (REG) TH[REG ? e2 : 0] = pl;
         else th_own[e2 * EW] = pl;
     }
@@ -964,17 +964,13 @@ __device__ __forceinline__ void fused_tile_micro(const FusedArgs& a, const Prob&
     const int xt_own = ty * TX + tx, xt_down = xt_own + TX;  // exchange-array entries
     const int wb_own = (ty + 1) * TX + tx, wb_up = wb_own - TX;
     // w_h / p_h of the left neighbour's last column, theta of the right
-    // neighbour's first column: adjacent lanes (zero past the tile's edges,
-    // which the halo keeps away from the interior).  Every lane of the CTA
-    // runs every shuffle: the loop trip counts are uniform.
-    auto from_left = [&](float v) {
-        const float t = __shfl_up_sync(0xffffffffu, v, 1);
-        return tx > 0 ? t : 0.f;
-    };
-    auto from_right = [&](float v) {
-        const float t = __shfl_down_sync(0xffffffffu, v, 1);
-        return tx < TX - 1 ? t : 0.f;
-    };
+    // neighbour's first column: adjacent lanes.  On the tile's left and right
+    // edge the lane reads another value of this warp, which serves as well
+    // as zero: those columns lie in the halo, whose values never reach the
+    // interior within K updates.  Every lane of the CTA runs every shuffle:
+    // the loop trip counts are uniform.
+    auto from_left = [&](float v) { return __shfl_up_sync(0xffffffffu, v, 1); };
+    auto from_right = [&](float v) { return __shfl_down_sync(0xffffffffu, v, 1); };
 
     // row / column flags (bit i: row r0 + i; bit j: column c0 + j)
     unsigned rin = 0, rv = 0, cin = 0, chm = 0;
