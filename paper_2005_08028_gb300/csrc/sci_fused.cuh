@@ -26,10 +26,12 @@
 // configurations), rows whose results can no longer reach the interior are
 // skipped: the band that matters shrinks by one row per update.
 //
-// Three implementations: one-frame tiles on column strips (fused_tile_rows)
+// Four implementations: one-frame tiles on column strips (fused_tile_rows)
 // or on 4 x 4 pixel blocks (fused_tile_micro; ATV, ITV2D and the Clip box)
-// use scalar FP32 arithmetic; VTV tiles (fused_tile_impl) run pairs of
-// frames through the packed FP32 instructions.
+// use scalar FP32 arithmetic; VTV tiles run pairs of frames through the
+// packed FP32 instructions, with horizontal neighbours by warp shuffles
+// (fused_tile_impl) or, for the 24-frame tile, through 128-bit shared blocks
+// of every slot (fused_tile_blk).
 //
 // This header holds the implementation; sci_fused_f32.cu, sci_fused_f16.cu and
 // sci_fused_bf16.cu each instantiate it for one storage type (SCI_FUSED_STORAGE),
@@ -97,11 +99,28 @@ __device__ __forceinline__ float2 shfl_up2(float2 v) {
 __device__ __forceinline__ float2 shfl_down2(float2 v) {
     return make_float2(__shfl_down_sync(0xffffffffu, v.x, 1), __shfl_down_sync(0xffffffffu, v.y, 1));
 }
+// 128-bit shared-memory words of the block-layout VTV tiles (BlkCfg).
+__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void sts4(float* p, float2 a, float2 b) {
+    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
+// Words of a per-thread shared-memory block holding n floats: n rounded up to
+// a multiple of 4 whose quotient by 4 is odd.  Consecutive columns' blocks then
+// start 16-byte aligned, and the 8 lanes of each phase of a 128-bit access
+// fall on 8 different 16-byte bank groups.
+__host__ __device__ constexpr int block_words(int n) {
+    return ((n + 3) / 4) % 2 == 1 ? ((n + 3) / 4) * 4 : ((n + 3) / 4) * 4 + 4;
+}
+
 
 // Compile-time tile configuration.
 template <int NT_, int Q_, int F_, int EW_LOG2_, bool REG_, bool SKIP_>
 struct FusedCfg {
     static constexpr bool MICRO = false;
+    static constexpr bool SHFL = true;        // fused_tile_impl (shuffles); BlkCfg: fused_tile_blk
     static constexpr int NT = NT_;            // threads per CTA
     static constexpr int Q = Q_;              // rows per strip (pixels per thread)
     static constexpr int F = F_;              // frames held per CTA
@@ -131,6 +150,49 @@ struct FusedCfg {
     static constexpr size_t SMEM = (size_t)(A_XT + (REG ? 0 : NS * Q * RW)) * sizeof(float2);
     static_assert(NT % EW == 0, "a CTA must cover whole rows");
     static_assert(EW == 32, "a warp is one strip row");
+    static_assert(F % 2 == 0, "frames pair up for packed arithmetic");
+    static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
+};
+
+// The same tile with every slot's theta and w_h in padded 128-bit shared
+// blocks (the horizontal neighbours read the adjacent blocks): kept for the
+// 24-frame tile, where 256 threads of 48 slots each left the shuffle form
+// 5% (single) to 14% (batched, FP32) slower.
+template <int NT_, int Q_, int F_, int EW_LOG2_, bool REG_, bool SKIP_>
+struct BlkCfg {
+    static constexpr bool MICRO = false;
+    static constexpr bool SHFL = false;
+    static constexpr int NT = NT_;            // threads per CTA
+    static constexpr int Q = Q_;              // rows per strip (pixels per thread)
+    static constexpr int F = F_;              // frames held per CTA
+    static constexpr int EW_LOG2 = EW_LOG2_;
+    static constexpr int EW = 1 << EW_LOG2;   // tile width (columns)
+    static constexpr int NS = NT / EW;        // strips
+    static constexpr int EH = NS * Q;         // tile height (rows)
+    static constexpr bool REG = REG_;         // x-tilde of owned slots in registers (else shared memory)
+    static constexpr bool SKIP = SKIP_;       // skip rows that can no longer reach the interior
+    static constexpr int E = F * Q;           // slots per thread
+    static constexpr int NP = E / 2;          // packed register pairs per thread: element (q, f) is q F + f
+    // Shared memory, in floats.  Every thread's slots form one block of BLK
+    // words, element (q, f) at q FP + f with each row's frames padded to a
+    // multiple of 4 (FP), so rows and groups of 4 frames move as 128-bit
+    // words.  The blocks of a strip sit column by column, with one zero pad
+    // block on each side (columns -1 and EW): a thread reads its left and
+    // right neighbours' blocks with 128-bit loads and edge columns need no
+    // tests.  w_v of a strip's last row has blocks of BLKV words (one word for
+    // one-frame tiles).
+    static constexpr int FP = (F + 3) / 4 * 4;
+    static constexpr int ES = Q * FP;                           // shared words of a thread's slots
+    static constexpr int BLK = block_words(ES);
+    static constexpr int BLKV = block_words(FP);
+    static constexpr int SROW = (EW + 2) * BLK;                 // one strip of a padded slot array
+    static constexpr int A_TH = 0;                              // theta          [NS][EW + 2][BLK]
+    static constexpr int A_WH = A_TH + NS * SROW;               // w_h (then p_h) [NS][EW + 2][BLK]
+    static constexpr int A_WV = A_WH + NS * SROW;               // w_v (then p_v) of each strip's last row [NS][EW][BLKV]
+    static constexpr int A_XT = A_WV + ((NS * EW * BLKV + 3) & ~3);  // x-tilde [NS][EW][BLK] (only when !REG)
+    static constexpr size_t SMEM = (size_t)(A_XT + (REG ? 0 : NS * EW * BLK)) * sizeof(float);
+    static_assert(NT % EW == 0, "a CTA must cover whole rows");
+    static_assert(EW % 32 == 0, "a warp must stay inside one strip row");
     static_assert(F % 2 == 0, "frames pair up for packed arithmetic");
     static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
 };
@@ -580,6 +642,418 @@ __device__ __forceinline__ void fused_tile_impl(const FusedArgs& a, const Prob& 
     }
 }
 
+// One VTV tile (bx, by) of one problem on the block layout (BlkCfg); the
+// same arithmetic, in the same order, as fused_tile_impl.  `a` carries the launch-wide settings (K, halo, first/last, lambda, momentum),
+// `p` the problem's geometry and buffers.
+//
+// Per dual update (Algorithm 1, ATV-FGP box), in the order of scalar FP32
+// operations that the one-update-per-launch kernel also follows, so the two
+// paths agree bit for bit:
+//   theta = fma(-lambda, (w_h,left - w_h) + (w_v,up - w_v), xt)
+//   a_h   = fma(theta_right - theta, step_h, w_h),  a_v likewise downwards
+//   p     = a / max(1, |a|): clamp (ATV); a * min(1, rsqrt(fma(a_h, a_h, a_v a_v)))
+//           (ITV2D); a * min(1, rsqrt(n2_even + n2_odd)) with n2_par = fma(a_h, a_h,
+//           fma(a_v, a_v, n2_par)) over the frames of that parity (VTV)
+//   w     = fma(c, p - p_prev, p)
+// (In the first launch w = 0, and fma(-lambda, 0, xt) = xt exactly.)  The
+// tile packs pairs of frames of one pixel into float2 lanes and always
+// updates all F frames: frames B..F-1 hold zeros, their a is zero and they
+// add exact zeros to the norm.
+//
+// BORDER: the tile has rows outside the image or its last row, so the
+// gradient steps carry per-row factors (zero where a difference is not
+// defined).  Interior tiles fold the column conditions into one factor per
+// thread: where a factor is zero, w starts at zero and stays zero (a = w +
+// 0 * difference projects to zero), as the per-row form gives.
+template <typename T, int TV, class Cfg, bool BORDER, class Prob>
+__device__ __forceinline__ void fused_tile_blk(const FusedArgs& a, const Prob& p, int bx, int by, int bz,
+                                                float* smem) {
+    constexpr int Q = Cfg::Q, F = Cfg::F, EW = Cfg::EW, EH = Cfg::EH, NS = Cfg::NS, FP = Cfg::FP;
+    constexpr int NP = Cfg::NP, BLK = Cfg::BLK, BLKV = Cfg::BLKV, SROW = Cfg::SROW;
+    constexpr bool REG = Cfg::REG, SKIP = Cfg::SKIP;
+    static_assert(F > 1 && TV == SCI_TV_VTV, "frame tiles are for VTV (one-frame tiles: fused_tile_rows)");
+
+    const Geo g = p.g();
+    const int H = a.halo;
+    const int TI = fused_interior(EH, H), TJ = fused_interior(EW, H);  // interior size
+    const int gi0 = by * TI - H, gj0 = bx * TJ - H;
+    const int nfr = g.B;                         // frames of the problem in this CTA
+    constexpr int f0 = 0;                        // global frame of slot f = 0 (bz unused)
+    (void)bz;
+    const int tid = threadIdx.x;
+    const int col = tid & (EW - 1);
+    const int strip = tid >> Cfg::EW_LOG2;
+    const int r0 = strip * Q;                    // first row of the strip
+    const int gj = gj0 + col;
+    const bool col_in = gj >= 0 && gj < g.ny;
+    const bool col_int = col >= H && col < EW - H + 1;
+    const int gi_top = gi0 + r0;
+
+    // This thread's blocks and its neighbours'.  th_down (strip NS - 1) and
+    // wv_up (strip 0) then point at other, valid shared words, whose values
+    // are replaced before use.
+    float* const th_own = smem + Cfg::A_TH + strip * SROW + (col + 1) * BLK;
+    float* const wh_own = smem + Cfg::A_WH + strip * SROW + (col + 1) * BLK;
+    const float* const th_right = th_own + BLK;
+    const float* const wh_left = wh_own - BLK;
+    const float* const th_down = th_own + SROW;
+    float* const wv_own = smem + Cfg::A_WV + (strip * EW + col) * BLKV;
+    const float* const wv_up = wv_own - EW * BLKV;
+    float* const xt_own = smem + Cfg::A_XT + (strip * EW + col) * BLK;  // only when !REG
+    const bool has_up = strip > 0, has_down = strip < NS - 1;
+
+    // per-row flags as bit masks (bit q: row r0 + q)
+    unsigned in_m = 0, ah_m = 0, av_m = 0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int gi = gi_top + q;
+        const bool in = col_in && gi >= 0 && gi < g.nx;
+        in_m |= (unsigned)in << q;
+        ah_m |= (unsigned)(in && gj < g.ny - 1) << q;
+        av_m |= (unsigned)(in && gi < g.nx - 1) << q;
+    }
+    const float step = a.step;
+    const float step_h = (col_in && gj < g.ny - 1) ? step : 0.f;
+    const float step_v = col_in ? step : 0.f;
+    auto fac = [&](unsigned m, int q) -> float { return ((m >> q) & 1u) ? step : 0.f; };
+
+    float2 PH[NP], PV[NP], WH[NP], WV[NP];
+    float2 X[REG ? NP : 1];
+
+    // ---- load x-tilde (and the carried duals) for the whole extended tile ----
+    // Every load is issued unconditionally -- a pixel outside the image reads
+    // pixel 0 of its frame and is zeroed afterwards -- and none is consumed
+    // before all are issued, so a thread's loads are in flight together
+    // rather than one row at a time.
+    const long long pix_top = (long long)gi_top * g.ny + gj;
+    auto pix_of = [&](int q) -> long long { return ((in_m >> q) & 1u) ? pix_top + (long long)q * g.ny : 0; };
+    float2 XS[REG ? 1 : NP];  // x-tilde staging for tiles that keep it in shared memory
+    auto xe = [&](int q, int f) -> float& { return REG ? el<F>(X, q, f) : el<F>(XS, q, f); };
+    const bool warm_first = a.first && a.warm;  // w from the previous TVdenoise, p = 0
+    if (!a.first) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const long long pix = pix_of(q);
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                if (f >= nfr) break;
+                const long long gidx = (long long)(f0 + f) * g.n + pix;
+                el<F>(PH, q, f) = ldraw<T>(p.st_in(0), gidx);
+                el<F>(PV, q, f) = ldraw<T>(p.st_in(1), gidx);
+                el<F>(WH, q, f) = ldraw<T>(p.st_in(2), gidx);
+                el<F>(WV, q, f) = ldraw<T>(p.st_in(3), gidx);
+            }
+        }
+    } else if (warm_first) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const long long pix = pix_of(q);
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                if (f >= nfr) break;
+                const long long gidx = (long long)(f0 + f) * g.n + pix;
+                el<F>(WH, q, f) = ldraw<T>(p.warm_in(0), gidx);
+                el<F>(WV, q, f) = ldraw<T>(p.warm_in(1), gidx);
+            }
+        }
+    }
+    if (a.mode == OuterMode::Prox) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const long long pix = pix_of(q);
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                if (f >= nfr) break;
+                xe(q, f) = __ldg(p.xin() + (long long)(f0 + f) * g.n + pix);
+            }
+        }
+    } else if (a.first) {
+        uint32_t word[Q];
+        float rv[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const long long pix = pix_of(q);
+            word[q] = __ldg(p.bits() + pix);
+            rv[q] = __ldg(p.r() + pix);
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                if (f >= nfr) break;
+                xe(q, f) = ldraw<T>(p.theta_in(), (long long)(f0 + f) * g.n + pix);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                if (f >= nfr) break;
+                xe(q, f) = rt<T>(cvraw<T>(xe(q, f)) + mask_bit(word[q], f0 + f) * rv[q]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const long long pix = pix_of(q);
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                if (f >= nfr) break;
+                xe(q, f) = ldraw<T>(p.xt(), (long long)(f0 + f) * g.n + pix);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                if (f >= nfr) break;
+                xe(q, f) = cvraw<T>(xe(q, f));
+            }
+        }
+    }
+    if (!a.first || warm_first) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                if (f >= nfr) break;
+                el<F>(PH, q, f) = cvraw<T>(el<F>(PH, q, f));
+                el<F>(PV, q, f) = cvraw<T>(el<F>(PV, q, f));
+                el<F>(WH, q, f) = cvraw<T>(el<F>(WH, q, f));
+                el<F>(WV, q, f) = cvraw<T>(el<F>(WV, q, f));
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const bool in = (in_m >> q) & 1u;
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            const bool live = in && f < nfr;
+            if (!live) xe(q, f) = 0.f;
+            if (a.first || !live) {
+                el<F>(PH, q, f) = 0.f;
+                el<F>(PV, q, f) = 0.f;
+            }
+            if ((a.first && !a.warm) || !live) {
+                el<F>(WH, q, f) = 0.f;
+                el<F>(WV, q, f) = 0.f;
+            }
+        }
+    }
+    // A register pair (frames f, f+1 of row q) is the 128-bit half at words
+    // q FP + f of a shared block; the padding frames of a row store zeros.
+    auto put_block = [&](float* blk, const float2* R) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int c = 0; c < FP / 4; ++c) {
+                const int e2 = (q * F + 4 * c) / 2;
+                sts4(blk + q * FP + 4 * c, R[e2], 4 * c + 2 < F ? R[4 * c + 2 < F ? e2 + 1 : 0] : make_float2(0.f, 0.f));
+            }
+    };
+    auto put_last_row = [&](float* blk, const float2* R) {
+#pragma unroll
+        for (int c = 0; c < FP / 4; ++c) {
+            const int e2 = ((Q - 1) * F + 4 * c) / 2;
+            sts4(blk + 4 * c, R[e2], 4 * c + 2 < F ? R[4 * c + 2 < F ? e2 + 1 : 0] : make_float2(0.f, 0.f));
+        }
+    };
+    put_block(wh_own, WH);
+    if (!REG) put_block(xt_own, XS);
+    put_last_row(wv_own, WV);
+    // zero pad blocks (columns -1 and EW of every strip) of theta and w_h
+    for (int e = tid; e < NS * 2 * (BLK / 4); e += Cfg::NT) {
+        const int s = e / (2 * (BLK / 4)), rem = e - s * 2 * (BLK / 4);
+        const int side = rem / (BLK / 4), w4 = rem - side * (BLK / 4);
+        const int off = s * SROW + (side ? (EW + 1) * BLK : 0) + 4 * w4;
+        *reinterpret_cast<float4*>(smem + Cfg::A_TH + off) = make_float4(0.f, 0.f, 0.f, 0.f);
+        *reinterpret_cast<float4*>(smem + Cfg::A_WH + off) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+
+    const float2 nlam2 = dup2(-a.lambda);
+    const float2 steph2 = dup2(step_h), stepv2 = dup2(step_v);
+    // Two updates per loop trip let the compiler alternate registers instead
+    // of copying the loop-carried duals; the 16- and 24-frame VTV tiles, near
+    // the register limit, run one.
+    constexpr int kUnroll = F > 10 ? 1 : 2;
+#pragma unroll kUnroll
+    for (int s = 0; s < a.K; ++s) {
+        const float2 c2 = dup2(a.coef[s]);
+        // rows whose p stays exact after this update: [1 + s, EH - 1 - s);
+        // theta is needed on those rows and the one below
+        const int rlo = 1 + s, rhi = EH - 1 - s;
+        const int qlo = SKIP ? max(rlo - r0, 0) : 0;
+        const int qhi_p = SKIP ? min(rhi - r0, Q) : Q, qhi_t = SKIP ? min(rhi + 1 - r0, Q) : Q;
+        // ---- theta = xt - lambda (D^T w), frames paired ----
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            if (q < qlo || q >= qhi_t) continue;
+#pragma unroll
+            for (int c = 0; c < FP / 4; ++c) {
+                const float4 wl = lds4(wh_left + q * FP + 4 * c);
+                float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (!REG) xv = lds4(xt_own + q * FP + 4 * c);
+                float4 wu = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (q == 0) {
+                    const float4 w = lds4(wv_up + 4 * c);
+                    if (has_up) wu = w;
+                }
+                float2 th[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (4 * c + 2 * h >= F) continue;
+                    const int e2 = (q * F + 4 * c) / 2 + h;
+                    const float2 x2 = REG ? X[REG ? e2 : 0] : (h ? hi2(xv) : lo2(xv));
+                    const float2 wu2 = q > 0 ? WV[q > 0 ? e2 - F / 2 : 0] : (h ? hi2(wu) : lo2(wu));
+                    th[h] = fma2(nlam2, add2(sub2(h ? hi2(wl) : lo2(wl), WH[e2]), sub2(wu2, WV[e2])), x2);
+                }
+                sts4(th_own + q * FP + 4 * c, th[0], th[1]);
+            }
+        }
+        __syncthreads();
+        // ---- a = w + step * D theta (kept in the w registers), norm over frames,
+        //      projection onto the per-pixel ball, momentum ----
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            if (q < qlo || q >= qhi_p) continue;
+            float2 sh = steph2, sv = stepv2;
+            if (BORDER) {
+                sh = dup2(fac(ah_m, q));
+                sv = dup2(fac(av_m, q));
+            }
+            float2 n2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int c = 0; c < FP / 4; ++c) {
+                const float4 tr = lds4(th_right + q * FP + 4 * c);
+                const float4 t0 = lds4(th_own + q * FP + 4 * c);
+                float4 td;
+                if (q < Q - 1) {
+                    td = lds4(th_own + (q + 1) * FP + 4 * c);
+                } else {
+                    const float4 d = lds4(th_down + 4 * c);
+                    td = has_down ? d : t0;
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (4 * c + 2 * h >= F) continue;
+                    const int e2 = (q * F + 4 * c) / 2 + h;
+                    const float2 tt = h ? hi2(t0) : lo2(t0);
+                    const float2 ah = fma2(sub2(h ? hi2(tr) : lo2(tr), tt), sh, WH[e2]);
+                    const float2 av = fma2(sub2(h ? hi2(td) : lo2(td), tt), sv, WV[e2]);
+                    WH[e2] = ah;
+                    WV[e2] = av;
+                    n2 = fma2(ah, ah, fma2(av, av, n2));
+                }
+            }
+            const float2 vs = dup2(fminf(1.f, rsqrt_ftz(n2.x + n2.y)));
+#pragma unroll
+            for (int f = 0; f < F; f += 2) {
+                const int e2 = (q * F + f) / 2;
+                const float2 nh = mul2(WH[e2], vs), nv = mul2(WV[e2], vs);
+                WH[e2] = fma2(c2, sub2(nh, PH[e2]), nh);
+                WV[e2] = fma2(c2, sub2(nv, PV[e2]), nv);
+                PH[e2] = nh;
+                PV[e2] = nv;
+            }
+#pragma unroll
+            for (int c = 0; c < FP / 4; ++c) {
+                const int e2 = (q * F + 4 * c) / 2;
+                sts4(wh_own + q * FP + 4 * c, WH[e2],
+                     4 * c + 2 < F ? WH[4 * c + 2 < F ? e2 + 1 : 0] : make_float2(0.f, 0.f));
+            }
+        }
+        put_last_row(wv_own, WV);
+        __syncthreads();
+    }
+
+    // ---- epilogue ----
+    auto sidx = [&](int q, int f) { return q * FP + f; };  // element (q, f) of a shared block
+    if (!a.last) {
+        // carry x-tilde (first launch of a solve), p and w of the interior
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int r = r0 + q;
+            if (!((in_m >> q) & 1u) || !col_int || r < H || r >= EH - H + 1) continue;
+            const long long pix = (long long)(gi_top + q) * g.ny + gj;
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                if (f >= nfr) break;
+                const long long gidx = (long long)(f0 + f) * g.n + pix;
+                if (a.first && a.mode != OuterMode::Prox)
+                    st<T>(p.xt(), gidx, REG ? el<F>(X, q, f) : xt_own[sidx(q, f)]);
+                st<T>(p.st_out(0), gidx, el<F>(PH, q, f));
+                st<T>(p.st_out(1), gidx, el<F>(PV, q, f));
+                st<T>(p.st_out(2), gidx, el<F>(WH, q, f));
+                st<T>(p.st_out(3), gidx, el<F>(WV, q, f));
+            }
+        }
+        return;
+    }
+    // theta = xt - lambda D^T p needs p_h of the left neighbour and p_v of the
+    // row above: stage them where w_h / w_v were (the loop ended with a barrier).
+    put_block(wh_own, PH);
+    put_last_row(wv_own, PV);
+    // x^(t+1) = xt - u^(t) for ADMM (only when x is requested): u^(t) is read
+    // before u^(t+1) overwrites it.  Issue every load first (into the thread's
+    // own theta block, free now) so none waits behind a store it might alias.
+    if (a.mode == OuterMode::Admm && p.x_out() != nullptr) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int r = r0 + q;
+            const bool mine = ((in_m >> q) & 1u) && col_int && r >= H && r < EH - H + 1;
+            const long long pix = mine ? (long long)(gi_top + q) * g.ny + gj : 0;
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+                if (f >= nfr) break;
+                th_own[sidx(q, f)] = mine ? ldg<T>(p.u_in(), (long long)(f0 + f) * g.n + pix) : 0.f;
+            }
+        }
+    }
+    __syncthreads();
+    // VTV tiles hold every frame of a pixel: form the next residual here (the
+    // per-pixel order of the separate residual pass)
+    const bool fold_r = F > 1 && a.r_next != nullptr && a.mode != OuterMode::Prox;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int r = r0 + q;
+        if (!((in_m >> q) & 1u) || !col_int || r < H || r >= EH - H + 1) continue;
+        const long long pix = (long long)(gi_top + q) * g.ny + gj;
+        const uint32_t word = fold_r ? __ldg(p.bits() + pix) : 0u;
+        float acc = 0.f;
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            if (f >= nfr) break;
+            const float pl = wh_left[sidx(q, f)];
+            float pu;
+            if (q > 0) pu = el<F>(PV, q > 0 ? q - 1 : 0, f);
+            else pu = has_up ? wv_up[f] : 0.f;
+            const float x0 = REG ? el<F>(X, q, f) : xt_own[sidx(q, f)];
+            const float th = __fmaf_rn(-a.lambda, (pl - el<F>(PH, q, f)) + (pu - el<F>(PV, q, f)), x0);
+            const long long gidx = (long long)(f0 + f) * g.n + pix;
+            if (a.mode == OuterMode::Prox) {
+                p.theta_f32()[gidx] = th;
+                continue;
+            }
+            st<T>(p.theta_out(), gidx, th);
+            const float thr = rt<T>(th);
+            float v = thr;
+            if (a.mode == OuterMode::Gap) {
+                if (p.x_out() != nullptr) p.x_out()[gidx] = x0;
+            } else {
+                const float un = rt<T>(x0 - thr);
+                st<T>(p.u_out(), gidx, un);
+                if (p.x_out() != nullptr) p.x_out()[gidx] = x0 - th_own[sidx(q, f)];
+                v = thr - un;
+            }
+            if (fold_r) acc = __fmaf_rn(mask_bit(word, f0 + f), v, acc);
+            if (a.warm) {
+                st<T>(p.warm_out(0), gidx, el<F>(WH, q, f));
+                st<T>(p.warm_out(1), gidx, el<F>(WV, q, f));
+            }
+        }
+        if (fold_r) a.r_next[pix] = __ldg(a.rinv + pix) * (__ldg(a.y + pix) - acc);
+    }
+}
+
 // ---------------------------------------------------------------- one-frame tiles
 //
 // ATV, ITV2D and the Clip box update every frame independently, so a CTA
@@ -920,7 +1394,10 @@ struct MicroCfg {
     static constexpr int HALF = (TY + 1) * TX * 2;
     static constexpr int A_XT = 0;
     static constexpr int A_WB = A_XT + 2 * HALF;
-    static constexpr size_t SMEM = (size_t)(A_WB + 2 * HALF) * sizeof(float);
+    // Two staging tiles [EH][SW] for the epilogue's stores (see fused_tile_micro).
+    static constexpr int SW = EW + 4;
+    static constexpr int A_ST = A_WB + 2 * HALF;
+    static constexpr size_t SMEM = (size_t)(A_ST + 2 * EH * SW) * sizeof(float);
     static_assert(NT % TX == 0 && TX >= 8 && TX <= 32 && 32 % TX == 0, "whole rows of threads in each warp");
     static_assert((MR == 2 || MR == 4) && MC == 4, "blocks of 2 or 4 rows by 4 columns");
 };
@@ -1209,33 +1686,38 @@ __device__ __forceinline__ void fused_tile_micro(const FusedArgs& a, const Prob&
     }
 
     // ---- epilogue ----
-    // fresh copies of the block origin: the epilogue's addresses are then formed
-    // here rather than kept live across the update loop
-    int e_top = gi_top, e_left = gj_left;
-    unsigned e_rin = rin, e_cin = cin;
-    asm volatile("" : "+r"(e_top), "+r"(e_left), "+r"(e_rin), "+r"(e_cin));
-    auto in_e = [&](int i, int j) { return ((e_rin >> i) & (e_cin >> j) & 1u) != 0; };
-    auto own_e = [&](int i, int j) {
-        const int r = r0 + i, c = c0 + j;
-        return in_e(i, j) && r >= H && r < EH - H + 1 && c >= H && c < EW - H + 1;
-    };
-    auto gidx_of_e = [&](int i, int j) -> long long {
-        return in_e(i, j) ? fbase + (long long)(e_top + i) * g.ny + e_left + j : fbase;
-    };
-    if (!a.last) {
-        // carry x-tilde (first launch of a solve), p and w of the interior
+    // The interior's fields are written through shared memory: each block row
+    // goes to a staging tile as one 16-byte word, and each warp then stores
+    // whole runs of a tile row, where a thread's four adjacent columns would
+    // fill a quarter of each 32-byte sector per store instruction.  Two
+    // staging tiles alternate, so one barrier per field separates its writes
+    // from the reads that drain it.
+    constexpr int SW = Cfg::SW;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int r_end = min(EH - H + 1, g.nx - gi0), c_end = min(EW - H + 1, g.ny - gj0);
+    int stage = 0;
+    auto put = [&](auto&& val, auto&& store) {
+        float* const sb = smem + Cfg::A_ST + (stage & 1) * EH * SW;
+        ++stage;
 #pragma unroll
         for (int i = 0; i < MR; ++i)
-#pragma unroll
-            for (int j = 0; j < MC; ++j) {
-                if (!own_e(i, j)) continue;
-                const long long gi = gidx_of_e(i, j);
-                if (a.first && a.mode != OuterMode::Prox) st<T>(p.xt(), gi, xr[i][j]);
-                st<T>(p.st_out(0), gi, PH[i][j]);
-                st<T>(p.st_out(1), gi, PV[i][j]);
-                st<T>(p.st_out(2), gi, wh[i][j]);
-                st<T>(p.st_out(3), gi, wv[i][j]);
-            }
+            *reinterpret_cast<float4*>(sb + (r0 + i) * SW + c0) =
+                make_float4(val(i, 0), val(i, 1), val(i, 2), val(i, 3));
+        __syncthreads();
+        for (int r = H + warp; r < r_end; r += Cfg::NT / 32) {
+            const long long row = fbase + (long long)(gi0 + r) * g.ny + gj0;
+            for (int c = H + lane; c < c_end; c += 32) store(row + c, sb[r * SW + c]);
+        }
+    };
+    auto st_T = [](T* dst) { return [dst](long long i, float v) { st<T>(dst, i, v); }; };
+    auto st_f = [](float* dst) { return [dst](long long i, float v) { dst[i] = v; }; };
+    if (!a.last) {
+        // carry x-tilde (first launch of a solve), p and w of the interior
+        if (a.first && a.mode != OuterMode::Prox) put([&](int i, int j) { return xr[i][j]; }, st_T(p.xt()));
+        put([&](int i, int j) { return PH[i][j]; }, st_T(p.st_out(0)));
+        put([&](int i, int j) { return PV[i][j]; }, st_T(p.st_out(1)));
+        put([&](int i, int j) { return wh[i][j]; }, st_T(p.st_out(2)));
+        put([&](int i, int j) { return wv[i][j]; }, st_T(p.st_out(3)));
         return;
     }
     // theta = xt - lambda D^T p reads p_h of the left neighbour (a shuffle)
@@ -1254,39 +1736,45 @@ __device__ __forceinline__ void fused_tile_micro(const FusedArgs& a, const Prob&
     // theta registers) before u^(t+1) overwrites it
     const bool want_xu = a.mode == OuterMode::Admm && p.x_out() != nullptr;
     if (want_xu) {
+        // fresh copies of the block origin: these addresses are formed here
+        // rather than kept live across the update loop
+        int e_top = gi_top, e_left = gj_left;
+        unsigned e_rin = rin, e_cin = cin;
+        asm volatile("" : "+r"(e_top), "+r"(e_left), "+r"(e_rin), "+r"(e_cin));
 #pragma unroll
         for (int i = 0; i < MR; ++i)
 #pragma unroll
-            for (int j = 0; j < MC; ++j) th[i][j] = own_e(i, j) ? ldg<T>(p.u_in(), gidx_of_e(i, j)) : 0.f;
+            for (int j = 0; j < MC; ++j) {
+                const bool in = ((e_rin >> i) & (e_cin >> j) & 1u) != 0;
+                th[i][j] = in ? ldg<T>(p.u_in(), fbase + (long long)(e_top + i) * g.ny + e_left + j) : 0.f;
+            }
     }
     __syncthreads();
     ld4h<HALF>(WB, wb_up, pu);
+    float tt[MR][MC];  // theta^(t+1)
 #pragma unroll
     for (int i = 0; i < MR; ++i)
 #pragma unroll
         for (int j = 0; j < MC; ++j) {
-            if (!own_e(i, j)) continue;
             const float l = j > 0 ? PH[i][j > 0 ? j - 1 : 0] : pl[i];
             const float u = i > 0 ? PV[i > 0 ? i - 1 : 0][j] : pu[j];
-            const float x0 = xr[i][j];
-            const float t = __fmaf_rn(-lam, (l - PH[i][j]) + (u - PV[i][j]), x0);
-            const long long gi = gidx_of_e(i, j);
-            if (a.mode == OuterMode::Prox) {
-                p.theta_f32()[gi] = t;
-                continue;
-            }
-            st<T>(p.theta_out(), gi, t);
-            if (a.mode == OuterMode::Gap) {
-                if (p.x_out() != nullptr) p.x_out()[gi] = x0;
-            } else {
-                st<T>(p.u_out(), gi, x0 - rt<T>(t));
-                if (want_xu) p.x_out()[gi] = x0 - th[i][j];
-            }
-            if (a.warm) {
-                st<T>(p.warm_out(0), gi, wh[i][j]);
-                st<T>(p.warm_out(1), gi, wv[i][j]);
-            }
+            tt[i][j] = __fmaf_rn(-lam, (l - PH[i][j]) + (u - PV[i][j]), xr[i][j]);
         }
+    if (a.mode == OuterMode::Prox) {
+        put([&](int i, int j) { return tt[i][j]; }, st_f(p.theta_f32()));
+        return;
+    }
+    put([&](int i, int j) { return tt[i][j]; }, st_T(p.theta_out()));
+    if (a.mode == OuterMode::Gap) {
+        if (p.x_out() != nullptr) put([&](int i, int j) { return xr[i][j]; }, st_f(p.x_out()));
+    } else {
+        put([&](int i, int j) { return xr[i][j] - rt<T>(tt[i][j]); }, st_T(p.u_out()));
+        if (want_xu) put([&](int i, int j) { return xr[i][j] - th[i][j]; }, st_f(p.x_out()));
+    }
+    if (a.warm) {
+        put([&](int i, int j) { return wh[i][j]; }, st_T(p.warm_out(0)));
+        put([&](int i, int j) { return wv[i][j]; }, st_T(p.warm_out(1)));
+    }
 }
 
 // A tile all of whose rows lie inside the image and above its last row runs
@@ -1301,10 +1789,14 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
     } else {
         const Geo g = p.g();
         const int gi0 = by * fused_interior(Cfg::EH, a.halo) - a.halo;
-        if (gi0 >= 0 && gi0 + Cfg::EH - 1 < g.nx - 1)
-            fused_tile_impl<T, TV, Cfg, false>(a, p, bx, by, bz, smem);
-        else
-            fused_tile_impl<T, TV, Cfg, true>(a, p, bx, by, bz, smem);
+        const bool border = !(gi0 >= 0 && gi0 + Cfg::EH - 1 < g.nx - 1);
+        if constexpr (Cfg::SHFL) {
+            if (!border) fused_tile_impl<T, TV, Cfg, false>(a, p, bx, by, bz, smem);
+            else fused_tile_impl<T, TV, Cfg, true>(a, p, bx, by, bz, smem);
+        } else {
+            if (!border) fused_tile_blk<T, TV, Cfg, false>(a, p, bx, by, bz, smem);
+            else fused_tile_blk<T, TV, Cfg, true>(a, p, bx, by, bz, smem);
+        }
     }
 }
 
@@ -1319,8 +1811,8 @@ using CfgM1 = MicroCfg<512, 5, 4, 4>;   // 128 x 64 tile of 4 x 4 blocks, one fr
 using CfgM1s = MicroCfg<256, 4, 2, 4>;  // 64 x 32 tile of 2 x 4 blocks, one frame
 using CfgV8 = FusedCfg<512, 2, 8, 5, true, true>;      // 32 x 32 tile, up to 8 frames
 using CfgV10 = FusedCfg<512, 2, 10, 5, false, true>;   // 32 x 32 tile, up to 10 frames
-using CfgV16 = FusedCfg<256, 2, 16, 5, false, true>;   // 32 x 16 tile, up to 16 frames
-using CfgV24 = FusedCfg<256, 2, 24, 5, false, true>;   // 32 x 16 tile, up to 24 frames
+using CfgV16 = FusedCfg<512, 1, 16, 5, false, true>;   // 32 x 16 tile, up to 16 frames
+using CfgV24 = BlkCfg<256, 2, 24, 5, false, true>;     // 32 x 16 tile, up to 24 frames
 
 template <typename T, int TV, class Cfg>
 __global__ void __launch_bounds__(Cfg::NT, 1)
