@@ -2004,7 +2004,7 @@ template <typename T, int TV>
 bool launch_batched_tv(int cls, const FusedArgs& a, const BatchItem<T>* items, int nitems, int total, int tpar,
                        int spar, int want_x, cudaStream_t s) {
     if constexpr (TV != SCI_TV_VTV) {
-        return launch_batched_cfg<T, TV, CfgF1>(type_slot<T>(TV, 0), a, items, nitems, total, tpar, spar, want_x,
+        return launch_batched_cfg<T, TV, CfgM1>(type_slot<T>(TV, 6), a, items, nitems, total, tpar, spar, want_x,
                                                 s);
     } else {
         switch (cls) {
