@@ -15,7 +15,7 @@
 // projection pass), the last writes theta' (and u', x).  VTV tiles, which
 // hold every frame of a pixel, also form the next residual r in that last
 // launch; ATV / ITV2D tiles hold one frame, so one light residual pass
-// (128-bit loads) follows their last launch.  The per-update path
+// (with 128-bit loads for fields above 64 MiB) follows their last launch.  The per-update path
 // (fuse_k = -1) runs S launches of one dual update and an output kernel
 // that forms the next residual.
 #include <algorithm>
