@@ -54,6 +54,15 @@ constexpr uint32_t kRowBytes = kC * 2;                       // 64 B per voxel
 constexpr uint32_t kABytes = kBW * (kBH + 2) * kRowBytes;    // 12 KB per A stage
 constexpr uint32_t kWTapBytes = kC * kC * 2;       // 2 KB per tap
 constexpr uint32_t kWBytes = 27 * kWTapBytes;      // 54 KB
+// The 32 -> 1 output layer runs the same kernel with N = 16: one 16-row
+// weight block per (dz, dy) pair holds output channel 0 of its three dx taps
+// (rows 0-2) and zeros (rows 3-15), so an MMA computes G_-1, G_0, G_+1 of that
+// channel in accumulator columns 0-2 (an N = 96 form would carry 31 zero
+// channels per tap).
+constexpr int kN1 = 16;
+constexpr uint32_t kW1PairBytes = kN1 * kC * 2;    // 1 KB per (dz, dy) pair
+constexpr uint32_t kW1Bytes = 9 * kW1PairBytes;    // 9 KB
+template <int NN> constexpr uint32_t w_bytes() { return NN == kN ? kWBytes : kW1Bytes; }
 constexpr long long kSpinLimit = 1LL << 26;        // bounded mbarrier waits
 
 // ---- PTX helpers --------------------------------------------------------
@@ -113,15 +122,18 @@ __device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
     return d;
 }
 
-// kind::f16 instruction descriptor: D = FP32, A = B = BF16, both K-major, M = 128, N = 96.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
-                            ((uint32_t)(kTileM >> 4) << 24);
+// kind::f16 instruction descriptor: D = FP32, A = B = BF16, both K-major, M = 128, N = NN.
+template <int NN>
+constexpr uint32_t idesc() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NN >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
+}
 
+template <int NN>
 __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        "l"(adesc), "l"(bdesc), "r"(idesc<NN>()), "r"(accumulate)
         : "memory");
 }
 
@@ -170,13 +182,15 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // overlaps the MMAs of tile j + 1 and the loads run ahead across tiles.
 constexpr int kThreads = 192;
 
+template <int NN>
 __global__ void __launch_bounds__(kThreads, 1)
 k_conv3d_c32_tc(const __grid_constant__ CUtensorMap act_map, const __grid_constant__ CUtensorMap w_map,
                 ConvTcArgs a) {
+    static_assert(NN == kN || NN == kN1, "the 32-channel form or the one-channel output form");
     extern __shared__ __align__(1024) unsigned char dsmem[];
     unsigned char* base = (unsigned char*)(((uintptr_t)dsmem + 1023) & ~(uintptr_t)1023);
     unsigned char* s_w = base;                        // 27 x 2 KB weights
-    unsigned char* s_a = base + kWBytes;              // kStages x 8 KB A ring
+    unsigned char* s_a = base + w_bytes<NN>();        // kStages x 12 KB A ring
     uint64_t* bars = reinterpret_cast<uint64_t*>(s_a + kStages * kABytes);
     // bars: full[kStages], empty[kStages], acc_full[2], acc_empty[2], weights, drain
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 6);
@@ -214,8 +228,12 @@ k_conv3d_c32_tc(const __grid_constant__ CUtensorMap act_map, const __grid_consta
 
     if (warp == 4 && lane == 0) {
         // ---------------- TMA producer ----------------
-        mbar_expect_tx(bar_w, kWBytes);
-        for (int t = 0; t < 27; ++t) tma_load_3d(smem_u32(s_w + t * kWTapBytes), &w_map, bar_w, 0, 0, t);
+        mbar_expect_tx(bar_w, w_bytes<NN>());
+        if constexpr (NN == kN) {
+            for (int t = 0; t < 27; ++t) tma_load_3d(smem_u32(s_w + t * kWTapBytes), &w_map, bar_w, 0, 0, t);
+        } else {
+            for (int t = 0; t < 9; ++t) tma_load_3d(smem_u32(s_w + t * kW1PairBytes), &w_map, bar_w, 0, 0, t);
+        }
         uint32_t q = 0;
         long long issued_tiles = 0;
         for (long long j = 0; j < my_tiles && !*s_abort; ++j) {
@@ -255,12 +273,14 @@ k_conv3d_c32_tc(const __grid_constant__ CUtensorMap act_map, const __grid_consta
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
                 for (int dyi = 0; dyi < 3; ++dyi) {
-                    // taps (dz, dy, dx = -1..+1) are consecutive 2 KB blocks: one N = 96 operand
+                    // taps (dz, dy, dx = -1..+1) are consecutive 2 KB blocks: one N = 96
+                    // operand (N = 16: the pair's 1 KB block)
                     const int t = k * 9 + dyi * 3;
                     const uint32_t abase = smem_u32(s_a + s * kABytes) + (uint32_t)dyi * kBW * kRowBytes;
-                    const uint32_t bbase = smem_u32(s_w + t * kWTapBytes);
-                    umma_bf16(d, smem_desc_sw64(abase), smem_desc_sw64(bbase), (k > 0 || dyi > 0) ? 1u : 0u);
-                    umma_bf16(d, smem_desc_sw64(abase + 32), smem_desc_sw64(bbase + 32), 1u);
+                    const uint32_t bbase = NN == kN ? smem_u32(s_w + t * kWTapBytes)
+                                                    : smem_u32(s_w + (k * 3 + dyi) * kW1PairBytes);
+                    umma_bf16<NN>(d, smem_desc_sw64(abase), smem_desc_sw64(bbase), (k > 0 || dyi > 0) ? 1u : 0u);
+                    umma_bf16<NN>(d, smem_desc_sw64(abase + 32), smem_desc_sw64(bbase + 32), 1u);
                 }
                 umma_commit(bar_empty + 8 * s);
             }
@@ -291,6 +311,14 @@ k_conv3d_c32_tc(const __grid_constant__ CUtensorMap act_map, const __grid_consta
             const uint32_t lanes = (uint32_t)(warp * 32) << 16;
             const bool one = a.mode == 3;  // only output channel 0 is used
             tmem_ld_32cols(tmem + b * kAccCols + lanes, v);
+            if constexpr (NN == kN1) {
+                // columns 0-2: G_-1, G_0, G_+1 of output channel 0
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar_acce + 8 * b);
+                v[0] += __shfl_down_sync(0xffffffffu, v[1], 1);
+                v[0] += __shfl_down_sync(0xffffffffu, v[2], 2);
+            } else {
             tmem_ld_32cols(tmem + b * kAccCols + 32 + lanes, g);
             if (one) {
                 v[0] += __shfl_down_sync(0xffffffffu, g[0], 1);
@@ -307,6 +335,7 @@ k_conv3d_c32_tc(const __grid_constant__ CUtensorMap act_map, const __grid_consta
             } else {
 #pragma unroll
                 for (int c = 0; c < 32; ++c) v[c] += __shfl_down_sync(0xffffffffu, g[c], 2);
+            }
             }
             long long tr = blockIdx.x + j * gridDim.x;
             const int tw = (int)(tr % a.tiles_w); tr /= a.tiles_w;
@@ -368,10 +397,13 @@ EncodeFn encode_fn() {
 
 }  // namespace
 
-size_t conv3d_c32_tc_smem() { return kWBytes + kStages * kABytes + 1024 + 256; }  // 2 CTAs per SM
+// 2 CTAs per SM (the N = 96 form)
+template <int NN>
+size_t conv_smem() { return w_bytes<NN>() + kStages * kABytes + 1024 + 256; }
 
 namespace {
 
+template <int NN>
 bool launch_conv(const __nv_bfloat16* act, const __nv_bfloat16* w, ConvTcArgs a, cudaStream_t s) {
     EncodeFn enc = encode_fn();
     if (enc == nullptr) return false;
@@ -395,18 +427,20 @@ bool launch_conv(const __nv_bfloat16* act, const __nv_bfloat16* w, ConvTcArgs a,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return false;
-    const cuuint64_t wdims[3] = {(cuuint64_t)kC, (cuuint64_t)kC, 27};
-    const cuuint64_t wstr[2] = {(cuuint64_t)kC * 2, (cuuint64_t)kC * kC * 2};
-    const cuuint32_t wbox[3] = {(cuuint32_t)kC, (cuuint32_t)kC, 1};
+    // weights: [27][32 out][32 in] (N = 96), or [9][16][32] (N = 16: the one-channel layer)
+    const cuuint32_t wrows = NN == kN ? (cuuint32_t)kC : (cuuint32_t)kN1;
+    const cuuint64_t wdims[3] = {(cuuint64_t)kC, (cuuint64_t)wrows, NN == kN ? 27u : 9u};
+    const cuuint64_t wstr[2] = {(cuuint64_t)kC * 2, (cuuint64_t)wrows * kC * 2};
+    const cuuint32_t wbox[3] = {(cuuint32_t)kC, wrows, 1};
     if (enc(&wmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(w), wdims, wstr, wbox, ones,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return false;
 
     static bool attr = false;
-    const size_t smem = conv3d_c32_tc_smem();
+    const size_t smem = conv_smem<NN>();
     if (!attr) {
-        if (cudaFuncSetAttribute(k_conv3d_c32_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        if (cudaFuncSetAttribute(k_conv3d_c32_tc<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return false;
         attr = true;
@@ -415,7 +449,7 @@ bool launch_conv(const __nv_bfloat16* act, const __nv_bfloat16* w, ConvTcArgs a,
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long grid = std::min<long long>(a.ntiles, (long long)sms * 2);
-    k_conv3d_c32_tc<<<(unsigned)grid, kThreads, smem, s>>>(amap, wmap, a);
+    k_conv3d_c32_tc<NN><<<(unsigned)grid, kThreads, smem, s>>>(amap, wmap, a);
     return true;
 }
 
@@ -437,13 +471,13 @@ bool launch_conv3d_c32_tc(const __nv_bfloat16* act, const __nv_bfloat16* w, cons
     a.mask_act = mask_act;
     a.out = out;
     a.err = err;
-    return launch_conv(act, w, a, s);
+    return launch_conv<kN>(act, w, a, s);
 }
 
 // The 32 -> 1 output layer with the residual: theta = x + bias[0] + sum_tap
-// W[tap][0] . act[voxel + tap], on the same tensor-core kernel with the
-// weights zero-padded to 32 output channels (w: BF16 [27][32][32], only
-// output channel 0 nonzero); x, theta: FP32 [nvol][D][H][W].
+// W[tap][0] . act[voxel + tap], on the same tensor-core kernel at N = 16
+// (w: BF16 [9][16][32], block (dz, dy) = rows dx + 1 for dx = -1..+1 holding
+// W[(dz, dy, dx)][0][:], rows 3-15 zero); x, theta: FP32 [nvol][D][H][W].
 bool launch_conv3d_c32_to1_tc(const __nv_bfloat16* act, const __nv_bfloat16* w, const float* bias, const float* x,
                               float* theta, int nvol, int D, int H, int W, int* err, cudaStream_t s) {
     ConvTcArgs a{};
@@ -456,7 +490,7 @@ bool launch_conv3d_c32_to1_tc(const __nv_bfloat16* act, const __nv_bfloat16* w, 
     a.xres = x;
     a.out1 = theta;
     a.err = err;
-    return launch_conv(act, w, a, s);
+    return launch_conv<kN1>(act, w, a, s);
 }
 
 }  // namespace sci

@@ -88,17 +88,21 @@ __device__ __forceinline__ void store32(__nv_bfloat16* p, const float (&a)[32]) 
 }
 
 // BF16 copies of the 32 -> 32 weights: forward [tap][o][i] and, for the
-// input gradient, the tap-reversed transpose wt[tap][i][o] = w[26 - tap][o][i].
+// input gradient, the tap-reversed transpose wt[tap][i][o] = w[26 - tap][o][i];
+// and of layer 4 (32 -> 1) for the tensor cores' N = 16 form: w4n[pair][row][i]
+// with pair = (dz + 1) 3 + (dy + 1), rows 0-2 the taps dx = -1..+1, rows 3-15 zero.
 __global__ void k_prep_weights(const float* __restrict__ prm, __nv_bfloat16* __restrict__ w2, __nv_bfloat16* w2t,
-                               __nv_bfloat16* __restrict__ w3, __nv_bfloat16* w3t, __nv_bfloat16* __restrict__ w4p) {
+                               __nv_bfloat16* __restrict__ w3, __nv_bfloat16* w3t, __nv_bfloat16* __restrict__ w4n) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= 27 * C * C) return;
     const int tap = idx / (C * C), o = (idx / C) % C, i = idx % C;
     const int tidx = (26 - tap) * C * C + i * C + o;
     w2[idx] = __float2bfloat16_rn(prm[kW2 + idx]);
     w3[idx] = __float2bfloat16_rn(prm[kW3 + idx]);
-    // layer 4 (32 -> 1) as a 32 -> 32 weight block with output channel 0 only
-    w4p[idx] = o == 0 ? __float2bfloat16_rn(prm[kW4 + tap * C + i]) : __float2bfloat16_rn(0.f);
+    if (idx < 9 * 16 * C) {
+        const int pair = idx / (16 * C), row = (idx / C) % 16;
+        w4n[idx] = row < 3 ? __float2bfloat16_rn(prm[kW4 + (pair * 3 + row) * C + i]) : __float2bfloat16_rn(0.f);
+    }
     if (w2t) w2t[tidx] = __float2bfloat16_rn(prm[kW2 + idx]);
     if (w3t) w3t[tidx] = __float2bfloat16_rn(prm[kW3 + idx]);
 }
@@ -511,7 +515,7 @@ __global__ void k_adam(float* __restrict__ prm, const float* __restrict__ grad, 
 }
 
 struct LWork {
-    __nv_bfloat16 *a1, *a2, *a3, *ga, *gb, *w2, *w2t, *w3, *w3t, *w4p;
+    __nv_bfloat16 *a1, *a2, *a3, *ga, *gb, *w2, *w2t, *w3, *w3t, *w4n;
     float *g4, *grad, *wpart;
     double* partials;
     int* err;
@@ -528,7 +532,7 @@ LWork lwork_layout(long long V, bool training, void* base) {
     L.a3 = reinterpret_cast<__nv_bfloat16*>(take((size_t)V * C * 2));
     L.w2 = reinterpret_cast<__nv_bfloat16*>(take(27 * C * C * 2));
     L.w3 = reinterpret_cast<__nv_bfloat16*>(take(27 * C * C * 2));
-    L.w4p = reinterpret_cast<__nv_bfloat16*>(take(27 * C * C * 2));
+    L.w4n = reinterpret_cast<__nv_bfloat16*>(take(9 * 16 * C * 2));
     L.err = reinterpret_cast<int*>(take(256));
     L.partials = reinterpret_cast<double*>(take((size_t)((V + 255) / 256 + 1) * 8));
     if (training) {
@@ -624,7 +628,7 @@ __global__ void k_project_vols(const float* __restrict__ theta, const float* __r
 // forward through the four layers; theta = x + f(x)
 bool enqueue_forward(const float* prm, const float* x, Vol g, const LWork& L, float* theta, const float* target,
                      cudaStream_t s) {
-    k_prep_weights<<<(27 * C * C + 255) / 256, 256, 0, s>>>(prm, L.w2, L.w2t, L.w3, L.w3t, L.w4p);
+    k_prep_weights<<<(27 * C * C + 255) / 256, 256, 0, s>>>(prm, L.w2, L.w2t, L.w3, L.w3t, L.w4n);
     {
         const int tiles_w = (g.W + kCiW - 1) / kCiW, tiles_h = (g.H + kCiH - 1) / kCiH;
         const long long blocks = (long long)g.nvol * g.D * tiles_h * tiles_w;
@@ -635,10 +639,10 @@ bool enqueue_forward(const float* prm, const float* x, Vol g, const LWork& L, fl
     if (!launch_conv3d_c32_tc(L.a2, L.w3, prm + kB3, nullptr, 0, g.nvol, g.D, g.H, g.W, L.a3, L.err, s))
         return false;
     if (target == nullptr) {
-        // inference: the 32 -> 1 layer on the tensor cores (weights zero-padded
-        // to 32 output channels), which beats the per-voxel CUDA-core form
-        // despite the padding; training keeps k_conv_out for its loss terms
-        return launch_conv3d_c32_to1_tc(L.a3, L.w4p, prm + kB4, x, theta, g.nvol, g.D, g.H, g.W, L.err, s);
+        // inference: the 32 -> 1 layer on the tensor cores (N = 16: the three
+        // dx taps of output channel 0 per MMA), which beats the per-voxel
+        // CUDA-core form; training keeps k_conv_out for its loss terms
+        return launch_conv3d_c32_to1_tc(L.a3, L.w4n, prm + kB4, x, theta, g.nvol, g.D, g.H, g.W, L.err, s);
     }
     k_conv_out<<<grid_for(g.V), 256, 0, s>>>(L.a3, prm, g, x, theta, target, L.g4, L.partials);
     return true;
