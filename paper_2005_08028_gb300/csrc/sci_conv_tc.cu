@@ -377,6 +377,165 @@ k_conv3d_c32_tc(const __grid_constant__ CUtensorMap act_map, const __grid_consta
     }
 }
 
+// ---- weight gradients of a 32 -> 32 layer --------------------------------
+// dW[(dz, dy, dx)][o][i] = sum_v g[v][o] act[v + (dz, dy, dx)][i] is, with
+// u = v + dx along the row, sum_u g[u - dx][o] act[u + (dz, dy)][i]: a GEMM
+// over voxels, K-major in both operands once the fields are transposed so a
+// row's voxels are contiguous per channel (actT[row][c][x], and three copies
+// of gT shifted by dx = -1, 0, +1).  A tile is 32 voxels of one row (K = 32,
+// two MMAs of K = 16).  Operand A stacks four (dz, dy) pairs' 32-channel x
+// 32-voxel TMA boxes (M = 128), B the three shifted gradient boxes (N = 96,
+// rows (dx, o)), in the same 64-byte-swizzled K-major layout as the forward
+// pass.  Pairs 0-3, 4-7 and 8 make three accumulators; the fourth block of
+// the last group holds ones, so its rows give sum_u gT[o][u] (the bias
+// gradient, from the dx = 0 copy).  Each CTA walks its tiles and writes its
+// totals to its own slot (27 x 32 x 32 weights, then 32 biases), which a
+// fixed-order reduction adds up.
+constexpr int kWgStages = 4;
+constexpr uint32_t kWgBox = 32 * 32 * 2;                  // 2 KB: 32 rows x 64 B
+constexpr uint32_t kWgABytes = 12 * kWgBox;               // three groups of four blocks
+constexpr uint32_t kWgStage = kWgABytes + 3 * kWgBox;     // + the three B boxes: 30 KB
+constexpr uint32_t kWgTx = 12 * kWgBox;                   // loaded per tile: 9 A + 3 B boxes
+constexpr int kWgSlotLen = 27 * kC * kC + kC;
+
+struct WgradTcArgs {
+    int nvol, D, H, tiles_x;  // rows nvol x D x H of 32 tiles_x (padded) voxels
+    long long ntiles;
+    float* part;              // [gridDim.x][kWgSlotLen]
+    int* err;
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_wgrad_c32_tc(const __grid_constant__ CUtensorMap a_map, const __grid_constant__ CUtensorMap g_map,
+               WgradTcArgs a) {
+    extern __shared__ __align__(1024) unsigned char dsmem[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)dsmem + 1023) & ~(uintptr_t)1023);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + kWgStages * kWgStage);
+    // bars: full[kWgStages], empty[kWgStages], acc_full, drain
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 2 * kWgStages + 2);
+    volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t bar_full = smem_u32(bars), bar_empty = smem_u32(bars + kWgStages);
+    const uint32_t bar_acc = smem_u32(bars + 2 * kWgStages), bar_drain = smem_u32(bars + 2 * kWgStages + 1);
+
+    if (tid == 0) {
+        for (int s = 0; s < kWgStages; ++s) {
+            mbar_init(bar_full + 8 * s, 1);
+            mbar_init(bar_empty + 8 * s, 1);
+        }
+        mbar_init(bar_acc, 1);
+        mbar_init(bar_drain, 1);
+        *s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // blocks 9-11 of every stage are never loaded: 9 holds BF16 ones (rows of
+    // equal values, which the swizzle leaves unchanged), 10 and 11 zeros
+    for (int e = tid; e < kWgStages * 3 * (int)(kWgBox / 4); e += kThreads) {
+        const int st = e / (3 * (kWgBox / 4)), w = e % (3 * (kWgBox / 4));
+        uint32_t* blk = reinterpret_cast<uint32_t*>(base + st * kWgStage + 9 * kWgBox);
+        blk[w] = w < (int)(kWgBox / 4) ? 0x3F803F80u : 0u;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic-proxy writes, read by the MMAs
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(s_tmem))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *s_tmem;
+    const long long my_tiles = a.ntiles > blockIdx.x ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+    if (warp == 4 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        long long j = 0;
+        for (; j < my_tiles && !*s_abort; ++j) {
+            long long tr = blockIdx.x + j * gridDim.x;
+            const int tx = (int)(tr % a.tiles_x); tr /= a.tiles_x;
+            const int y = (int)(tr % a.H); tr /= a.H;
+            const int z = (int)(tr % a.D), vol = (int)(tr / a.D);
+            const uint32_t s = (uint32_t)(j % kWgStages), use = (uint32_t)(j / kWgStages);
+            if (use > 0 && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1)) {
+                *s_abort = 1;
+                atomicExch(a.err, 1);
+                break;
+            }
+            const uint32_t st = smem_u32(base + s * kWgStage);
+            mbar_expect_tx(bar_full + 8 * s, kWgTx);
+            for (int p = 0; p < 9; ++p)  // pair (dz, dy) = (p / 3 - 1, p % 3 - 1)
+                tma_load_5d(st + p * kWgBox, &a_map, bar_full + 8 * s, tx * 32, 0, y + p % 3 - 1, z + p / 3 - 1, vol);
+            for (int c = 0; c < 3; ++c)  // dx = c - 1
+                tma_load_5d(st + kWgABytes + c * kWgBox, &g_map, bar_full + 8 * s, tx * 32, 0, y, z,
+                            c * a.nvol + vol);
+        }
+        // drain: every load issued must have landed before the CTA exits
+        for (long long k = (j >= kWgStages ? j - kWgStages : 0); k < j; ++k)
+            mbar_wait(bar_full + 8 * (uint32_t)(k % kWgStages), (uint32_t)(k / kWgStages) & 1);
+    }
+    if (warp == 5 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        bool ok = true;
+        for (long long j = 0; j < my_tiles && !*s_abort; ++j) {
+            const uint32_t s = (uint32_t)(j % kWgStages), use = (uint32_t)(j / kWgStages);
+            if (!mbar_wait(bar_full + 8 * s, use & 1)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t st = smem_u32(base + s * kWgStage);
+#pragma unroll
+            for (int grp = 0; grp < 3; ++grp)
+#pragma unroll
+                for (int kk = 0; kk < 2; ++kk)
+                    umma_bf16<kN>(tmem + grp * 128, smem_desc_sw64(st + grp * 4 * kWgBox + kk * 32),
+                                  smem_desc_sw64(st + kWgABytes + kk * 32), (j > 0 || kk > 0) ? 1u : 0u);
+            umma_commit(bar_empty + 8 * s);
+        }
+        if (!ok) {
+            // every MMA issued so far must finish before tensor memory is freed
+            umma_commit(bar_drain);
+            mbar_wait(bar_drain, 0);
+            *s_abort = 1;
+            atomicExch(a.err, 1);
+        }
+        umma_commit(bar_acc);
+    }
+    if (warp < 4) {
+        // ---------------- epilogue: this CTA's totals ----------------
+        const bool got = __all_sync(0xffffffffu, mbar_wait(bar_acc, 0));
+        if (got && !*s_abort) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            float* dst = a.part + (size_t)blockIdx.x * kWgSlotLen;
+            const uint32_t lanes = (uint32_t)(warp * 32) << 16;
+#pragma unroll 1
+            for (int grp = 0; grp < 3; ++grp) {
+                const int blk = grp * 4 + warp;  // this warp's lanes: rows (blk, i = lane)
+#pragma unroll 1
+                for (int c = 0; c < 3; ++c) {
+                    float v[32];
+                    tmem_ld_32cols(tmem + grp * 128 + c * 32 + lanes, v);  // v[o]: dx = c - 1
+                    if (blk < 9) {
+                        const int tap = blk * 3 + c;
+#pragma unroll
+                        for (int o = 0; o < 32; ++o) dst[(tap * kC + o) * kC + lane] = v[o];
+                    } else if (blk == 9 && c == 1 && lane == 0) {
+#pragma unroll
+                        for (int o = 0; o < 32; ++o) dst[27 * kC * kC + o] = v[o];
+                    }
+                }
+            }
+        } else if (lane == 0) {
+            *s_abort = 1;
+            atomicExch(a.err, 1);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 5) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    }
+}
+
 // ---- host: tensor maps ---------------------------------------------------
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -453,6 +612,56 @@ bool launch_conv(const __nv_bfloat16* act, const __nv_bfloat16* w, ConvTcArgs a,
     return true;
 }
 
+bool launch_wgrad(const __nv_bfloat16* actT, const __nv_bfloat16* gT, int nvol, int D, int H, int Wp, float* part,
+                  int max_slots, int* err, int* nslots, cudaStream_t s) {
+    EncodeFn enc = encode_fn();
+    if (enc == nullptr || Wp % 32 != 0 || max_slots < 1) return false;
+    if (((uintptr_t)actT & 15) != 0 || ((uintptr_t)gT & 15) != 0) return false;
+    CUtensorMap amap, gmap;
+    std::memset(&amap, 0, sizeof(amap));
+    std::memset(&gmap, 0, sizeof(gmap));
+    // [vol][z][y][c][x] with x contiguous; the gradient's three shifted copies stack along vol
+    const cuuint64_t row = (cuuint64_t)Wp * 2;
+    const cuuint64_t str[4] = {row, row * kC, row * kC * H, row * kC * H * D};
+    const cuuint32_t box[5] = {32, (cuuint32_t)kC, 1, 1, 1};
+    const cuuint32_t ones[5] = {1, 1, 1, 1, 1};
+    const cuuint64_t adims[5] = {(cuuint64_t)Wp, (cuuint64_t)kC, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)nvol};
+    const cuuint64_t gdims[5] = {(cuuint64_t)Wp, (cuuint64_t)kC, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)3 * nvol};
+    if (enc(&amap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(actT), adims, str, box, ones,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    if (enc(&gmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(gT), gdims, str, box, ones,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    WgradTcArgs a{};
+    a.nvol = nvol;
+    a.D = D;
+    a.H = H;
+    a.tiles_x = Wp / 32;
+    a.ntiles = (long long)nvol * D * H * a.tiles_x;
+    a.part = part;
+    a.err = err;
+    static bool attr = false;
+    const size_t smem = (size_t)kWgStages * kWgStage + 1024 + 256;  // one CTA per SM (512 tensor-memory columns)
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_wgrad_c32_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return false;
+        attr = true;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // every CTA gets at least one tile (its accumulators start with its first MMA)
+    const long long grid = std::min<long long>({a.ntiles, (long long)sms, (long long)max_slots});
+    if (grid < 1) return false;
+    k_wgrad_c32_tc<<<(unsigned)grid, kThreads, smem, s>>>(amap, gmap, a);
+    *nslots = (int)grid;
+    return true;
+}
+
 }  // namespace
 
 // out[vol][z][h][w][:] = epilogue(sum_tap W[tap] * act[vol][z+dz][h+dy][w+dx][:]).
@@ -491,6 +700,17 @@ bool launch_conv3d_c32_to1_tc(const __nv_bfloat16* act, const __nv_bfloat16* w, 
     a.out1 = theta;
     a.err = err;
     return launch_conv<kN1>(act, w, a, s);
+}
+
+// Weight and bias gradients of a 32 -> 32 layer on the tensor cores, per-CTA
+// totals: actT [nvol][D][H][32][Wp] (the layer's input, transposed per row),
+// gT [3][nvol][D][H][32][Wp] (its output gradient, transposed per row and
+// shifted by dx = -1, 0, +1: gT[c][..][o][x] = g[..][x - (c - 1)][o], zero
+// outside the row); Wp a multiple of 32.  Slot b of part (at most max_slots)
+// receives dW[27][32 o][32 i] then db[32]; *nslots the number written.
+bool launch_wgrad_c32_tc(const __nv_bfloat16* actT, const __nv_bfloat16* gT, int nvol, int D, int H, int Wp,
+                         float* part, int max_slots, int* err, int* nslots, cudaStream_t s) {
+    return launch_wgrad(actT, gT, nvol, D, H, Wp, part, max_slots, err, nslots, s);
 }
 
 }  // namespace sci

@@ -30,6 +30,8 @@ bool launch_conv3d_c32_tc(const __nv_bfloat16* act, const __nv_bfloat16* w, cons
                           __nv_bfloat16* out, int* err, cudaStream_t s);
 bool launch_conv3d_c32_to1_tc(const __nv_bfloat16* act, const __nv_bfloat16* w, const float* bias, const float* x,
                               float* theta, int nvol, int D, int H, int W, int* err, cudaStream_t s);
+bool launch_wgrad_c32_tc(const __nv_bfloat16* actT, const __nv_bfloat16* gT, int nvol, int D, int H, int Wp,
+                         float* part, int max_slots, int* err, int* nslots, cudaStream_t s);
 
 namespace {
 
@@ -241,117 +243,36 @@ __global__ void k_dgrad_out(const float* __restrict__ g4, const float* __restric
     store32(g3 + u * C, acc);
 }
 
-// Weight and bias gradients of a 32 -> 32 layer, tiled:
-//   dw[tap][o][i] = sum_v gout[v][o] * ain[v + offset(tap)][i],  db[o] = sum_v gout[v][o].
-// A tile is kWgTile voxels of one row.  The CTA stages, as FP32, the nine
-// (dz, dy) neighbour rows of ain over columns x0 - 1 .. x0 + kWgTile (zero
-// outside the volume) and gout over the tile with a zero border.  Thread
-// (o, i-quad) walks the ain columns c with the gout values of columns c - 1,
-// c, c + 1 in registers: one 16-byte shared load of ain[row][c][i..i+3] feeds
-// the three column taps (output voxel c - dx for tap dx), 12 FMAs.  Each CTA
-// writes its 27 x 32 x 32 + 32 totals to its own slot of `part`;
-// k_wgrad_reduce sums the slots in a fixed order (no atomics, so the
-// gradient is the same on every run).
+// Weight and bias gradients of a 32 -> 32 layer run on the tensor cores
+// (k_wgrad_c32_tc), as a GEMM over voxels whose operands have each row's
+// voxels contiguous per channel: the layer input transposed per row, and its
+// output gradient transposed per row and shifted by dx = -1, 0, +1.
+// out[row][c][x] = in[row][x - shift][c] for x < Wp (zero outside [0, W)):
+// one CTA moves a 32-voxel x 32-channel tile through shared memory, reading
+// voxels' channel vectors and writing channels' voxel runs, both coalesced.
 constexpr int kWgTile = 64, kWgCols = kWgTile + 2, kWgMaxBlocks = 256, kWgSlot = 27 * C * C + C;
 
-size_t wgrad_smem() { return (size_t)(9 * kWgCols + kWgCols + 2) * C * sizeof(float); }
-
-__global__ void __launch_bounds__(256, 1) k_wgrad_c32_tiled(const __nv_bfloat16* __restrict__ gout,
-                                                            const __nv_bfloat16* __restrict__ ain, Vol g,
-                                                            int tiles_x, float* __restrict__ part) {
-    extern __shared__ float4 wg_smem4[];
-    float* sA = reinterpret_cast<float*>(wg_smem4);  // [9][kWgCols][32]: ain rows (dz, dy), columns x0-1 ..
-    float* sG = sA + 9 * kWgCols * C;                // [kWgCols + 2][32]: gout at columns x0-2 .. x0+kWgTile+1
-    const int o = threadIdx.x >> 3, iq = (threadIdx.x & 7) * 4;
-    float acc[27][4];
-#pragma unroll
-    for (int t = 0; t < 27; ++t)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc[t][k] = 0.f;
-    float bacc = 0.f;
-    const long long ntiles = (long long)g.nvol * g.D * g.H * tiles_x;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int tx = (int)(tile % tiles_x);
-        long long r = tile / tiles_x;
-        const int y = (int)(r % g.H);
-        r /= g.H;
-        const int z = (int)(r % g.D), n = (int)(r / g.D);
-        const int x0 = tx * kWgTile;
+__global__ void __launch_bounds__(256) k_rows_transpose(const __nv_bfloat16* __restrict__ in,
+                                                        __nv_bfloat16* __restrict__ out, long long rows, int W,
+                                                        int Wp, int shift) {
+    __shared__ unsigned short t[32][33];
+    const int tiles = Wp / 32;
+    const unsigned short* src = reinterpret_cast<const unsigned short*>(in);
+    unsigned short* dst = reinterpret_cast<unsigned short*>(out);
+    for (long long tile = blockIdx.x; tile < rows * tiles; tile += gridDim.x) {
+        const long long row = tile / tiles;
+        const int x0 = (int)(tile % tiles) * 32;
         __syncthreads();  // the previous tile's reads are done
-        for (int e = threadIdx.x; e < 9 * kWgCols * 4; e += blockDim.x) {
-            const int q = e & 3, col = (e >> 2) % kWgCols, row = (e >> 2) / kWgCols;
-            const int zz = z + row / 3 - 1, yy = y + row % 3 - 1, xx = x0 - 1 + col;
-            float f[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) f[k] = 0.f;
-            if (zz >= 0 && zz < g.D && yy >= 0 && yy < g.H && xx >= 0 && xx < g.W) {
-                const long long u = (((long long)n * g.D + zz) * g.H + yy) * g.W + xx;
-                const uint4 raw = __ldg(reinterpret_cast<const uint4*>(ain + u * C + q * 8));
-                const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&raw);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const float2 v2 = __bfloat1622float2(h[k]);
-                    f[2 * k] = v2.x;
-                    f[2 * k + 1] = v2.y;
-                }
-            }
-            float4* d = reinterpret_cast<float4*>(sA + (row * kWgCols + col) * C + q * 8);
-            d[0] = make_float4(f[0], f[1], f[2], f[3]);
-            d[1] = make_float4(f[4], f[5], f[6], f[7]);
-        }
-        for (int e = threadIdx.x; e < (kWgCols + 2) * 4; e += blockDim.x) {
-            const int q = e & 3, col = e >> 2;  // column x0 - 2 + col
-            const int xx = x0 - 2 + col;
-            float f[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) f[k] = 0.f;
-            if (xx >= x0 && xx < x0 + kWgTile && xx < g.W) {
-                const long long v = (((long long)n * g.D + z) * g.H + y) * g.W + xx;
-                const uint4 raw = __ldg(reinterpret_cast<const uint4*>(gout + v * C + q * 8));
-                const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&raw);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const float2 v2 = __bfloat1622float2(h[k]);
-                    f[2 * k] = v2.x;
-                    f[2 * k + 1] = v2.y;
-                }
-            }
-            float4* d = reinterpret_cast<float4*>(sG + col * C + q * 8);
-            d[0] = make_float4(f[0], f[1], f[2], f[3]);
-            d[1] = make_float4(f[4], f[5], f[6], f[7]);
+        for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+            const int xl = e >> 5, c = e & 31, xs = x0 + xl - shift;
+            t[c][xl] = (xs >= 0 && xs < W) ? src[(row * W + xs) * C + c] : (unsigned short)0;
         }
         __syncthreads();
-        // ain column c is x0 - 1 + c; gout column c is sG[c + 1] (x0 - 1 + c)
-        float gm = sG[0 * C + o], g0 = sG[1 * C + o];  // columns c - 1, c for c = 0
-        for (int c = 0; c < kWgCols; ++c) {
-            const float gp = sG[(c + 2) * C + o];  // column c + 1
-            if (iq == 0) bacc += g0;
-#pragma unroll
-            for (int row = 0; row < 9; ++row) {
-                const float4 a = *reinterpret_cast<const float4*>(sA + (row * kWgCols + c) * C + iq);
-                // tap (row, dx): output voxel c - dx, i.e. gout column c - dx
-                acc[row * 3 + 0][0] = fmaf(gp, a.x, acc[row * 3 + 0][0]);  // dx = -1
-                acc[row * 3 + 0][1] = fmaf(gp, a.y, acc[row * 3 + 0][1]);
-                acc[row * 3 + 0][2] = fmaf(gp, a.z, acc[row * 3 + 0][2]);
-                acc[row * 3 + 0][3] = fmaf(gp, a.w, acc[row * 3 + 0][3]);
-                acc[row * 3 + 1][0] = fmaf(g0, a.x, acc[row * 3 + 1][0]);  // dx = 0
-                acc[row * 3 + 1][1] = fmaf(g0, a.y, acc[row * 3 + 1][1]);
-                acc[row * 3 + 1][2] = fmaf(g0, a.z, acc[row * 3 + 1][2]);
-                acc[row * 3 + 1][3] = fmaf(g0, a.w, acc[row * 3 + 1][3]);
-                acc[row * 3 + 2][0] = fmaf(gm, a.x, acc[row * 3 + 2][0]);  // dx = +1
-                acc[row * 3 + 2][1] = fmaf(gm, a.y, acc[row * 3 + 2][1]);
-                acc[row * 3 + 2][2] = fmaf(gm, a.z, acc[row * 3 + 2][2]);
-                acc[row * 3 + 2][3] = fmaf(gm, a.w, acc[row * 3 + 2][3]);
-            }
-            gm = g0;
-            g0 = gp;
+        for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+            const int c = e >> 5, xl = e & 31;
+            dst[(row * C + c) * Wp + x0 + xl] = t[c][xl];
         }
     }
-    float* dst = part + (size_t)blockIdx.x * kWgSlot;
-#pragma unroll
-    for (int t = 0; t < 27; ++t)
-        *reinterpret_cast<float4*>(dst + (t * C + o) * C + iq) = make_float4(acc[t][0], acc[t][1], acc[t][2], acc[t][3]);
-    if (iq == 0) dst[27 * C * C + o] = bacc;
 }
 
 // Slots of `len` values (the first nw weight gradients, then bias gradients):
@@ -516,13 +437,18 @@ __global__ void k_adam(float* __restrict__ prm, const float* __restrict__ grad, 
 
 struct LWork {
     __nv_bfloat16 *a1, *a2, *a3, *ga, *gb, *w2, *w2t, *w3, *w3t, *w4n;
+    __nv_bfloat16 *actT, *gT;  // weight gradients: the transposed operands (training)
     float *g4, *grad, *wpart;
     double* partials;
     int* err;
     size_t total;
 };
 
-LWork lwork_layout(long long V, bool training, void* base) {
+int padded_width(int W) { return (W + 31) / 32 * 32; }
+
+// V voxels in rows of W (the transposed weight-gradient operands pad rows to
+// a multiple of 32 voxels).
+LWork lwork_layout(long long V, int W, bool training, void* base) {
     LWork L{};
     size_t off = 0;
     char* b = static_cast<char*>(base);
@@ -543,6 +469,9 @@ LWork lwork_layout(long long V, bool training, void* base) {
         L.g4 = reinterpret_cast<float*>(take((size_t)V * 4));
         L.grad = reinterpret_cast<float*>(take(kParams * 4));
         L.wpart = reinterpret_cast<float*>(take((size_t)kWgMaxBlocks * kWgSlot * 4));
+        const size_t tbytes = (size_t)(V / W) * padded_width(W) * C * 2;
+        L.actT = reinterpret_cast<__nv_bfloat16*>(take(tbytes));
+        L.gT = reinterpret_cast<__nv_bfloat16*>(take(3 * tbytes));
     }
     L.total = off;
     return L;
@@ -550,24 +479,22 @@ LWork lwork_layout(long long V, bool training, void* base) {
 
 int grid_for(long long V) { return (int)((V + 255) / 256); }
 
-// Weight and bias gradients of a 32 -> 32 layer into dw / db (added).
-bool enqueue_wgrad_c32(const __nv_bfloat16* gout, const __nv_bfloat16* ain, Vol g, float* part, float* dw,
+// Weight and bias gradients of a 32 -> 32 layer into dw / db (added): the
+// operands transposed per row, the tensor-core totals per CTA, then the
+// fixed-order sum over the CTAs' slots (the same gradient on every run).
+bool enqueue_wgrad_c32(const __nv_bfloat16* gout, const __nv_bfloat16* ain, Vol g, const LWork& L, float* dw,
                        float* db, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(k_wgrad_c32_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)wgrad_smem()) != cudaSuccess)
-            return false;
-        attr = true;
-    }
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int tiles_x = (g.W + kWgTile - 1) / kWgTile;
-    const long long ntiles = (long long)g.nvol * g.D * g.H * tiles_x;
-    const int grid = (int)std::max(1LL, std::min<long long>({ntiles, (long long)sms, (long long)kWgMaxBlocks}));
-    k_wgrad_c32_tiled<<<grid, 256, wgrad_smem(), s>>>(gout, ain, g, tiles_x, part);
-    k_wgrad_reduce<<<(kWgSlot + 255) / 256, 256, 0, s>>>(part, grid, kWgSlot, 27 * C * C, dw, db);
+    const int Wp = padded_width(g.W);
+    const long long rows = (long long)g.nvol * g.D * g.H;
+    const size_t tsize = (size_t)rows * Wp * C;  // elements of one transposed field
+    const long long tiles = rows * (Wp / 32);
+    const unsigned tgrid = (unsigned)std::min<long long>(tiles, 152LL * 16);
+    k_rows_transpose<<<tgrid, 256, 0, s>>>(ain, L.actT, rows, g.W, Wp, 0);
+    for (int c = 0; c < 3; ++c) k_rows_transpose<<<tgrid, 256, 0, s>>>(gout, L.gT + c * tsize, rows, g.W, Wp, c - 1);
+    int nslots = 0;
+    if (!launch_wgrad_c32_tc(L.actT, L.gT, g.nvol, g.D, g.H, Wp, L.wpart, kWgMaxBlocks, L.err, &nslots, s))
+        return false;
+    k_wgrad_reduce<<<(kWgSlot + 255) / 256, 256, 0, s>>>(L.wpart, nslots, kWgSlot, 27 * C * C, dw, db);
     return true;
 }
 
@@ -664,7 +591,7 @@ size_t sci_lprox_param_count(void) { return kParams; }
 
 size_t sci_lprox_workspace(int nx, int ny, int B, int count, int training) {
     if (!vol_ok(nx, ny, B, count)) return 0;
-    return lwork_layout((long long)nx * ny * B * count, training != 0, nullptr).total;
+    return lwork_layout((long long)nx * ny * B * count, ny, training != 0, nullptr).total;
 }
 
 sci_status sci_lprox_apply(const float* params, const float* x, int nx, int ny, int B, int count, float* theta,
@@ -672,9 +599,9 @@ sci_status sci_lprox_apply(const float* params, const float* x, int nx, int ny, 
     if (params == nullptr || x == nullptr || theta == nullptr || x == theta || !vol_ok(nx, ny, B, count))
         return SCI_ERR_ARG;
     const Vol g{count, B, nx, ny, (long long)nx * ny * B * count};
-    const LWork need = lwork_layout(g.V, false, nullptr);
+    const LWork need = lwork_layout(g.V, g.W, false, nullptr);
     if (work == nullptr || work_bytes < need.total || ((uintptr_t)work & 255u) != 0) return SCI_ERR_WORKSPACE;
-    const LWork L = lwork_layout(g.V, false, work);
+    const LWork L = lwork_layout(g.V, g.W, false, work);
     cudaStream_t s = (cudaStream_t)stream;
     cudaMemsetAsync(L.err, 0, sizeof(int), s);
     if (!enqueue_forward(params, x, g, L, theta, nullptr, s)) return SCI_ERR_CUDA;
@@ -689,9 +616,9 @@ sci_status sci_lprox_train_step(float* params, float* adam_m, float* adam_v, int
         return SCI_ERR_ARG;
     if (!std::isfinite(lr) || !(lr > 0.f)) return SCI_ERR_ARG;
     const Vol g{count, B, nx, ny, (long long)nx * ny * B * count};
-    const LWork need = lwork_layout(g.V, true, nullptr);
+    const LWork need = lwork_layout(g.V, g.W, true, nullptr);
     if (work == nullptr || work_bytes < need.total || ((uintptr_t)work & 255u) != 0) return SCI_ERR_WORKSPACE;
-    const LWork L = lwork_layout(g.V, true, work);
+    const LWork L = lwork_layout(g.V, g.W, true, work);
     cudaStream_t s = (cudaStream_t)stream;
     cudaMemsetAsync(L.err, 0, sizeof(int), s);
     if (!enqueue_forward(params, x, g, L, nullptr, target, s)) return SCI_ERR_CUDA;
@@ -702,11 +629,11 @@ sci_status sci_lprox_train_step(float* params, float* adam_m, float* adam_v, int
         return SCI_ERR_CUDA;
     k_dgrad_out<<<grid_for(g.V), 256, 0, s>>>(L.g4, params, g, L.a3, L.ga);  // ga = g3
     // layer 3
-    if (!enqueue_wgrad_c32(L.ga, L.a2, g, L.wpart, L.grad + kW3, L.grad + kB3, s)) return SCI_ERR_CUDA;
+    if (!enqueue_wgrad_c32(L.ga, L.a2, g, L, L.grad + kW3, L.grad + kB3, s)) return SCI_ERR_CUDA;
     if (!launch_conv3d_c32_tc(L.ga, L.w3t, nullptr, L.a2, 1, g.nvol, g.D, g.H, g.W, L.gb, L.err, s))
         return SCI_ERR_CUDA;  // gb = g2
     // layer 2
-    if (!enqueue_wgrad_c32(L.gb, L.a1, g, L.wpart, L.grad + kW2, L.grad + kB2, s)) return SCI_ERR_CUDA;
+    if (!enqueue_wgrad_c32(L.gb, L.a1, g, L, L.grad + kW2, L.grad + kB2, s)) return SCI_ERR_CUDA;
     if (!launch_conv3d_c32_tc(L.gb, L.w2t, nullptr, L.a1, 1, g.nvol, g.D, g.H, g.W, L.ga, L.err, s))
         return SCI_ERR_CUDA;  // ga = g1
     // layer 1
@@ -726,9 +653,9 @@ sci_status sci_lprox_grads(const float* params, const float* x, const float* tar
     if (params == nullptr || x == nullptr || target == nullptr || grad == nullptr || !vol_ok(nx, ny, B, count))
         return SCI_ERR_ARG;
     const Vol g{count, B, nx, ny, (long long)nx * ny * B * count};
-    const LWork need = lwork_layout(g.V, true, nullptr);
+    const LWork need = lwork_layout(g.V, g.W, true, nullptr);
     if (work == nullptr || work_bytes < need.total || ((uintptr_t)work & 255u) != 0) return SCI_ERR_WORKSPACE;
-    LWork L = lwork_layout(g.V, true, work);
+    LWork L = lwork_layout(g.V, g.W, true, work);
     L.grad = grad;
     cudaStream_t s = (cudaStream_t)stream;
     cudaMemsetAsync(L.err, 0, sizeof(int), s);
@@ -738,10 +665,10 @@ sci_status sci_lprox_grads(const float* params, const float* x, const float* tar
     if (!enqueue_wgrad_1ch(false, nullptr, L.g4, nullptr, L.a3, g, L.wpart, grad + kW4, grad + kB4, s))
         return SCI_ERR_CUDA;
     k_dgrad_out<<<grid_for(g.V), 256, 0, s>>>(L.g4, params, g, L.a3, L.ga);
-    if (!enqueue_wgrad_c32(L.ga, L.a2, g, L.wpart, grad + kW3, grad + kB3, s)) return SCI_ERR_CUDA;
+    if (!enqueue_wgrad_c32(L.ga, L.a2, g, L, grad + kW3, grad + kB3, s)) return SCI_ERR_CUDA;
     if (!launch_conv3d_c32_tc(L.ga, L.w3t, nullptr, L.a2, 1, g.nvol, g.D, g.H, g.W, L.gb, L.err, s))
         return SCI_ERR_CUDA;
-    if (!enqueue_wgrad_c32(L.gb, L.a1, g, L.wpart, grad + kW2, grad + kB2, s)) return SCI_ERR_CUDA;
+    if (!enqueue_wgrad_c32(L.gb, L.a1, g, L, grad + kW2, grad + kB2, s)) return SCI_ERR_CUDA;
     if (!launch_conv3d_c32_tc(L.gb, L.w2t, nullptr, L.a1, 1, g.nvol, g.D, g.H, g.W, L.ga, L.err, s))
         return SCI_ERR_CUDA;
     if (!enqueue_wgrad_1ch(true, L.ga, nullptr, x, nullptr, g, L.wpart, grad + kW1, grad + kB1, s))
@@ -753,7 +680,7 @@ size_t sci_gap_tv_lprox_workspace(int nx, int ny, int B, int count, const sci_pa
     if (!vol_ok(nx, ny, B, count) || plain == nullptr) return 0;
     const size_t N = (size_t)nx * ny * B * count;
     return align256(N * 4) * 2 + align256((size_t)count * 8) + align256(sci_reduce_workspace()) +
-           std::max(lwork_layout((long long)N, false, nullptr).total, sci_solver_workspace(nx, ny, B, plain));
+           std::max(lwork_layout((long long)N, ny, false, nullptr).total, sci_solver_workspace(nx, ny, B, plain));
 }
 
 sci_status sci_gap_tv_lprox(const float* params, const float* y, const uint32_t* bits, int nx, int ny, int B,
@@ -778,7 +705,7 @@ sci_status sci_gap_tv_lprox(const float* params, const float* y, const uint32_t*
     void* inner = static_cast<char*>(rwork) + align256(sci_reduce_workspace());
     const size_t inner_bytes = work_bytes - (size_t)(static_cast<char*>(inner) - w);
     const Vol g{count, B, nx, ny, N};
-    const LWork L = lwork_layout(N, false, inner);
+    const LWork L = lwork_layout(N, ny, false, inner);
     cudaMemsetAsync(L.err, 0, sizeof(int), s);
     if (init) {
         for (int v = 0; v < count; ++v)
@@ -839,9 +766,9 @@ sci_status sci_gap_tv_lprox(const float* params, const float* y, const uint32_t*
 sci_status sci_lprox_error_word(void* work, size_t work_bytes, int nx, int ny, int B, int count, int training,
                                 int** out) {
     if (out == nullptr || !vol_ok(nx, ny, B, count)) return SCI_ERR_ARG;
-    const LWork need = lwork_layout((long long)nx * ny * B * count, training != 0, nullptr);
+    const LWork need = lwork_layout((long long)nx * ny * B * count, ny, training != 0, nullptr);
     if (work == nullptr || work_bytes < need.total) return SCI_ERR_WORKSPACE;
-    *out = lwork_layout((long long)nx * ny * B * count, training != 0, work).err;
+    *out = lwork_layout((long long)nx * ny * B * count, ny, training != 0, work).err;
     return SCI_OK;
 }
 
