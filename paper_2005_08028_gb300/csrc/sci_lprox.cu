@@ -247,30 +247,44 @@ __global__ void k_dgrad_out(const float* __restrict__ g4, const float* __restric
 // (k_wgrad_c32_tc), as a GEMM over voxels whose operands have each row's
 // voxels contiguous per channel: the layer input transposed per row, and its
 // output gradient transposed per row and shifted by dx = -1, 0, +1.
-// out[row][c][x] = in[row][x - shift][c] for x < Wp (zero outside [0, W)):
-// one CTA moves a 32-voxel x 32-channel tile through shared memory, reading
-// voxels' channel vectors and writing channels' voxel runs, both coalesced.
+// (kWgTile / kWgCols: the one-channel layers' tiled gradient kernels below.)
 constexpr int kWgTile = 64, kWgCols = kWgTile + 2, kWgMaxBlocks = 256, kWgSlot = 27 * C * C + C;
 
-__global__ void __launch_bounds__(256) k_rows_transpose(const __nv_bfloat16* __restrict__ in,
-                                                        __nv_bfloat16* __restrict__ out, long long rows, int W,
-                                                        int Wp, int shift) {
-    __shared__ unsigned short t[32][33];
+// Both operands in one pass over a 32-voxel x 32-channel tile of a row:
+// actT[row][c][x] = act[row][x][c] and gT[k][row][c][x] = g[row][x - (k - 1)][c]
+// for k = 0, 1, 2 and x < Wp (zero outside [0, W)).  The tile's activations
+// and its gradient columns x0 - 1 .. x0 + 32 pass through shared memory, read
+// as voxels' channel vectors and written as channels' voxel runs, both
+// coalesced; the three shifted copies come from the one staged gradient tile.
+__global__ void __launch_bounds__(256) k_wgrad_operands(const __nv_bfloat16* __restrict__ act,
+                                                        const __nv_bfloat16* __restrict__ grad,
+                                                        __nv_bfloat16* __restrict__ actT, __nv_bfloat16* __restrict__ gT,
+                                                        long long rows, int W, int Wp) {
+    __shared__ unsigned short ta[32][33];
+    __shared__ unsigned short tg[32][35];
     const int tiles = Wp / 32;
-    const unsigned short* src = reinterpret_cast<const unsigned short*>(in);
-    unsigned short* dst = reinterpret_cast<unsigned short*>(out);
+    const unsigned short* a16 = reinterpret_cast<const unsigned short*>(act);
+    const unsigned short* g16 = reinterpret_cast<const unsigned short*>(grad);
+    unsigned short* at16 = reinterpret_cast<unsigned short*>(actT);
+    unsigned short* gt16 = reinterpret_cast<unsigned short*>(gT);
+    const size_t copy = (size_t)rows * C * Wp;  // elements of one transposed field
     for (long long tile = blockIdx.x; tile < rows * tiles; tile += gridDim.x) {
         const long long row = tile / tiles;
         const int x0 = (int)(tile % tiles) * 32;
         __syncthreads();  // the previous tile's reads are done
-        for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
-            const int xl = e >> 5, c = e & 31, xs = x0 + xl - shift;
-            t[c][xl] = (xs >= 0 && xs < W) ? src[(row * W + xs) * C + c] : (unsigned short)0;
+        for (int e = threadIdx.x; e < 34 * 32; e += blockDim.x) {
+            const int j = e >> 5, c = e & 31, x = x0 - 1 + j;  // gradient columns x0 - 1 .. x0 + 32
+            const bool in = x >= 0 && x < W;
+            tg[c][j] = in ? g16[(row * W + x) * C + c] : (unsigned short)0;
+            if (j >= 1 && j <= 32) ta[c][j - 1] = in ? a16[(row * W + x) * C + c] : (unsigned short)0;
         }
         __syncthreads();
         for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
             const int c = e >> 5, xl = e & 31;
-            dst[(row * C + c) * Wp + x0 + xl] = t[c][xl];
+            const size_t at = ((size_t)row * C + c) * Wp + x0 + xl;
+            at16[at] = ta[c][xl];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) gt16[k * copy + at] = tg[c][xl - k + 2];
         }
     }
 }
@@ -486,11 +500,9 @@ bool enqueue_wgrad_c32(const __nv_bfloat16* gout, const __nv_bfloat16* ain, Vol 
                        float* db, cudaStream_t s) {
     const int Wp = padded_width(g.W);
     const long long rows = (long long)g.nvol * g.D * g.H;
-    const size_t tsize = (size_t)rows * Wp * C;  // elements of one transposed field
     const long long tiles = rows * (Wp / 32);
     const unsigned tgrid = (unsigned)std::min<long long>(tiles, 152LL * 16);
-    k_rows_transpose<<<tgrid, 256, 0, s>>>(ain, L.actT, rows, g.W, Wp, 0);
-    for (int c = 0; c < 3; ++c) k_rows_transpose<<<tgrid, 256, 0, s>>>(gout, L.gT + c * tsize, rows, g.W, Wp, c - 1);
+    k_wgrad_operands<<<tgrid, 256, 0, s>>>(ain, gout, L.actT, L.gT, rows, g.W, Wp);
     int nslots = 0;
     if (!launch_wgrad_c32_tc(L.actT, L.gT, g.nvol, g.D, g.H, Wp, L.wpart, kWgMaxBlocks, L.err, &nslots, s))
         return false;
