@@ -69,20 +69,25 @@ def test_network_forward_matches_oracle(pkg):
         assert np.abs(f_got - f_ref).max() <= 0.05 * rms + 1e-4, (np.abs(f_got - f_ref).max(), rms)
 
 
-def test_network_gradients_match_oracle(pkg):
+# rows of 20 voxels (one padded tile of the tensor-core weight gradient) and
+# of 70 (three tiles, the last one partly padding), frames and rows that put
+# every (dz, dy) tap over the volume's edges
+@pytest.mark.parametrize("shape", [(2, 3, 10, 20), (1, 4, 5, 70)])
+def test_network_gradients_match_oracle(pkg, shape):
     ps, flat = _params(9)
     rng = np.random.default_rng(10)
-    x = rng.random((2, 3, 10, 20)).astype(np.float32)
+    x = rng.random(shape).astype(np.float32)
     t = (x + 0.05 * rng.normal(size=x.shape)).astype(np.float32)
     net = pkg.LearnedProx(params=torch.from_numpy(flat).cuda())
     g, loss = net.grads(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
     g = g.cpu().numpy().astype(np.float64)
-    # the oracle's mean is over all voxels of both volumes
+    # the oracle's mean is over all voxels of every volume
     tot = None
-    for k in range(2):
+    nv = x.shape[0]
+    for k in range(nv):
         lk, gk = L.lprox_loss_and_grads(x[k], t[k], ps)
         flat_k = np.concatenate([np.concatenate([dw.reshape(-1), db]) for dw, db in gk])
-        tot = flat_k / 2 if tot is None else tot + flat_k / 2
+        tot = flat_k / nv if tot is None else tot + flat_k / nv
     # per layer: direction and size; per tap (27) and per output channel: the
     # slice's relative error, so a wrong tap or channel is located; per entry:
     # no gradient entry off by more than a tenth of the layer's largest.  The
@@ -98,12 +103,19 @@ def test_network_gradients_match_oracle(pkg):
         assert cos > 0.995 and abs(np.linalg.norm(a) / np.linalg.norm(b) - 1) < 0.03, (shp, cos)
         assert np.abs(a - b).max() <= 0.1 * np.abs(b).max(), shp
         if len(shp) == 3:
+            # a slice's error against its own size, but not below a floor of
+            # 5% of the layer's largest slice: BF16 operands put a noise floor
+            # proportional to the layer's scale under slices that are nearly
+            # zero (an output channel whose ReLU is rarely open), while a wrong
+            # tap or channel errs by the order of its own slice
             A, Bm = a.reshape(shp), b.reshape(shp)
+            tap_n = [np.linalg.norm(Bm[tap]) for tap in range(27)]
             for tap in range(27):
-                d = np.linalg.norm(A[tap] - Bm[tap]) / (np.linalg.norm(Bm[tap]) + 1e-30)
+                d = np.linalg.norm(A[tap] - Bm[tap]) / max(tap_n[tap], 0.05 * max(tap_n), 1e-30)
                 assert d < 0.1, (shp, "tap", tap, d)
+            out_n = [np.linalg.norm(Bm[:, o]) for o in range(shp[1])]
             for o in range(shp[1]):
-                d = np.linalg.norm(A[:, o] - Bm[:, o]) / (np.linalg.norm(Bm[:, o]) + 1e-30)
+                d = np.linalg.norm(A[:, o] - Bm[:, o]) / max(out_n[o], 0.05 * max(out_n), 1e-30)
                 assert d < 0.1, (shp, "out", o, d)
 
 
