@@ -391,7 +391,7 @@ k_conv3d_c32_tc(const __grid_constant__ CUtensorMap act_map, const __grid_consta
 // gradient, from the dx = 0 copy).  Each CTA walks its tiles and writes its
 // totals to its own slot (27 x 32 x 32 weights, then 32 biases), which a
 // fixed-order reduction adds up.
-constexpr int kWgStages = 4;
+constexpr int kWgStages = 7;
 constexpr uint32_t kWgBox = 32 * 32 * 2;                  // 2 KB: 32 rows x 64 B
 constexpr uint32_t kWgABytes = 12 * kWgBox;               // three groups of four blocks
 constexpr uint32_t kWgStage = kWgABytes + 3 * kWgBox;     // + the three B boxes: 30 KB

@@ -260,31 +260,47 @@ __global__ void __launch_bounds__(256) k_wgrad_operands(const __nv_bfloat16* __r
                                                         const __nv_bfloat16* __restrict__ grad,
                                                         __nv_bfloat16* __restrict__ actT, __nv_bfloat16* __restrict__ gT,
                                                         long long rows, int W, int Wp) {
-    __shared__ unsigned short ta[32][33];
-    __shared__ unsigned short tg[32][35];
+    // tiles of 64 voxels; a voxel's 32 channels move as four 16-byte words,
+    // a channel's run of 8 voxels as one
+    __shared__ unsigned short ta[32][64 + 2];
+    __shared__ unsigned short tg[32][66 + 2];
     const int tiles = Wp / 32;
-    const unsigned short* a16 = reinterpret_cast<const unsigned short*>(act);
-    const unsigned short* g16 = reinterpret_cast<const unsigned short*>(grad);
+    const uint4* a4 = reinterpret_cast<const uint4*>(act);
+    const uint4* g4 = reinterpret_cast<const uint4*>(grad);
     unsigned short* at16 = reinterpret_cast<unsigned short*>(actT);
     unsigned short* gt16 = reinterpret_cast<unsigned short*>(gT);
     const size_t copy = (size_t)rows * C * Wp;  // elements of one transposed field
-    for (long long tile = blockIdx.x; tile < rows * tiles; tile += gridDim.x) {
-        const long long row = tile / tiles;
-        const int x0 = (int)(tile % tiles) * 32;
+    const int tiles2 = (tiles + 1) / 2;          // 64-voxel tiles per row
+    for (long long tile = blockIdx.x; tile < rows * tiles2; tile += gridDim.x) {
+        const long long row = tile / tiles2;
+        const int x0 = (int)(tile % tiles2) * 64;
+        const int nx = min(64, Wp - x0);  // 32 or 64 columns of this tile
         __syncthreads();  // the previous tile's reads are done
-        for (int e = threadIdx.x; e < 34 * 32; e += blockDim.x) {
-            const int j = e >> 5, c = e & 31, x = x0 - 1 + j;  // gradient columns x0 - 1 .. x0 + 32
+        for (int e = threadIdx.x; e < (nx + 2) * 4; e += blockDim.x) {
+            const int j = e >> 2, q = e & 3, x = x0 - 1 + j;  // gradient columns x0 - 1 .. x0 + nx
             const bool in = x >= 0 && x < W;
-            tg[c][j] = in ? g16[(row * W + x) * C + c] : (unsigned short)0;
-            if (j >= 1 && j <= 32) ta[c][j - 1] = in ? a16[(row * W + x) * C + c] : (unsigned short)0;
+            const uint4 gv = in ? __ldg(g4 + (row * W + x) * 4 + q) : make_uint4(0, 0, 0, 0);
+            const unsigned short* gs = reinterpret_cast<const unsigned short*>(&gv);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) tg[q * 8 + k][j] = gs[k];
+            if (j >= 1 && j <= nx) {
+                const uint4 av = in ? __ldg(a4 + (row * W + x) * 4 + q) : make_uint4(0, 0, 0, 0);
+                const unsigned short* as = reinterpret_cast<const unsigned short*>(&av);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) ta[q * 8 + k][j - 1] = as[k];
+            }
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
-            const int c = e >> 5, xl = e & 31;
-            const size_t at = ((size_t)row * C + c) * Wp + x0 + xl;
-            at16[at] = ta[c][xl];
+        for (int e = threadIdx.x; e < 32 * (nx / 8); e += blockDim.x) {
+            const int c = e / (nx / 8), x8 = (e % (nx / 8)) * 8;
+            const size_t at = ((size_t)row * C + c) * Wp + x0 + x8;
+            auto pack = [](const unsigned short* r) {  // eight 16-bit values, first lowest
+                return make_uint4((unsigned)r[0] | (unsigned)r[1] << 16, (unsigned)r[2] | (unsigned)r[3] << 16,
+                                  (unsigned)r[4] | (unsigned)r[5] << 16, (unsigned)r[6] | (unsigned)r[7] << 16);
+            };
+            *reinterpret_cast<uint4*>(at16 + at) = pack(&ta[c][x8]);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) gt16[k * copy + at] = tg[c][xl - k + 2];
+            for (int d = 0; d < 3; ++d) *reinterpret_cast<uint4*>(gt16 + d * copy + at) = pack(&tg[c][x8 - d + 2]);
         }
     }
 }
@@ -500,7 +516,7 @@ bool enqueue_wgrad_c32(const __nv_bfloat16* gout, const __nv_bfloat16* ain, Vol 
                        float* db, cudaStream_t s) {
     const int Wp = padded_width(g.W);
     const long long rows = (long long)g.nvol * g.D * g.H;
-    const long long tiles = rows * (Wp / 32);
+    const long long tiles = rows * ((Wp / 32 + 1) / 2);
     const unsigned tgrid = (unsigned)std::min<long long>(tiles, 152LL * 16);
     k_wgrad_operands<<<tgrid, 256, 0, s>>>(ain, gout, L.actT, L.gT, rows, g.W, Wp);
     int nslots = 0;
