@@ -20,8 +20,11 @@
 // 54 N = 32 ones per tile: with 32 output channels the MMA issue rate, not
 // the tensor datapath, bounds the narrow form.
 //
-// Warp-specialised and persistent: one lane issues TMA loads into a ring of
-// A stages, one lane issues the MMAs (a commit frees each stage), and four
+// Warp-specialised and persistent: each CTA walks whole columns of tiles
+// (one row block and column block of a volume) frame by frame, so each
+// frame's box, loaded once, serves the three tiles that read it; one lane
+// issues TMA loads into a ring of A stages, one lane issues the MMAs (a
+// commit frees a frame's stage once its last tile is issued), and four
 // warps read the double-buffered accumulator with tcgen05.ld (warp w owns
 // lanes 32w..32w+31, i.e. voxels 32w..32w+31 of the tile) and apply the
 // epilogue while the next tile accumulates.  Every mbarrier wait is
@@ -224,7 +227,21 @@ k_conv3d_c32_tc(const __grid_constant__ CUtensorMap act_map, const __grid_consta
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *s_tmem;
-    const long long my_tiles = a.ntiles > blockIdx.x ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    // Each CTA walks whole columns of tiles -- (volume, row block, column
+    // block) -- frame by frame, so a frame's activation box serves the three
+    // tiles (frames z - 1, z, z + 1) that read it: a column of D tiles loads
+    // D + 2 boxes (frames -1 and D arrive as zeros) where tile by tile it
+    // would load 3 D.  Ring slot q holds the column's frame q - q0 - 1.
+    const long long ncols = (long long)a.nvol * a.tiles_h * a.tiles_w;
+    const long long my_cols = ncols > blockIdx.x ? (ncols - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const long long my_tiles = my_cols * a.D;
+    auto column = [&](long long cj, int& tw, int& th, int& vol) {
+        long long c = blockIdx.x + cj * gridDim.x;
+        tw = (int)(c % a.tiles_w);
+        c /= a.tiles_w;
+        th = (int)(c % a.tiles_h);
+        vol = (int)(c / a.tiles_h);
+    };
 
     if (warp == 4 && lane == 0) {
         // ---------------- TMA producer ----------------
@@ -235,41 +252,39 @@ k_conv3d_c32_tc(const __grid_constant__ CUtensorMap act_map, const __grid_consta
             for (int t = 0; t < 9; ++t) tma_load_3d(smem_u32(s_w + t * kW1PairBytes), &w_map, bar_w, 0, 0, t);
         }
         uint32_t q = 0;
-        long long issued_tiles = 0;
-        for (long long j = 0; j < my_tiles && !*s_abort; ++j) {
-            long long tr = blockIdx.x + j * gridDim.x;
-            const int tw = (int)(tr % a.tiles_w); tr /= a.tiles_w;
-            const int th = (int)(tr % a.tiles_h); tr /= a.tiles_h;
-            const int z = (int)(tr % a.D), vol = (int)(tr / a.D);
+        for (long long cj = 0; cj < my_cols && !*s_abort; ++cj) {
+            int tw, th, vol;
+            column(cj, tw, th, vol);
             const int w0 = tw * a.BW, h0 = th * a.BH;
             bool ok = true;
-            for (int k = 0; k < 3; ++k, ++q) {  // dz = k - 1
+            for (int f = -1; f <= a.D; ++f, ++q) {  // the column's frames, with a zero frame at each end
                 const uint32_t s = q % kStages, use = q / kStages;
                 if (use > 0 && !mbar_wait(bar_empty + 8 * s, (use - 1) & 1)) { ok = false; break; }
                 mbar_expect_tx(bar_full + 8 * s, kABytes);
-                tma_load_5d(smem_u32(s_a + s * kABytes), &act_map, bar_full + 8 * s, 0, w0 - 1, h0 - 1, z + k - 1,
-                            vol);
+                tma_load_5d(smem_u32(s_a + s * kABytes), &act_map, bar_full + 8 * s, 0, w0 - 1, h0 - 1, f, vol);
             }
             if (!ok) { *s_abort = 1; atomicExch(a.err, 1); break; }
-            ++issued_tiles;
         }
         // drain: every load issued must have landed before the CTA exits
         for (uint32_t k = (q >= kStages ? q - kStages : 0); k < q; ++k)
             mbar_wait(bar_full + 8 * (k % kStages), (k / kStages) & 1);
-        (void)issued_tiles;
     }
     if (warp == 5 && lane == 0) {
         // ---------------- MMA issuer ----------------
         bool ok = mbar_wait(bar_w, 0);
-        uint32_t q = 0;
-        for (long long j = 0; j < my_tiles && ok && !*s_abort; ++j) {
+        uint32_t q0 = 0;  // ring index of the current column's frame -1
+        long long j = 0;  // tiles issued (the accumulator buffers alternate)
+        for (long long cj = 0; cj < my_cols && ok && !*s_abort; ++cj) {
+        for (int z = 0; z < a.D; ++z, ++j) {
             const uint32_t b = (uint32_t)(j & 1), use_b = (uint32_t)(j >> 1);
             if (use_b > 0 && !mbar_wait(bar_acce + 8 * b, (use_b - 1) & 1)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t d = tmem + b * kAccCols;
-            for (int k = 0; k < 3; ++k, ++q) {  // dz = k - 1
+            for (int k = 0; k < 3; ++k) {  // dz = k - 1: frame z + k - 1, ring index q0 + z + k
+                const uint32_t q = q0 + (uint32_t)(z + k);
                 const uint32_t s = q % kStages, use = q / kStages;
-                if (!mbar_wait(bar_full + 8 * s, use & 1)) { ok = false; break; }
+                // each frame is waited for once, by the first tile that reads it
+                if ((z == 0 || k == 2) && !mbar_wait(bar_full + 8 * s, use & 1)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
                 for (int dyi = 0; dyi < 3; ++dyi) {
@@ -282,10 +297,16 @@ k_conv3d_c32_tc(const __grid_constant__ CUtensorMap act_map, const __grid_consta
                     umma_bf16<NN>(d, smem_desc_sw64(abase), smem_desc_sw64(bbase), (k > 0 || dyi > 0) ? 1u : 0u);
                     umma_bf16<NN>(d, smem_desc_sw64(abase + 32), smem_desc_sw64(bbase + 32), 1u);
                 }
-                umma_commit(bar_empty + 8 * s);
             }
             if (!ok) break;
             umma_commit(bar_accf + 8 * b);
+            umma_commit(bar_empty + 8 * ((q0 + (uint32_t)z) % kStages));  // frame z - 1 is read no more
+        }
+        if (!ok) break;
+        // the column's last two frames
+        umma_commit(bar_empty + 8 * ((q0 + (uint32_t)a.D) % kStages));
+        umma_commit(bar_empty + 8 * ((q0 + (uint32_t)a.D + 1) % kStages));
+        q0 += (uint32_t)a.D + 2;
         }
         if (!ok) {
             // every MMA issued so far must finish before tensor memory is freed
@@ -337,10 +358,9 @@ k_conv3d_c32_tc(const __grid_constant__ CUtensorMap act_map, const __grid_consta
                 for (int c = 0; c < 32; ++c) v[c] += __shfl_down_sync(0xffffffffu, g[c], 2);
             }
             }
-            long long tr = blockIdx.x + j * gridDim.x;
-            const int tw = (int)(tr % a.tiles_w); tr /= a.tiles_w;
-            const int th = (int)(tr % a.tiles_h); tr /= a.tiles_h;
-            const int z = (int)(tr % a.D), vol = (int)(tr / a.D);
+            int tw, th, vol;
+            column(j / a.D, tw, th, vol);
+            const int z = (int)(j % a.D);
             const int hh = th * a.BH + warp, ww = tw * a.BW + lane;
             if (lane < kOutW && hh < a.H && ww < a.W) {
                 const long long vox = (((long long)vol * a.D + z) * a.H + hh) * a.W + ww;
@@ -607,7 +627,8 @@ bool launch_conv(const __nv_bfloat16* act, const __nv_bfloat16* w, ConvTcArgs a,
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long grid = std::min<long long>(a.ntiles, (long long)sms * 2);
+    const long long ncols = a.ntiles / a.D;  // columns of tiles, each walked by one CTA
+    const long long grid = std::max(1LL, std::min<long long>(ncols, (long long)sms * 2));
     k_conv3d_c32_tc<NN><<<(unsigned)grid, kThreads, smem, s>>>(amap, wmap, a);
     return true;
 }
