@@ -1385,34 +1385,36 @@ struct MicroCfg {
     static constexpr int MR = MR_, MC = MC_;  // block rows and columns per thread
     static constexpr int EW = TX * MC;        // tile width (columns)
     static constexpr int EH = TY * MR;        // tile height (rows)
-    // Exchange arrays, in floats: one 4-vector per thread as two float2 halves
-    // (columns 0-1, then 2-3: HALF floats apart), entry (row, tx) at float2
-    // index row TX + tx, so a warp's 64-bit accesses are conflict-free; zero
-    // pad rows where a tile-edge thread reads past the tile.
+    // Exchange arrays, in floats: one MC-vector per thread as MC / 2 float2
+    // planes (columns 0-1, 2-3, ...: HALF floats apart), entry (row, tx) at
+    // float2 index row TX + tx of each plane, so a warp's 64-bit accesses are
+    // conflict-free; zero pad rows where a tile-edge thread reads past the tile.
     //   XT: theta (Clip: theta_v) of the block's first row, rows 0 .. TY - 1 = ty, pad row TY
     //   WB: w_v (at the end p_v) of the block's last row,    rows 1 .. TY = ty + 1, pad row 0
     static constexpr int HALF = (TY + 1) * TX * 2;
     static constexpr int A_XT = 0;
-    static constexpr int A_WB = A_XT + 2 * HALF;
+    static constexpr int A_WB = A_XT + (MC / 2) * HALF;
     // Two staging tiles [EH][SW] for the epilogue's stores (see fused_tile_micro).
     static constexpr int SW = EW + 4;
-    static constexpr int A_ST = A_WB + 2 * HALF;
+    static constexpr int A_ST = A_WB + (MC / 2) * HALF;
     static constexpr size_t SMEM = (size_t)(A_ST + 2 * EH * SW) * sizeof(float);
     static_assert(NT % TX == 0 && TX >= 8 && TX <= 32 && 32 % TX == 0, "whole rows of threads in each warp");
-    static_assert((MR == 2 || MR == 4) && MC == 4, "blocks of 2 or 4 rows by 4 columns");
+    static_assert((MR == 2 || MR == 4) && (MC == 4 || MC == 8), "blocks of 2 or 4 rows by 4 or 8 columns");
 };
 
-// A 4-vector of an exchange array: two float2 halves HALF floats apart.
-template <int HALF>
-__device__ __forceinline__ void ld4h(const float* base, int idx, float (&v)[4]) {
-    const float2 lo = reinterpret_cast<const float2*>(base)[idx];
-    const float2 hi = reinterpret_cast<const float2*>(base + HALF)[idx];
-    v[0] = lo.x, v[1] = lo.y, v[2] = hi.x, v[3] = hi.y;
+// An N-vector of an exchange array: N / 2 float2 planes HALF floats apart.
+template <int HALF, int N>
+__device__ __forceinline__ void ld4h(const float* base, int idx, float (&v)[N]) {
+#pragma unroll
+    for (int p = 0; p < N / 2; ++p) {
+        const float2 t = reinterpret_cast<const float2*>(base + p * HALF)[idx];
+        v[2 * p] = t.x, v[2 * p + 1] = t.y;
+    }
 }
-template <int HALF>
-__device__ __forceinline__ void st4h(float* base, int idx, const float (&v)[4]) {
-    reinterpret_cast<float2*>(base)[idx] = make_float2(v[0], v[1]);
-    reinterpret_cast<float2*>(base + HALF)[idx] = make_float2(v[2], v[3]);
+template <int HALF, int N>
+__device__ __forceinline__ void st4h(float* base, int idx, const float (&v)[N]) {
+#pragma unroll
+    for (int p = 0; p < N / 2; ++p) reinterpret_cast<float2*>(base + p * HALF)[idx] = make_float2(v[2 * p], v[2 * p + 1]);
 }
 
 // One tile (bx, by) of frame bz on micro-tiles.  The arithmetic of every slot
@@ -1570,7 +1572,7 @@ __device__ __forceinline__ void fused_tile_micro(const FusedArgs& a, const Prob&
 
     // zero the pad rows (XT row TY, WB row 0), then publish w_v of the last row
     if (tid < TX) {
-        const float zero[4] = {0.f, 0.f, 0.f, 0.f};
+        const float zero[MC] = {};
         st4h<HALF>(XT, TY * TX + tid, zero);
         st4h<HALF>(WB, tid, zero);
     }
@@ -1701,8 +1703,10 @@ __device__ __forceinline__ void fused_tile_micro(const FusedArgs& a, const Prob&
         ++stage;
 #pragma unroll
         for (int i = 0; i < MR; ++i)
-            *reinterpret_cast<float4*>(sb + (r0 + i) * SW + c0) =
-                make_float4(val(i, 0), val(i, 1), val(i, 2), val(i, 3));
+#pragma unroll
+            for (int j = 0; j < MC; j += 4)
+                *reinterpret_cast<float4*>(sb + (r0 + i) * SW + c0 + j) =
+                    make_float4(val(i, j), val(i, j + 1), val(i, j + 2), val(i, j + 3));
         __syncthreads();
         for (int r = H + warp; r < r_end; r += Cfg::NT / 32) {
             const long long row = fbase + (long long)(gi0 + r) * g.ny + gj0;

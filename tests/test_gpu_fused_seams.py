@@ -17,10 +17,11 @@ from gpu_helpers import TOL_F32, lib, make_problem, to_dev
 
 pytestmark = pytest.mark.gpu
 
-# One-frame tiles (128 x 64 extended; 64 x 32 for small images at K <= 7) and
-# the 32 x 32 VTV tile: several tiles per axis, none dividing the extent.
+# One-frame tiles (64 x 128 extended; 32 x 64 for small images at K <= 7) and
+# the VTV tiles (32 x 32 for up to 10 frames, 32 x 16 for 16 and 24): several
+# tiles per axis, none dividing the extent.
 CASES = [("atv", 200, 330, 3), ("atv", 150, 120, 2), ("itv2d", 173, 259, 2), ("vtv", 97, 131, 10),
-         ("vtv", 61, 45, 7)]
+         ("vtv", 61, 45, 7), ("vtv", 70, 83, 16), ("vtv", 40, 53, 24)]
 
 
 @pytest.fixture(scope="module")
