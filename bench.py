@@ -252,15 +252,12 @@ def run_gpu(args):
                          u=torch.empty((B, nx, ny), device=dev), x=torch.empty((B, nx, ny), device=dev),
                          work=pkg.Workspace(dev)))
 
-    def solve_all(yy, bb):
-        n = 0
-        for bf in bufs:
-            _solve(pkg, bf, yy, bb)
-            n += pkg.sci_last_solve_launches()
-        return n
-
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    lanes = _lanes(torch, dev, stream, args.streams)
+
+    def solve_all(yy, bb):
+        return _run_six(pkg, torch, lanes, bufs, yy, bb)
 
     for _ in range(args.warmup):
         solve_all(y, bits)
@@ -322,7 +319,7 @@ def run_gpu(args):
     learned = None if args.no_learned else _learned(pkg, torch, dev, stream, flush)
 
     # ---- end to end: host buffers through the public API ----
-    e2e = _e2e(pkg, torch, dev, stream, args, c, masks_h, y, bufs, flush, world)
+    e2e = _e2e(pkg, torch, dev, stream, args, c, masks_h, y, bufs, flush, lanes, world)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -330,6 +327,7 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(_workload_desc(c), l2="flushed between timed steps (256 MiB write)",
                        parallelism=f"replicas x{world} (independent measurements, no collective)",
+                       streams=len(lanes),
                        step_ms=[round(s, 3) for s in step_ms],
                        paper_context="paper: ~3 min for 150 iterations of 512x512x10 ITV3D-FGP on an "
                                      "i7 laptop (about 2.2e6 voxel-iters/s; real data, inner iterations "
@@ -357,6 +355,33 @@ def run_gpu(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def _lanes(torch, dev, stream, n):
+    """The streams the six reconstructions of a step are spread over: the
+    launching stream first, then n - 1 more."""
+    return [stream] + [torch.cuda.Stream(dev) for _ in range(max(1, n) - 1)]
+
+
+def _run_six(pkg, torch, lanes, bufs, yy, bb, outs_h=None):
+    """One step: reconstruction i runs on stream i mod len(lanes) (each has
+    its own buffers and workspace), after everything already queued on the
+    launching stream, which then waits for all of them.  With outs_h, each
+    x^(T) is copied to its pinned host buffer on its reconstruction's stream.
+    Returns the number of kernels launched."""
+    main = lanes[0]
+    for s in lanes[1:]:
+        s.wait_stream(main)
+    n = 0
+    for i, bf in enumerate(bufs):
+        with torch.cuda.stream(lanes[i % len(lanes)]):
+            _solve(pkg, bf, yy, bb)
+            n += pkg.sci_last_solve_launches()
+            if outs_h is not None:
+                outs_h[i].copy_(bf["x"], non_blocking=True)
+    for s in lanes[1:]:
+        main.wait_stream(s)
+    return n
 
 
 def _solve(pkg, bf, y, bits):
@@ -945,10 +970,11 @@ def _bf16_peak():
     return 1900.0
 
 
-def _e2e(pkg, torch, dev, stream, args, c, masks_h, y_dev, bufs, flush, world=1):
+def _e2e(pkg, torch, dev, stream, args, c, masks_h, y_dev, bufs, flush, lanes, world=1):
     """Same metric through the public API with host inputs/outputs: each step
     copies y and the dense masks from pinned host memory, packs the masks,
-    runs the six reconstructions and copies every x^(T) back."""
+    runs the six reconstructions (on the timed step's streams) and copies
+    every x^(T) back."""
     B, nx, ny = c["B"], c["nx"], c["ny"]
     N = B * nx * ny
     y_h = y_dev.cpu().pin_memory()
@@ -961,9 +987,7 @@ def _e2e(pkg, torch, dev, stream, args, c, masks_h, y_dev, bufs, flush, world=1)
         y_d.copy_(y_h, non_blocking=True)
         m_d.copy_(m_h, non_blocking=True)
         bb = pkg.sci_masks_pack(m_d, check=False)
-        for bf, oh in zip(bufs, outs_h):
-            _solve(pkg, bf, y_d, bb)
-            oh.copy_(bf["x"], non_blocking=True)
+        _run_six(pkg, torch, lanes, bufs, y_d, bb, outs_h)
 
     step()
     torch.cuda.synchronize(dev)
@@ -1018,6 +1042,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["sci", "reference"], default="sci")
+    ap.add_argument("--streams", type=int, default=2,
+                    help="CUDA streams the six reconstructions of a step are spread over")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-measurement batched solve")
     ap.add_argument("--no-learned", action="store_true", help="skip training and running the learned prox")
