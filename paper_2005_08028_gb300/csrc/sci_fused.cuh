@@ -1806,9 +1806,11 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
 
 // ---------------------------------------------------------------- configurations
 
-// One-frame tiles (16-row strips) update every row: skipping rows would idle
-// whole strips and stall the others at the barriers.  The VTV tiles have
-// 1- or 2-row strips, where skipping balances well and saves work.
+// One-frame tiles update every row: idling a 16-row strip, or a warp of 4 x 4
+// blocks whose rows can no longer reach an exact row, costs more than it
+// saves (the test splits the two-update loop body the compiler interleaves).
+// The VTV tiles have 1- or 2-row strips, where skipping balances well and
+// saves work.
 using CfgF1 = RowCfg<512, 16, 7>;    // 128 x 64 tile, one frame
 using CfgF1s = RowCfg<256, 8, 6>;    // 64 x 32 tile, one frame (small images)
 using CfgM1 = MicroCfg<512, 5, 4, 4>;   // 128 x 64 tile of 4 x 4 blocks, one frame
