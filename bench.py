@@ -1050,7 +1050,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip the fuse-depth autotuner section")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the 2048x2048x32 FP32 / FP16 / BF16 storage solves")
-    ap.add_argument("--kernel-case", choices=["fused", "conv", "lprox"], default=None,
+    ap.add_argument("--kernel-case", choices=["fused", "conv", "lprox", "large", "batched"], default=None,
                     help="run one launch of the dominant kernel per TV form and exit (for profilers)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -1065,7 +1065,13 @@ def run_kernel_case(args):
     size.  conv: one tensor-core 32->32 conv over 8 x 10 x 512 x 512 voxels
     (1.3 GB of BF16 activations, larger than L2).  lprox: the learned prox from
     its initial weights, five applies on 8 x 10 x 512 x 512 and five training
-    steps on 32 x 8 x 64 x 64 (two of each untimed), timed with CUDA events."""
+    steps on 32 x 8 x 64 x 64 (two of each untimed), timed with CUDA events.
+    large: two outer iterations of GAP-ITV2D on the 2048x2048x32 size (512 MiB
+    per FP32 field, larger than L2) with FP32, then BF16 storage.  batched: two
+    outer iterations of the batched GAP-VTV solve (S = 5, BF16) on eight
+    measurements, two of each size class (128x128x8, 256x256x8, 512x512x10,
+    1024x1024x24).  The last two draw uniform random videos and Bernoulli(0.5)
+    masks on the device: they exist to be profiled, not to be checked."""
     import torch
     from paper_2005_08028_gb300 import build as b
     if not os.path.exists(b.LIB_PATH):
@@ -1105,6 +1111,31 @@ def run_kernel_case(args):
         torch.cuda.synchronize()
         print(json.dumps({"kernel_case": "conv", "ok": int(err.item()) == 0}))
         return 0 if int(err.item()) == 0 else 1
+    if args.kernel_case in ("large", "batched"):
+        gen = torch.Generator(device=dev).manual_seed(3)
+
+        def measurement(B, nx, ny):
+            x = torch.rand((B, nx, ny), generator=gen, device=dev)
+            bits = pkg.sci_masks_pack((torch.rand((B, nx, ny), generator=gen, device=dev) < 0.5).to(torch.uint8))
+            return pkg.sci_forward(x, bits), bits
+
+        if args.kernel_case == "large":
+            B, nx, ny = 32, 2048, 2048
+            y, bits = measurement(B, nx, ny)
+            theta = torch.empty((B, nx, ny), device=dev)
+            work = pkg.Workspace(dev)
+            for storage in ("f32", "bf16"):
+                pkg.sci_gap_tv(y, bits, B, "itv2d", 0.05, 2, 10, theta=theta, init=True, work=work, storage=storage)
+        else:
+            ys, bitss, Bs = [], [], []
+            for (nx, ny, B) in ((128, 128, 8), (256, 256, 8), (512, 512, 10), (1024, 1024, 24)) * 2:
+                y, bits = measurement(B, nx, ny)
+                ys.append(y), bitss.append(bits), Bs.append(B)
+            batch = pkg.Batch(ys, bitss, Bs)
+            pkg.sci_gap_tv_batched(batch, "vtv", 0.05, 2, 5, storage="bf16")
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel_case": args.kernel_case, "ok": True}))
+        return 0
     x = torch.rand((c["B"], c["nx"], c["ny"]), device=dev)
     work = pkg.Workspace(dev)
     for tv in ("atv", "itv2d", "vtv"):
