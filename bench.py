@@ -453,6 +453,7 @@ def _roofline(pkg, torch, dev, stream, c, B, nx, ny):
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1) / reps
         per_tv[tv] = {"updates_per_launch": K, "launch_ms": round(ms, 5),
+                      "frac": round(ALU_OPS_PER_UPDATE * N * K / (ms * 1e-3) / _alu_peak(), 4),
                       "dram_bytes_ncu": NCU_DRAM_BYTES_PER_LAUNCH.get(tv)}
         traffic.append(NCU_DRAM_BYTES_PER_LAUNCH.get(tv))
         ops += ALU_OPS_PER_UPDATE * N * K
