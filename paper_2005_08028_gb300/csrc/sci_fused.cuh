@@ -1097,7 +1097,7 @@ struct RowCfg {
 template <typename T, int TV, class Cfg, class Prob>
 __device__ __forceinline__ void fused_tile_rows(const FusedArgs& a, const Prob& p, int bx, int by, int bz,
                                                 float* smem) {
-    constexpr int Q = Cfg::Q, EW = Cfg::EW, EH = Cfg::EH, NS = Cfg::NS, LD = Cfg::LD, FP = Cfg::FPP;
+    constexpr int Q = Cfg::Q, EW = Cfg::EW, EH = Cfg::EH, LD = Cfg::LD, FP = Cfg::FPP;
     constexpr bool CLIP = TV == kTvClip;
     float* s_th = smem;                      // [FPP] theta (Clip: theta_h)
     float* s_wh = s_th + FP;                 // [FPP]
@@ -1488,8 +1488,8 @@ __device__ __forceinline__ void fused_tile_micro(const FusedArgs& a, const Prob&
     float tv[CLIP ? MR : 1][CLIP ? MC : 1];  // Clip box: theta_v
     (void)tv;
     // The Clip box's p is its w: ph / pv stay unused there.
-    auto& PH = [&]() -> float(&)[MR][MC] { if constexpr (CLIP) return wh; else return ph; }();
-    auto& PV = [&]() -> float(&)[MR][MC] { if constexpr (CLIP) return wv; else return pv; }();
+    float(&PH)[MR][MC] = *[&] { if constexpr (CLIP) return &wh; else return &ph; }();
+    float(&PV)[MR][MC] = *[&] { if constexpr (CLIP) return &wv; else return &pv; }();
 
     // ---- loads for the whole extended tile, all issued before any is used ----
     const bool warm_first = a.first && a.warm;  // w from the previous TVdenoise, p = 0

@@ -2,7 +2,6 @@
 launch must reproduce the single-measurement solver exactly (FP32: the fused
 tile arithmetic does not depend on the tiling) and the FP64 oracle within
 1e-4."""
-import numpy as np
 import pytest
 
 import oracle as O

@@ -22,7 +22,7 @@ import pytest
 
 import oracle as O
 import sci_synth as ss
-from gpu_helpers import TOL_F32, lib, to_dev, torch
+from gpu_helpers import TOL_F32, lib, to_dev
 
 pytestmark = pytest.mark.gpu
 

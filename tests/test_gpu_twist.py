@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from gpu_helpers import TOL_F32, lib, make_problem, maxabs, to_dev, torch
+from gpu_helpers import TOL_F32, lib, make_problem, maxabs, to_dev
 
 pytestmark = pytest.mark.gpu
 
