@@ -1809,14 +1809,16 @@ __device__ __forceinline__ void fused_tile(const FusedArgs& a, const Prob& p, in
 // One-frame tiles update every row: idling a 16-row strip, or a warp of 4 x 4
 // blocks whose rows can no longer reach an exact row, costs more than it
 // saves (the test splits the two-update loop body the compiler interleaves).
-// The VTV tiles have 1- or 2-row strips, where skipping balances well and
-// saves work.
+// So do the 8- and 10-frame VTV tiles (measured 7-12% faster than skipping
+// rows: every warp then reaches each barrier with the same work).  The 16-
+// and 24-frame tiles skip such rows: updating every row measured slower for
+// the first and spills for the second.
 using CfgF1 = RowCfg<512, 16, 7>;    // 128 x 64 tile, one frame
 using CfgF1s = RowCfg<256, 8, 6>;    // 64 x 32 tile, one frame (small images)
 using CfgM1 = MicroCfg<512, 5, 4, 4>;   // 128 x 64 tile of 4 x 4 blocks, one frame
 using CfgM1s = MicroCfg<256, 4, 2, 4>;  // 64 x 32 tile of 2 x 4 blocks, one frame
-using CfgV8 = FusedCfg<512, 2, 8, 5, true, true>;      // 32 x 32 tile, up to 8 frames
-using CfgV10 = FusedCfg<512, 2, 10, 5, false, true>;   // 32 x 32 tile, up to 10 frames
+using CfgV8 = FusedCfg<512, 2, 8, 5, true, false>;     // 32 x 32 tile, up to 8 frames
+using CfgV10 = FusedCfg<512, 2, 10, 5, false, false>;  // 32 x 32 tile, up to 10 frames
 using CfgV16 = FusedCfg<512, 1, 16, 5, false, true>;   // 32 x 16 tile, up to 16 frames
 using CfgV24 = BlkCfg<256, 2, 24, 5, false, true>;     // 32 x 16 tile, up to 24 frames
 
